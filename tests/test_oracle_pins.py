@@ -1,0 +1,322 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+hand-worked examples, closed forms, textbook special cases, invariants of
+the method and brute force on tiny inputs.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import spamm_inputs as gen
+from oracle import oracle as O
+from tests.golden_io import read_worked_examples
+
+
+def _padded(A, b):
+    n = A.shape[0]
+    d = O.depth(n, b)
+    npad = b << d
+    P = np.zeros((npad, npad))
+    P[:n, :n] = A.astype(np.float64)
+    return P, d
+
+
+def _leaf_norm2(A, b):
+    """Leaf squared norms straight from numpy (independent of the oracle)."""
+    P, d = _padded(A, b)
+    nb = 1 << d
+    return (P * P).reshape(nb, b, nb, b).sum(axis=(1, 3))
+
+
+def _as_set(tr):
+    return set(map(tuple, np.asarray(tr).tolist()))
+
+
+# ------------------------------------------------------------- Eq. (depth)
+
+@pytest.mark.parametrize("n,b,d", [(1000, 16, 6), (1024, 16, 6), (7500, 16, 9),
+                                   (16384, 16, 10), (16384, 128, 7), (1, 16, 0),
+                                   (16, 16, 0), (17, 16, 1), (8192, 16, 9)])
+def test_depth_closed_form(n, b, d):
+    assert O.depth(n, b) == d
+    if n > b:   # the paper's formula itself, evaluated in floating point
+        assert math.ceil(math.log(n / b) / math.log(2)) == d
+
+
+# ------------------------------------------------------------- Eq. (norm)
+
+@pytest.mark.parametrize("n,b", [(40, 4), (64, 16), (100, 16), (33, 8)])
+def test_pyramid_matches_block_sums(n, b):
+    A = gen.exp_decay_nonsym(n, 0.8, seed=3)
+    pyr = O.pyramid(A, b)
+    P, d = _padded(A, b)
+    for t in range(d + 1):
+        w = 1 << t
+        s = (b << d) // w
+        ref = (P * P).reshape(w, s, w, s).sum(axis=(1, 3))
+        np.testing.assert_allclose(O.tier(pyr, t), ref, rtol=1e-13, atol=0)
+    assert pyr[0] == pytest.approx(np.linalg.norm(A.astype(np.float64)) ** 2, rel=1e-13)
+
+
+def test_parent_never_below_child():
+    A = gen.water_like(20, 5)  # n = 100
+    pyr = O.pyramid(A, 4)
+    d = O.depth(100, 4)
+    for t in range(d):
+        par = O.tier(pyr, t)
+        ch = O.tier(pyr, t + 1)
+        w = 1 << t
+        for di in range(2):
+            for dj in range(2):
+                assert np.all(par >= ch[di::2, dj::2][:w, :w])
+
+
+# ----------------------------------------------------- hand-worked golden
+
+def test_worked_examples():
+    mats, cases = read_worked_examples()
+    A = mats["A"]
+    assert cases
+    for case in cases:
+        r = O.multiply(A, A, case["b"], case["tau"])
+        assert sorted(_as_set(r.triples)) == case["triples"], case["name"]
+        np.testing.assert_array_equal(r.C, case["C"], err_msg=case["name"])
+        if "cand" in case:
+            assert list(r.cand) == case["cand"]
+            assert list(r.kept) == case["kept"]
+        d = O.depth(4, case["b"])
+        pa = O.pyramid(A, case["b"])
+        assert _as_set(O.cull_linkless(pa, pa, d, case["tau"])) == set(case["triples"])
+
+
+# ------------------------------------------------------------- tau = 0
+
+@pytest.mark.parametrize("n,b", [(50, 8), (64, 16), (37, 4), (100, 32), (16, 16), (5, 16)])
+def test_tau0_is_dense_product(n, b):
+    A = gen.uniform_dense(n, seed=1, symmetric=False)
+    B = gen.exp_decay_nonsym(n, 0.9, seed=2)
+    r = O.multiply(A, B, b, 0.0)
+    E = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.abs(r.C - E).max() <= 1e-13 * np.abs(E).max()
+    nbr = -(-n // b)
+    # every non-padding leaf is non-zero here, so all nbr^3 triples survive
+    assert len(r.triples) == nbr ** 3
+
+
+def test_transpose_is_not_confused():
+    n, b = 48, 8
+    A = gen.exp_decay_nonsym(n, 0.7, seed=5)
+    B = gen.uniform_dense(n, seed=6, symmetric=False)
+    r1 = O.multiply(A, B, b, 0.0).C
+    r2 = O.multiply(B.T.copy(), A.T.copy(), b, 0.0).C
+    np.testing.assert_allclose(r1, r2.T, rtol=0, atol=1e-12)
+    assert np.abs(r1 - r1.T).max() > 1e-3
+
+
+# --------------------------------------- flat (Algorithm 1) == recursive
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_linkless_equals_recursive(seed):
+    rng = np.random.default_rng(seed)
+    for n, b in [(64, 4), (96, 8), (128, 16), (20, 2)]:
+        A = gen.exp_decay_nonsym(n, float(rng.uniform(0.5, 0.95)), seed=seed)
+        B = gen.water_like(4, n // 4, seed=seed)[:n, :n].copy() if n % 4 == 0 else A
+        pa, pb = O.pyramid(A, b), O.pyramid(B, b)
+        d = O.depth(n, b)
+        for tau in [0.0] + list(10.0 ** rng.uniform(-8, 0, size=6)):
+            rec = _as_set(O.cull_recursive(pa, pb, d, tau)[0])
+            flat = _as_set(O.cull_linkless(pa, pb, d, tau))
+            assert rec == flat
+
+
+def test_brute_force_tiny():
+    """Every leaf triple enumerated directly with numpy norms."""
+    rng = np.random.default_rng(7)
+    for n, b in [(8, 2), (12, 4), (16, 2), (9, 4)]:
+        A = gen.exp_decay_nonsym(n, 0.6, seed=11)
+        B = gen.exp_decay_nonsym(n, 0.5, seed=12)
+        na, nb2 = _leaf_norm2(A, b), _leaf_norm2(B, b)
+        w = na.shape[0]
+        pa, pb = O.pyramid(A, b), O.pyramid(B, b)
+        d = O.depth(n, b)
+        for tau in 10.0 ** rng.uniform(-4, 0.5, size=8):
+            want = {(i, k, j) for i in range(w) for k in range(w) for j in range(w)
+                    if na[i, k] > 0 and nb2[k, j] > 0
+                    and math.sqrt(na[i, k]) * math.sqrt(nb2[k, j]) >= tau * (1 + 1e-12)}
+            maybe = {(i, k, j) for i in range(w) for k in range(w) for j in range(w)
+                     if na[i, k] > 0 and nb2[k, j] > 0
+                     and abs(math.sqrt(na[i, k] * nb2[k, j]) - tau) <= 1e-12 * tau}
+            got = _as_set(O.cull_recursive(pa, pb, d, tau)[0])
+            assert want <= got <= want | maybe
+            # and the numeric part: each C block is the plain sum over kept K
+            r = O.multiply(A, B, b, tau)
+            P, _ = _padded(A, b)
+            Q, _ = _padded(B, b)
+            Cref = np.zeros_like(P)
+            for (i, k, j) in got:
+                Cref[i*b:(i+1)*b, j*b:(j+1)*b] += P[i*b:(i+1)*b, k*b:(k+1)*b] @ \
+                    Q[k*b:(k+1)*b, j*b:(j+1)*b]
+            np.testing.assert_allclose(r.C, Cref[:n, :n], rtol=1e-13, atol=1e-15)
+
+
+# ------------------------------------------------------------ invariants
+
+def test_monotone_nesting():
+    A = gen.exp_decay(128, 0.85, seed=4)
+    pa = O.pyramid(A, 8)
+    d = O.depth(128, 8)
+    prev = None
+    for tau in [0, 1e-8, 1e-6, 1e-4, 1e-3, 1e-2, 1e-1, 1, 10]:
+        s = _as_set(O.cull_recursive(pa, pa, d, tau)[0])
+        if prev is not None:
+            assert s <= prev
+        prev = s
+
+
+def test_tau_above_root_product():
+    A = gen.exp_decay(64, 0.9, seed=1)
+    B = gen.uniform_dense(64, seed=2)
+    root = np.linalg.norm(A.astype(np.float64)) * np.linalg.norm(B.astype(np.float64))
+    C0 = gen.uniform_dense(64, seed=3).astype(np.float64)
+    r = O.multiply(A, B, 16, root * 1.0001, alpha=2.0, beta=-0.5, C=C0)
+    assert len(r.triples) == 0
+    np.testing.assert_array_equal(r.C, -0.5 * C0)
+    r2 = O.multiply(A, B, 16, root * 0.9999)
+    assert r2.kept[0] == 1                  # the root product itself survives
+    na, nb2 = np.sqrt(_leaf_norm2(A, 16)), np.sqrt(_leaf_norm2(B, 16))
+    best = max(na[i, k] * nb2[k, j] for i in range(4) for k in range(4) for j in range(4))
+    assert len(O.multiply(A, B, 16, best * 0.9999).triples) >= 1
+    assert len(O.multiply(A, B, 16, best * 1.0001).triples) == 0
+
+
+def test_alpha_beta_epilogue():
+    n = 40
+    A = gen.exp_decay(n, 0.8, seed=1)
+    C0 = gen.uniform_dense(n, seed=9, symmetric=False).astype(np.float64)
+    base = O.multiply(A, A, 8, 1e-3).C
+    r = O.multiply(A, A, 8, 1e-3, alpha=-1.5, beta=0.25, C=C0).C
+    np.testing.assert_allclose(r, -1.5 * base + 0.25 * C0, rtol=1e-14, atol=1e-14)
+    Cnan = np.full((n, n), np.nan)
+    r0 = O.multiply(A, A, 8, 1e-3, alpha=1.0, beta=0.0, C=Cnan).C
+    np.testing.assert_array_equal(r0, base)   # beta = 0: C is not read
+
+
+@pytest.mark.parametrize("n,b,lam", [(128, 8, 0.85), (100, 16, 0.9), (96, 4, 0.7)])
+def test_error_bound(n, b, lam):
+    """||AB - C_tau||_F <= sum over culled leaf pairs of ||A_IK|| ||B_KJ||
+    (triangle inequality and Frobenius submultiplicativity), which is
+    < N_culled * tau."""
+    A = gen.exp_decay_nonsym(n, lam, seed=21)
+    B = gen.exp_decay_nonsym(n, lam, seed=22)
+    E = A.astype(np.float64) @ B.astype(np.float64)
+    na, nb2 = np.sqrt(_leaf_norm2(A, b)), np.sqrt(_leaf_norm2(B, b))
+    w = na.shape[0]
+    full = {(i, k, j) for i in range(w) for k in range(w) for j in range(w)
+            if na[i, k] > 0 and nb2[k, j] > 0}
+    for tau in [1e-6, 1e-4, 1e-2, 1e-1]:
+        r = O.multiply(A, B, b, tau)
+        kept = _as_set(r.triples)
+        culled = full - kept
+        bound = sum(na[i, k] * nb2[k, j] for (i, k, j) in culled)
+        err = np.linalg.norm(E - r.C)
+        assert err <= bound * (1 + 1e-12) + 1e-14
+        assert bound <= len(culled) * tau * (1 + 1e-12)
+        if not culled:
+            assert err <= 1e-13 * np.abs(E).max()
+
+
+def test_identity_special_case():
+    """A = I: C_IJ = B_IJ exactly when sqrt(#diagonal ones in leaf I) *
+    ||B_IJ|| >= tau, else 0."""
+    n, b = 72, 16          # ragged: the last leaf holds 8 ones
+    I = np.eye(n, dtype=np.float32)
+    B = gen.exp_decay_nonsym(n, 0.8, seed=5)
+    nbB = np.sqrt(_leaf_norm2(B, b))
+    w = nbB.shape[0]
+    for tau in [1e-6, 1e-3, 0.05, 0.5, 2.0]:
+        r = O.multiply(I, B, b, tau)
+        for bi in range(w):
+            ones = max(0, min(n, (bi + 1) * b) - bi * b)
+            for bj in range(w):
+                blk = r.C[bi*b:(bi+1)*b, bj*b:(bj+1)*b]
+                ref = B[bi*b:(bi+1)*b, bj*b:(bj+1)*b].astype(np.float64)
+                keep = ones > 0 and nbB[bi, bj] > 0 and math.sqrt(ones) * nbB[bi, bj] >= tau
+                np.testing.assert_array_equal(blk, ref if keep else 0 * ref)
+
+
+def test_block_diagonal_exact():
+    n, b = 64, 16
+    rng = np.random.default_rng(3)
+    A = np.zeros((n, n), dtype=np.float32)
+    B = np.zeros((n, n), dtype=np.float32)
+    for q in range(n // b):
+        s = slice(q * b, (q + 1) * b)
+        A[s, s] = rng.uniform(-1, 1, (b, b))
+        B[s, s] = rng.uniform(-1, 1, (b, b))
+    na, nb2 = np.sqrt(_leaf_norm2(A, b)), np.sqrt(_leaf_norm2(B, b))
+    tau = 0.99 * min(na[q, q] * nb2[q, q] for q in range(n // b))
+    r = O.multiply(A, B, b, tau)
+    E = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.abs(r.C - E).max() <= 1e-14
+    assert _as_set(r.triples) == {(q, q, q) for q in range(n // b)}
+
+
+def test_algebraic_pm1_counts_are_sign_free():
+    """|s_ij| = 1 makes every leaf norm independent of the signs, so the kept
+    set does not depend on the seed and equals that of the all-positive
+    magnitude matrix 1 / (|i-j|^2 + 1)."""
+    n, b = 256, 16
+    i = np.arange(n)
+    M = (1.0 / ((i[:, None] - i[None, :]) ** 2 + 1.0)).astype(np.float32)
+    d = O.depth(n, b)
+    pm = O.pyramid(M, b)
+    for tau in [1e-5, 1e-4, 1e-3]:
+        ref = _as_set(O.cull_recursive(pm, pm, d, tau)[0])
+        for seed in (0, 1):
+            A = gen.algebraic_decay(n, seed=seed)
+            pa = O.pyramid(A, b)
+            assert _as_set(O.cull_recursive(pa, pa, d, tau)[0]) == ref
+
+
+# ------------------------------------------------ Morton, Sec. III.E.1-2
+
+def test_morton_hand_values():
+    # l = sum_m i_m 2^(2m+1) + j_m 2^(2m)
+    assert O.morton(0, 0) == 0
+    assert O.morton(0, 1) == 1
+    assert O.morton(1, 0) == 2
+    assert O.morton(1, 1) == 3
+    assert O.morton(2, 1) == 0b1001
+    assert O.morton(3, 5) == 0b11011       # i bits 0,1 -> 1,3; j bits 0,2 -> 0,4
+    assert O.morton(0xFFFF, 0) == int("10" * 16, 2)
+
+
+def test_morton_tree_and_masks():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        i, k, j = (int(x) for x in rng.integers(0, 1 << 20, size=3))
+        l = O.morton(i, j)
+        assert O.morton_decode(l) == (i, j)
+        for a in range(2):
+            for c in range(2):   # a child appends two digits: parent * 4 + quadrant
+                assert O.morton(2 * i + a, 2 * j + c) == 4 * l + 2 * a + c
+        lA, lB = O.morton(i, k), O.morton(k, j)
+        assert O.k_key_A(lA) == O.k_key_B(lB)            # same k digits
+        assert O.convolve(lA, lB) == O.morton(i, j)      # Eq. (convolution)
+        k2 = int(rng.integers(0, 1 << 20))
+        if k2 != k:
+            assert O.k_key_A(lA) != O.k_key_B(O.morton(k2, j))
+
+
+# --------------------------------------------------- sampled blocks agree
+
+def test_blocks_match_full_oracle():
+    n, b = 200, 16
+    A = gen.water_like(8, 25, seed=2)
+    for tau in [0.0, 1e-3, 1e-1]:
+        r = O.multiply(A, A, b, tau)
+        ij = [(0, 0), (3, 7), (12, 12), (12, 0), (5, 9)]
+        acc, _ = O.blocks(A, A, b, tau, ij)
+        for q, (I, J) in enumerate(ij):
+            blk = r.C[I*b:min(n, (I+1)*b), J*b:min(n, (J+1)*b)]
+            np.testing.assert_allclose(acc[q][:blk.shape[0], :blk.shape[1]], blk,
+                                       rtol=1e-13, atol=1e-15)
