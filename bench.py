@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""SpAMM benchmark on the water-cluster-like density matrix (n = 7500).
+
+One step = one pass of the whole hot path over one input: the norm quadtree
+of A (stage 1), the level-by-level cull and grouping (stages 2-3) and the
+leaf products into C (stage 4) for C = A A at the tolerance tau* whose max
+error against the FP64 product matches cuBLAS SGEMM's ("equal max error"),
+found on a half-decade tau grid before timing.
+
+Prints ONE JSON line (rank 0).  ``value`` is kept leaf TFLOP/s (2 b^3 per
+surviving leaf triple) over the whole job; ``e2e`` is the same metric through
+the host-buffer entry point with the copies inside the timed region.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+Multi-GPU (torchrun): each rank multiplies its own replica (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import spamm_inputs as gen  # noqa: E402
+
+TAU_GRID = [1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10]
+WORKLOADS = {
+    "water7500": "water-cluster-like density matrix, 300 sites x 25 functions (n=7500), "
+                 "a_ij = g_ij exp(-0.5 r_ij), Hilbert order, b=16, A=B",
+    "exp1024": "exponential decay a_ij = u_ij 0.9^|i-j| (n=1024), b=16, A=B",
+    "alg16384": "algebraic decay a_ij = s_ij/(|i-j|^2+1) (n=16384), b=16, A=B",
+}
+TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense tensor-core ratio
+FP32_LANES_PER_SM = 128
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from an ncu capture, keyed by (kernel, workload, precision);
+# refreshed whenever that kernel changes.
+TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="spamm", choices=["spamm", "reference"])
+    p.add_argument("--workload", default="water7500", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "tf32", "bf16x3"])
+    p.add_argument("--leaf", type=int, default=16)
+    p.add_argument("--tau", default="auto")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def make_matrix(name):
+    if name == "water7500":
+        return gen.water_like(300, 25, 0.1, seed=0)
+    if name == "exp1024":
+        return gen.exp_decay(1024, 0.9, seed=0)
+    return gen.algebraic_decay(16384, seed=0)
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for row in csv.reader(f):
+                try:
+                    sm.append(float(row[1]))
+                    smax.append(float(row[2]))
+                except (ValueError, IndexError):
+                    continue
+                for k, name in enumerate(names):
+                    if len(row) > 5 + k and "Active" in row[5 + k] and "Not" not in row[5 + k]:
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def cpu_sample(A, b, tau, seconds, seed=0):
+    """The FP64 oracle on a random sample of C blocks, sized to ~seconds of
+    work on all host threads; returns (kept TFLOP/s, threads, description)."""
+    from oracle import oracle as O
+    n = A.shape[0]
+    nl = -(-n // b)
+    pa = O.pyramid(A, b)
+    threads = O.threads()
+    rng = np.random.default_rng(seed)
+    count = max(2 * threads, 8)
+    while True:
+        ij = rng.integers(0, nl, size=(count, 2))
+        t0 = time.perf_counter()
+        _, kept = O.blocks(A, A, b, tau, ij, pa, pa)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * seconds or count >= nl * nl:
+            break
+        count = min(nl * nl, int(count * max(2.0, 0.3 * seconds / max(dt, 1e-3))))
+    flops = 2.0 * b ** 3 * kept
+    desc = (f"FP64 oracle leaf products of {count} random C blocks (of {nl * nl}) at "
+            f"tau={tau:g}, {kept} kept leaf products, {dt:.1f} s")
+    return flops / dt / 1e12, threads, desc, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    A = make_matrix(args.workload)
+    b = args.leaf
+    tau = 1e-6 if args.tau == "auto" else float(args.tau)
+    budget = min(10.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    desc = ""
+    threads = 1
+    for s in range(args.warmup + args.steps):
+        v, threads, desc, _ = cpu_sample(A, b, tau, budget, seed=s)
+        if s >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "SpAMM leaf TFLOP/s (kept 2b^3 flops / time)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "tau": tau,
+                       "l2": "inputs larger than L2 not applicable (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def kernels_per_step(d):
+    return (1 + math.ceil(d / 5)) + (d + 2) + 4 + 1
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_1203_1692_gb300 as P
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    A_h = make_matrix(args.workload)
+    n = A_h.shape[0]
+    b = args.leaf
+    A = torch.from_numpy(A_h).to(dev)
+    stream = torch.cuda.current_stream()
+
+    # --- equal-error tau against cuBLAS SGEMM (not timed) ----------------
+    torch.backends.cuda.matmul.allow_tf32 = False
+    A64 = A.double()
+    C_exact = A64 @ A64
+    del A64
+    C_sgemm = A @ A
+    torch.cuda.synchronize()
+    err_sgemm = float((C_sgemm.double() - C_exact).abs().max())
+    scale = float(C_exact.abs().max())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        C_sgemm = A @ A
+    ev[0].record()
+    reps = 5
+    for _ in range(reps):
+        C_sgemm = A @ A
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_sgemm = ev[0].elapsed_time(ev[1]) / reps
+    del C_sgemm
+
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+    tree = ctx.build_norms(A)
+    C = torch.empty_like(A)
+    sweep = []
+    if args.tau == "auto":
+        tau = None
+        for t in TAU_GRID:
+            ctx.multiply(tree, tree, t, C=C)
+            err = float((C.double() - C_exact).abs().max())
+            st = ctx.stats()
+            sweep.append({"tau": t, "max_err": err, "kept": st["leaf_triples"],
+                          "ms": st["ms_total"]})
+            if err <= err_sgemm and tau is None:
+                tau = t
+        if tau is None:
+            tau = TAU_GRID[-1]
+    else:
+        tau = float(args.tau)
+    ctx.multiply(tree, tree, tau, C=C)
+    err_tau = float((C.double() - C_exact).abs().max())
+    del C_exact
+    torch.cuda.empty_cache()
+
+    # --- timed steps on resident inputs ----------------------------------
+    ctx.set_checked(False)
+
+    def step():
+        tree.rebuild(A)
+        ctx.multiply(tree, tree, tau, C=C)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    st0 = ctx.stats()
+    per = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    numeric_ms = []
+    e0.record(stream)
+    for k in range(args.steps):
+        per[k][0].record(stream)
+        step()
+        per[k][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    st = ctx.stats()     # also raises if a timed step failed
+    total_ms = e0.elapsed_time(e1)
+    lat = sorted(a.elapsed_time(c) for a, c in per)
+    # dominant kernel (leaf products): its own events, over separate launches
+    for _ in range(args.steps):
+        ctx.multiply(tree, tree, tau, C=C)
+        numeric_ms.append(ctx.stats()["ms_numeric"])
+    leaf_ms = statistics.mean(numeric_ms)
+    kept_flops = st["kept_flops"]
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = kept_flops * world / (ms_step * 1e-3) / 1e12
+
+    # --- end to end through the host entry point --------------------------
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A_h).pin_memory()
+        Ch = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        hctx = P.Context(leaf=b, precision=args.precision, checked=True)
+        for _ in range(2):
+            hctx.multiply_host(Ah, None, tau, C=Ch)
+        hctx.set_checked(False)
+        times = []
+        for _ in range(max(3, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hctx.multiply_host(Ah, None, tau, C=Ch)
+            times.append(time.perf_counter() - t0)
+        hs = hctx.stats()
+        e2e = {"value": hs["kept_flops"] * world / statistics.mean(times) / 1e12,
+               "unit": "TFLOP/s", "h2d_bytes_per_step": 4 * n * n,
+               "d2h_bytes_per_step": 4 * n * n,
+               "ms_per_step": 1e3 * statistics.mean(times)}
+        hctx.close()
+
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    if args.precision == "fp32":
+        mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "k_leaf_simt", "unit": "TFLOP/s",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz (median "
+                               "sampled SM clock)"}
+    else:
+        key = "bf16_tflops_sustained"
+        peak = peaks[key] * (TF32_OVER_BF16 if args.precision.startswith("tf32") else 1.0)
+        roof = {"bound": "tensor", "kernel": "k_leaf_tc", "unit": "TFLOP/s",
+                "peak_source": f"{key} of {peak_src} x "
+                               f"{'1.1/2.25 (tf32/bf16 nominal)' if args.precision.startswith('tf32') else '1'}"}
+    achieved = kept_flops / (leaf_ms * 1e-3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision)),
+                 "note": f"of {peak_src}; algorithmic flops = 2 b^3 x kept leaf triples"})
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, threads, desc, _ = cpu_sample(A_h, b, tau, args.cpu_seconds)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": "SpAMM leaf TFLOP/s (kept 2b^3 flops / step time) at equal max-err to SGEMM",
+        "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32"
+        else args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": n, "leaf": b, "tau": tau,
+                   "precision": args.precision,
+                   "l2": "inputs larger than L2 (A and C 4n^2 bytes each)",
+                   "parallelism": f"replicas x{world}"},
+        "speedup_vs_sgemm": t_sgemm / ms_step,
+        "sgemm_ms": t_sgemm, "effective_tflops": 2.0 * n ** 3 / (ms_step * 1e-3) / 1e12,
+        "max_err": err_tau, "sgemm_max_err": err_sgemm, "max_abs_C": scale,
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "kept_leaf_triples": st["leaf_triples"], "kept_fraction":
+            st["leaf_triples"] / float(-(-n // b)) ** 3,
+        "ms_symbolic": st0["ms_symbolic"], "ms_numeric": leaf_ms,
+        "tau_sweep": sweep, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": kernels_per_step(st["depth"]) * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * spamm.h -- C ABI of the GB300 SpAMM engine.
+ *
+ * SpAMM (Sparse Approximate Matrix Multiply, Bock & Challacombe) computes the
+ * SGEMM-shaped product C = alpha * A B + beta * C (Sec. II, problem
+ * statement) for matrices with decay, skipping every block product whose
+ * operand norms satisfy ||A_ik||_F ||B_kj||_F < tau (Eq. (norm_condition))
+ * at each tier of a quadtree of Frobenius norms (Eqs. (norm), (product)).
+ *
+ * The engine runs in four stages, each a CUDA kernel on one GPU:
+ *   1. spamm_build_norms: leaf squared norms (FP64) and the upper tiers of the
+ *      norm quadtree, plus, for tensor-core precisions, the matrix repacked
+ *      into tensor-core leaf tiles;
+ *   2. spamm_multiply: a level-by-level cull from the root that keeps a block
+ *      triple (I,K,J) iff nA2 * nB2 >= tau^2 with both norms non-zero;
+ *   3. grouping of the surviving leaf triples by 128 x 128 tile of C with
+ *      the kept (row-leaf, column-leaf) pairs of every K as a bit mask;
+ *   4. the dense leaf products accumulated into C in ascending K.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are square n x n, FP32, row-major with leading dimension
+ *     ld >= n (in elements).  Rectangular shapes are not supported.
+ *   - Matrix pointers are DEVICE pointers owned by the caller, except in
+ *     spamm_multiply_host, which takes HOST pointers.
+ *   - Calls are asynchronous and ordered on the context's stream unless the
+ *     comment says they synchronise.
+ *   - Errors are returned as spamm_status; no C++ exception crosses the ABI.
+ *     spamm_last_error(ctx) gives a message for the last failure on ctx.
+ *   - Not thread-safe: one host thread per context at a time.
+ */
+#ifndef SPAMM_H_
+#define SPAMM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPAMM_OK = 0,
+    SPAMM_ERR_INVALID_ARG = 1,  /* bad size, stride, pointer, tau or config */
+    SPAMM_ERR_NONFINITE = 2,    /* an operand holds Inf or NaN */
+    SPAMM_ERR_CAPACITY = 3,     /* the triple pool overflowed; C is not valid */
+    SPAMM_ERR_OOM = 4,          /* device or pinned allocation failed */
+    SPAMM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    SPAMM_ERR_UNSUPPORTED = 6,  /* valid request outside this build's scope */
+    SPAMM_ERR_CUDA = 7          /* a CUDA runtime call failed */
+} spamm_status;
+
+/* Arithmetic of the leaf products (stage 4). */
+typedef enum {
+    SPAMM_PREC_FP32 = 0,    /* FP32 FFMA on the CUDA cores, FP32 accumulate */
+    SPAMM_PREC_TF32X3 = 1,  /* tcgen05 kind::tf32, hi*hi + hi*lo + lo*hi, FP32 accumulate */
+    SPAMM_PREC_TF32 = 2,    /* tcgen05 kind::tf32, one pass, FP32 accumulate */
+    SPAMM_PREC_BF16X3 = 3   /* tcgen05 kind::f16 on bf16 hi/lo splits, FP32 accumulate */
+} spamm_precision;
+
+typedef struct {
+    int32_t leaf;          /* leaf block size b: 16, 32, 64 or 128 (tensor-core
+                              precisions: 16 or 32) */
+    int32_t precision;     /* spamm_precision */
+    double tie_rel;        /* relative half-width of the band around tau whose
+                              triples are counted in spamm_stats (default 1e-6) */
+    int64_t pool_bytes;    /* device pool for frontiers and triple lists;
+                              0 = 1 GiB, grown on demand in checked mode */
+    int32_t checked;       /* 1: spamm_multiply waits for completion, grows the
+                              pool and re-runs on overflow, and reports device
+                              errors in its return code; 0: fully asynchronous,
+                              check spamm_stats */
+    int32_t reserved[7];   /* must be zero */
+} spamm_config;
+
+/* Fill *cfg with the defaults: leaf 16, SPAMM_PREC_FP32, tie_rel 1e-6,
+ * pool_bytes 0, checked 1. */
+void spamm_config_default(spamm_config *cfg);
+
+typedef struct spamm_ctx spamm_ctx;
+typedef struct spamm_tree spamm_tree;
+
+#define SPAMM_MAX_TIERS 32
+
+typedef struct {
+    int32_t status;                    /* spamm_status of the last multiply */
+    int32_t depth;                     /* d of Eq. (depth) */
+    int64_t n;
+    int32_t leaf;
+    int32_t precision;
+    double tau;
+    int64_t tier_candidates[SPAMM_MAX_TIERS]; /* triples tested at tier t */
+    int64_t tier_kept[SPAMM_MAX_TIERS];       /* triples kept at tier t */
+    int64_t leaf_triples;              /* = tier_kept[depth] */
+    int64_t tie_band;                  /* tested triples with | ||A|| ||B|| - tau |
+                                          <= tie_rel * tau, over all tiers */
+    int64_t active_steps;              /* (C tile, K) pairs with >= 1 kept product */
+    int64_t tiles;                     /* 128 x 128 C tiles (incl. empty ones) */
+    double kept_flops;                 /* 2 b^3 per leaf triple */
+    double dense_flops;                /* 2 n^3 (Appendix A, square case) */
+    int64_t pool_bytes;                /* current pool size */
+    int64_t pool_needed_bytes;         /* bytes the last multiply needed */
+    float ms_symbolic;                 /* cull + grouping, CUDA events */
+    float ms_numeric;                  /* leaf products + C epilogue */
+    float ms_total;
+} spamm_stats_t;
+
+/* Create a context bound to the current CUDA device and to `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  cfg NULL = defaults.
+ * Allocates the pool and a small control block.  INVALID_ARG for a bad
+ * config, OOM, CUDA. */
+spamm_status spamm_create(spamm_ctx **ctx, void *stream, const spamm_config *cfg);
+
+/* Release the context and everything it owns (not the trees).  Synchronises
+ * the stream. */
+spamm_status spamm_destroy(spamm_ctx *ctx);
+
+/* Re-bind the context to another stream (a cudaStream_t). */
+spamm_status spamm_set_stream(spamm_ctx *ctx, void *stream);
+
+/* Switch checked mode (see spamm_config.checked) on or off. */
+spamm_status spamm_set_checked(spamm_ctx *ctx, int32_t checked);
+
+/* Grow the triple pool to at least pool_bytes (never shrinks).  Synchronises
+ * the stream when it reallocates.  OOM, INVALID_ARG (negative size). */
+spamm_status spamm_reserve(spamm_ctx *ctx, int64_t pool_bytes);
+
+/* Message for the last failure on ctx (never NULL; "" when none). */
+const char *spamm_last_error(const spamm_ctx *ctx);
+
+/* Stage 1, Sec. II.A-B.  Builds the norm quadtree of the n x n matrix A
+ * (device, row-major, leading dimension lda >= n): depth d from Eq. (depth)
+ * (the smallest d >= 0 with b 2^d >= n), the matrix zero-padded to
+ * n_p = b 2^d, leaf squared norms summed in FP64 from exact FP64 squares,
+ * and each upper node the sum of its four children.  For tensor-core
+ * precisions it also writes the leaf tiles in tensor-core layout.  *out is
+ * owned by the caller (spamm_tree_destroy).  The tree keeps the pointer A:
+ * the caller keeps A alive and unchanged until the last multiply that reads
+ * the tree has completed on the stream.  INVALID_ARG (n <= 0, lda < n, NULL
+ * pointers), UNSUPPORTED (more than 2^14 leaves per side), OOM, CUDA.
+ * Non-finite entries are detected by spamm_multiply (SPAMM_ERR_NONFINITE). */
+spamm_status spamm_build_norms(spamm_ctx *ctx, const float *A, int64_t n, int64_t lda,
+                               spamm_tree **out);
+
+/* Recompute an existing tree for new contents A (same n, same or larger
+ * lda is allowed), reusing its device storage.  Same errors as
+ * spamm_build_norms. */
+spamm_status spamm_tree_rebuild(spamm_ctx *ctx, spamm_tree *tree, const float *A,
+                                int64_t lda);
+
+/* Free a tree.  Synchronises its context's stream first. */
+spamm_status spamm_tree_destroy(spamm_tree *tree);
+
+/* Depth and node count of a tree (no synchronisation). */
+spamm_status spamm_tree_shape(const spamm_tree *tree, int32_t *depth, int64_t *nodes);
+
+/* Copy all squared norms of a tree to host memory (count >= nodes doubles;
+ * tier t row-major 2^t x 2^t at offset (4^t - 1) / 3).  Synchronises. */
+spamm_status spamm_tree_norms(spamm_ctx *ctx, const spamm_tree *tree, double *host_out,
+                              int64_t count);
+
+/* Stages 2-4, Eqs. (product) and (norm_condition), Algorithm 1:
+ * C = alpha * sum_{(I,K,J) kept} A_IK B_KJ + beta * C over the n x n device
+ * matrix C (row-major, ldc >= n).  A product is kept iff
+ * ||A_IK||^2 ||B_KJ||^2 >= tau^2 (FP64) with both norms non-zero, and so is
+ * every ancestor block product (the cull descends from the root).  Each C
+ * block accumulates its kept products in ascending K, so the result is
+ * deterministic.  When beta == 0, C is not read.  The two trees must have
+ * the same n and leaf size; they may be the same tree (A = B).  In checked
+ * mode the call waits for completion; otherwise status arrives through
+ * spamm_stats.  INVALID_ARG (tau < 0 or NaN, ldc < n, mismatched trees),
+ * NONFINITE, CAPACITY, TIMEOUT, OOM, CUDA. */
+spamm_status spamm_multiply(spamm_ctx *ctx, const spamm_tree *A, const spamm_tree *B,
+                            double tau, float alpha, float beta, float *C, int64_t ldc);
+
+/* End-to-end form with HOST matrices (row-major, ld = n): copies A and B
+ * (and C when beta != 0) to device buffers owned by ctx, builds both trees,
+ * multiplies and copies C back.  B may be NULL or equal to A for a square.
+ * Host buffers may be pageable or pinned (pinned is faster).  Synchronises. */
+spamm_status spamm_multiply_host(spamm_ctx *ctx, const float *A, const float *B, int64_t n,
+                                 double tau, float alpha, float beta, float *C);
+
+/* Statistics of the last multiply on ctx.  Synchronises the stream.  Returns
+ * the multiply's own status (e.g. CAPACITY) as well as writing *out. */
+spamm_status spamm_stats(spamm_ctx *ctx, spamm_stats_t *out);
+
+/* Copy the surviving leaf triples of the last multiply to host memory as
+ * int32 (I, K, J) rows, in no particular order; *count gets the number of
+ * triples (also when it exceeds cap, in which case only cap rows are
+ * written).  Synchronises. */
+spamm_status spamm_triples(spamm_ctx *ctx, int32_t *host_out, int64_t cap, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAMM_H_ */

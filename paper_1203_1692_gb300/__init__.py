@@ -1,0 +1,164 @@
+"""GB300-native SpAMM engine (Sparse Approximate Matrix Multiply, Bock &
+Challacombe).
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/spamm.h``); this package only marshals PyTorch CUDA tensors into
+that ABI.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (PRECISIONS, SpammError, spamm_build_norms, spamm_config_default,  # noqa: F401
+                   spamm_create, spamm_destroy, spamm_multiply, spamm_multiply_host,
+                   spamm_reserve, spamm_set_checked, spamm_set_stream, spamm_stats,
+                   spamm_tree_destroy, spamm_tree_norms, spamm_tree_rebuild, spamm_tree_shape,
+                   spamm_triples)
+
+__all__ = ["Context", "Tree", "SpammError", "PRECISIONS", "load"]
+
+
+def load():
+    """Load the engine library (raises if it has not been built)."""
+    return _abi.lib()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check_matrix(A):
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if A.dtype != torch.float32 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("expected a square float32 matrix")
+    if A.stride(1) != 1 or A.stride(0) < A.shape[0]:
+        raise ValueError("expected row-major storage with leading dimension >= n")
+    return A.shape[0], A.stride(0)
+
+
+class Tree:
+    """Norm quadtree of a matrix (holds a reference to the matrix)."""
+
+    def __init__(self, ctx: "Context", A):
+        n, lda = _check_matrix(A)
+        self.ctx = ctx
+        self.A = A
+        self.n = n
+        self.handle = spamm_build_norms(ctx.handle, A.data_ptr(), n, lda)
+        self.depth, self.nodes = spamm_tree_shape(self.handle)
+
+    def rebuild(self, A):
+        n, lda = _check_matrix(A)
+        if n != self.n:
+            raise ValueError("rebuild needs the same n")
+        self.A = A
+        spamm_tree_rebuild(self.ctx.handle, self.handle, A.data_ptr(), lda)
+
+    def norms(self) -> np.ndarray:
+        out = np.empty(self.nodes, dtype=np.float64)
+        spamm_tree_norms(self.ctx.handle, self.handle, out.ctypes.data, self.nodes)
+        return out
+
+    def close(self):
+        if self.handle:
+            spamm_tree_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A SpAMM context on the current CUDA device and stream."""
+
+    def __init__(self, leaf: int = 16, precision: str = "fp32", tie_rel: float = 1e-6,
+                 pool_bytes: int = 0, checked: bool = True, stream=None):
+        torch = _torch()
+        cfg = spamm_config_default()
+        cfg.leaf = leaf
+        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg.tie_rel = tie_rel
+        cfg.pool_bytes = pool_bytes
+        cfg.checked = 1 if checked else 0
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = spamm_create(self.stream.cuda_stream, cfg)
+        self.leaf = leaf
+        self.precision = precision
+
+    def build_norms(self, A) -> Tree:
+        return Tree(self, A)
+
+    def multiply(self, A: Tree, B: Tree, tau: float, alpha: float = 1.0, beta: float = 0.0,
+                 C=None):
+        torch = _torch()
+        if C is None:
+            C = torch.empty((A.n, A.n), dtype=torch.float32, device=A.A.device)
+        n, ldc = _check_matrix(C)
+        if n != A.n:
+            raise ValueError("C has the wrong size")
+        spamm_multiply(self.handle, A.handle, B.handle, tau, alpha, beta, C.data_ptr(), ldc)
+        return C
+
+    def multiply_host(self, A: np.ndarray, B, tau: float, alpha: float = 1.0,
+                      beta: float = 0.0, C=None) -> np.ndarray:
+        """End to end from host arrays (numpy float32, C-contiguous, or pinned
+        torch CPU tensors)."""
+        def ptr(x):
+            if hasattr(x, "data_ptr"):
+                return x.data_ptr()
+            return x.ctypes.data
+        n = A.shape[0]
+        if C is None:
+            C = np.zeros((n, n), dtype=np.float32)
+        spamm_multiply_host(self.handle, ptr(A), ptr(B) if B is not None else None, n, tau,
+                            alpha, beta, ptr(C))
+        return C
+
+    def set_checked(self, checked: bool):
+        spamm_set_checked(self.handle, checked)
+
+    def reserve(self, pool_bytes: int):
+        spamm_reserve(self.handle, pool_bytes)
+
+    def stats(self, raise_on_error: bool = True) -> dict:
+        s = spamm_stats(self.handle, raise_on_error)
+        d = s.depth
+        return {
+            "status": s.status, "depth": d, "n": s.n, "leaf": s.leaf,
+            "precision": s.precision, "tau": s.tau,
+            "tier_candidates": list(s.tier_candidates[:d + 1]),
+            "tier_kept": list(s.tier_kept[:d + 1]),
+            "leaf_triples": s.leaf_triples, "tie_band": s.tie_band,
+            "active_steps": s.active_steps, "tiles": s.tiles,
+            "kept_flops": s.kept_flops, "dense_flops": s.dense_flops,
+            "pool_bytes": s.pool_bytes, "pool_needed_bytes": s.pool_needed_bytes,
+            "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
+        }
+
+    def triples(self) -> np.ndarray:
+        count = ctypes.c_int64()
+        _abi.lib().spamm_triples(self.handle, None, 0, ctypes.byref(count))
+        out = np.empty((max(count.value, 1), 3), dtype=np.int32)
+        m = spamm_triples(self.handle, out.ctypes.data, count.value)
+        return out[:m]
+
+    def close(self):
+        if self.handle:
+            spamm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,192 @@
+"""ctypes binding of the C ABI in include/spamm.h.
+
+Argument marshalling only: every step of the SpAMM path runs in the CUDA
+kernels of ``libspamm_gb300.so``.  If the library has not been built the
+import fails loudly; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspamm_gb300.so")
+
+SPAMM_OK = 0
+SPAMM_ERR_INVALID_ARG = 1
+SPAMM_ERR_NONFINITE = 2
+SPAMM_ERR_CAPACITY = 3
+SPAMM_ERR_OOM = 4
+SPAMM_ERR_TIMEOUT = 5
+SPAMM_ERR_UNSUPPORTED = 6
+SPAMM_ERR_CUDA = 7
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "CAPACITY", 4: "OOM",
+                5: "TIMEOUT", 6: "UNSUPPORTED", 7: "CUDA"}
+
+SPAMM_PREC_FP32 = 0
+SPAMM_PREC_TF32X3 = 1
+SPAMM_PREC_TF32 = 2
+SPAMM_PREC_BF16X3 = 3
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "tf32": 2, "bf16x3": 3}
+
+SPAMM_MAX_TIERS = 32
+
+
+class spamm_config(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tie_rel", ctypes.c_double), ("pool_bytes", ctypes.c_int64),
+                ("checked", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class spamm_stats_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("depth", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("leaf", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tau", ctypes.c_double),
+                ("tier_candidates", ctypes.c_int64 * SPAMM_MAX_TIERS),
+                ("tier_kept", ctypes.c_int64 * SPAMM_MAX_TIERS),
+                ("leaf_triples", ctypes.c_int64), ("tie_band", ctypes.c_int64),
+                ("active_steps", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("kept_flops", ctypes.c_double), ("dense_flops", ctypes.c_double),
+                ("pool_bytes", ctypes.c_int64), ("pool_needed_bytes", ctypes.c_int64),
+                ("ms_symbolic", ctypes.c_float), ("ms_numeric", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_flt = ctypes.c_float
+
+# name -> (restype, argtypes); every symbol include/spamm.h declares
+SIGNATURES = {
+    "spamm_config_default": (None, [ctypes.POINTER(spamm_config)]),
+    "spamm_create": (_i32, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(spamm_config)]),
+    "spamm_destroy": (_i32, [_vp]),
+    "spamm_set_stream": (_i32, [_vp, _vp]),
+    "spamm_set_checked": (_i32, [_vp, _i32]),
+    "spamm_reserve": (_i32, [_vp, _i64]),
+    "spamm_last_error": (ctypes.c_char_p, [_vp]),
+    "spamm_build_norms": (_i32, [_vp, _vp, _i64, _i64, ctypes.POINTER(_vp)]),
+    "spamm_tree_rebuild": (_i32, [_vp, _vp, _vp, _i64]),
+    "spamm_tree_destroy": (_i32, [_vp]),
+    "spamm_tree_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "spamm_tree_norms": (_i32, [_vp, _vp, _vp, _i64]),
+    "spamm_multiply": (_i32, [_vp, _vp, _vp, _dbl, _flt, _flt, _vp, _i64]),
+    "spamm_multiply_host": (_i32, [_vp, _vp, _vp, _i64, _dbl, _flt, _flt, _vp]),
+    "spamm_stats": (_i32, [_vp, ctypes.POINTER(spamm_stats_t)]),
+    "spamm_triples": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded engine library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1203_1692_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SpammError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, ctx=None) -> None:
+    if status != SPAMM_OK:
+        msg = lib().spamm_last_error(ctx).decode() if ctx else ""
+        raise SpammError(status, msg)
+
+
+# Thin same-name wrappers -------------------------------------------------
+
+def spamm_config_default() -> spamm_config:
+    c = spamm_config()
+    lib().spamm_config_default(ctypes.byref(c))
+    return c
+
+
+def spamm_create(stream: int, cfg: spamm_config):
+    h = _vp()
+    check(lib().spamm_create(ctypes.byref(h), _vp(stream), ctypes.byref(cfg)))
+    return h
+
+
+def spamm_destroy(ctx) -> None:
+    check(lib().spamm_destroy(ctx))
+
+
+def spamm_set_stream(ctx, stream: int) -> None:
+    check(lib().spamm_set_stream(ctx, _vp(stream)), ctx)
+
+
+def spamm_set_checked(ctx, checked: bool) -> None:
+    check(lib().spamm_set_checked(ctx, 1 if checked else 0), ctx)
+
+
+def spamm_reserve(ctx, pool_bytes: int) -> None:
+    check(lib().spamm_reserve(ctx, int(pool_bytes)), ctx)
+
+
+def spamm_build_norms(ctx, A_ptr: int, n: int, lda: int):
+    h = _vp()
+    check(lib().spamm_build_norms(ctx, _vp(A_ptr), n, lda, ctypes.byref(h)), ctx)
+    return h
+
+
+def spamm_tree_rebuild(ctx, tree, A_ptr: int, lda: int) -> None:
+    check(lib().spamm_tree_rebuild(ctx, tree, _vp(A_ptr), lda), ctx)
+
+
+def spamm_tree_destroy(tree) -> None:
+    check(lib().spamm_tree_destroy(tree))
+
+
+def spamm_tree_shape(tree):
+    d = _i32()
+    m = _i64()
+    check(lib().spamm_tree_shape(tree, ctypes.byref(d), ctypes.byref(m)))
+    return d.value, m.value
+
+
+def spamm_tree_norms(ctx, tree, out_ptr: int, count: int) -> None:
+    check(lib().spamm_tree_norms(ctx, tree, _vp(out_ptr), count), ctx)
+
+
+def spamm_multiply(ctx, A_tree, B_tree, tau: float, alpha: float, beta: float, C_ptr: int,
+                   ldc: int) -> int:
+    st = lib().spamm_multiply(ctx, A_tree, B_tree, float(tau), float(alpha), float(beta),
+                              _vp(C_ptr), ldc)
+    check(st, ctx)
+    return st
+
+
+def spamm_multiply_host(ctx, A_ptr: int, B_ptr, n: int, tau: float, alpha: float,
+                        beta: float, C_ptr: int) -> None:
+    check(lib().spamm_multiply_host(ctx, _vp(A_ptr), _vp(B_ptr) if B_ptr else None, n,
+                                    float(tau), float(alpha), float(beta), _vp(C_ptr)), ctx)
+
+
+def spamm_stats(ctx, raise_on_error: bool = True) -> spamm_stats_t:
+    s = spamm_stats_t()
+    st = lib().spamm_stats(ctx, ctypes.byref(s))
+    if raise_on_error:
+        check(st, ctx)
+    return s
+
+
+def spamm_triples(ctx, out_ptr: int, cap: int) -> int:
+    cnt = _i64()
+    check(lib().spamm_triples(ctx, _vp(out_ptr), cap, ctypes.byref(cnt)), ctx)
+    return cnt.value

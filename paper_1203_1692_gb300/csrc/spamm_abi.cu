@@ -1,0 +1,477 @@
+// Host side of the C ABI declared in include/spamm.h: argument checks,
+// device memory owned by contexts and trees, and the stream-ordered launch
+// sequence of a multiply.  All arithmetic runs in the kernels of norms.cu,
+// cull.cu, leaf_simt.cu and leaf_tc.cu.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "spamm_internal.cuh"
+
+using namespace spamm;
+
+namespace spamm {
+
+spamm_status set_err(spamm_ctx* ctx, spamm_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+spamm_status cuda_err(spamm_ctx* ctx, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SPAMM_OK;
+    cudaGetLastError();  // clear a sticky launch error
+    const spamm_status st = (e == cudaErrorMemoryAllocation) ? SPAMM_ERR_OOM : SPAMM_ERR_CUDA;
+    return set_err(ctx, st, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int tiles_per_side(const spamm_tree* t) {
+    return (int)(t->nlp / (kTileRows / t->b));
+}
+
+}  // namespace spamm
+
+namespace {
+
+bool valid_leaf(int b) { return b == 16 || b == 32 || b == 64 || b == 128; }
+
+int depth_for(int64_t n, int b) {
+    int d = 0;
+    while ((int64_t)b * ((int64_t)1 << d) < n) ++d;
+    return d;
+}
+
+spamm_status alloc_pool(spamm_ctx* ctx, int64_t bytes) {
+    if (ctx->pool) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->pool);
+        ctx->pool = nullptr;
+        ctx->pool_words = 0;
+    }
+    bytes = std::max<int64_t>(bytes, 1 << 20);
+    bytes = (bytes + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&ctx->pool, (size_t)bytes);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "pool allocation");
+    ctx->pool_words = bytes / 8;
+    return SPAMM_OK;
+}
+
+spamm_status ensure_tiles(spamm_ctx* ctx, int64_t tiles) {
+    if (tiles <= ctx->tiles_cap) return SPAMM_OK;
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->tile_cnt);
+    cudaFree(ctx->tile_fill);
+    cudaFree(ctx->tile_off);
+    cudaFree(ctx->tile_steps);
+    ctx->tile_cnt = ctx->tile_fill = ctx->tile_off = ctx->tile_steps = nullptr;
+    ctx->tiles_cap = 0;
+    const int64_t cap = std::max<int64_t>(tiles, 1024);
+    cudaError_t e = cudaMalloc(&ctx->tile_cnt, sizeof(uint32_t) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_fill, sizeof(uint32_t) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_off, sizeof(uint32_t) * (cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_steps, sizeof(uint32_t) * cap);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "tile arrays");
+    ctx->tiles_cap = cap;
+    return SPAMM_OK;
+}
+
+void free_tree_storage(spamm_tree* t) {
+    cudaFree(t->pyr);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(t->packA[i]);
+        cudaFree(t->packB[i]);
+        t->packA[i] = t->packB[i] = nullptr;
+    }
+    t->pyr = nullptr;
+}
+
+spamm_status check_matrix(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda) {
+    if (!A) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "matrix pointer is NULL");
+    if (n <= 0) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "n must be positive");
+    if (lda < n) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "leading dimension below n");
+    return SPAMM_OK;
+}
+
+int64_t words_needed(const DevCtl& c, int d) {
+    unsigned long long s = 0;
+    for (int t = 0; t <= d; ++t) s += c.tier_count[t];
+    const unsigned long long m = c.tier_count[d];
+    return (int64_t)(s + 2 * ((m + 1) / 2) + m);
+}
+
+}  // namespace
+
+extern "C" {
+
+void spamm_config_default(spamm_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->leaf = 16;
+    cfg->precision = SPAMM_PREC_FP32;
+    cfg->tie_rel = 1e-6;
+    cfg->pool_bytes = 0;
+    cfg->checked = 1;
+}
+
+spamm_status spamm_create(spamm_ctx** out, void* stream, const spamm_config* cfg) {
+    if (!out) return SPAMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    spamm_config c;
+    if (cfg) c = *cfg; else spamm_config_default(&c);
+    if (!valid_leaf(c.leaf)) return SPAMM_ERR_INVALID_ARG;
+    if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_BF16X3) return SPAMM_ERR_INVALID_ARG;
+    if (precision_uses_tc(c.precision) && !(c.leaf == 16 || c.leaf == 32))
+        return SPAMM_ERR_UNSUPPORTED;
+    if (!(c.tie_rel >= 0.0 && c.tie_rel < 0.5) || c.pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
+    for (int i = 0; i < 7; ++i)
+        if (c.reserved[i]) return SPAMM_ERR_INVALID_ARG;
+    spamm_ctx* ctx = new (std::nothrow) spamm_ctx();
+    if (!ctx) return SPAMM_ERR_OOM;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->cfg = c;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ctl, sizeof(DevCtl));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->ctl_host, sizeof(DevCtl));
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+    if (e != cudaSuccess) {
+        spamm_status st = (e == cudaErrorMemoryAllocation) ? SPAMM_ERR_OOM : SPAMM_ERR_CUDA;
+        cudaGetLastError();
+        spamm_destroy(ctx);
+        return st;
+    }
+    memset(ctx->ctl_host, 0, sizeof(DevCtl));
+    spamm_status st = alloc_pool(ctx, c.pool_bytes ? c.pool_bytes : ((int64_t)1 << 30));
+    if (st == SPAMM_OK) st = ensure_tiles(ctx, 1024);
+    if (st != SPAMM_OK) {
+        spamm_destroy(ctx);
+        return st;
+    }
+    ctx->last_status = SPAMM_OK;
+    *out = ctx;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_destroy(spamm_ctx* ctx) {
+    if (!ctx) return SPAMM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->hostTreeA) spamm_tree_destroy(ctx->hostTreeA);
+    if (ctx->hostTreeB) spamm_tree_destroy(ctx->hostTreeB);
+    cudaFree(ctx->pool);
+    cudaFree(ctx->ctl);
+    if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+    cudaFree(ctx->tile_cnt);
+    cudaFree(ctx->tile_fill);
+    cudaFree(ctx->tile_off);
+    cudaFree(ctx->tile_steps);
+    cudaFree(ctx->dA);
+    cudaFree(ctx->dB);
+    cudaFree(ctx->dC);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    cudaGetLastError();
+    delete ctx;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_set_stream(spamm_ctx* ctx, void* stream) {
+    if (!ctx) return SPAMM_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_set_checked(spamm_ctx* ctx, int32_t checked) {
+    if (!ctx) return SPAMM_ERR_INVALID_ARG;
+    ctx->cfg.checked = checked ? 1 : 0;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_reserve(spamm_ctx* ctx, int64_t pool_bytes) {
+    if (!ctx || pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
+    if (pool_bytes <= ctx->pool_words * 8) return SPAMM_OK;
+    return alloc_pool(ctx, pool_bytes);
+}
+
+const char* spamm_last_error(const spamm_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+static spamm_status build_into(spamm_ctx* ctx, spamm_tree* t) {
+    cudaError_t e = launch_build_norms(t, ctx->stream);
+    return cuda_err(ctx, e, "norm build launch");
+}
+
+spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda,
+                               spamm_tree** out) {
+    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    spamm_status st = check_matrix(ctx, A, n, lda);
+    if (st != SPAMM_OK) return st;
+    const int b = ctx->cfg.leaf;
+    const int d = depth_for(n, b);
+    const int64_t nl = (n + b - 1) / b;
+    if (nl > kMaxLeavesPerSide || d >= SPAMM_MAX_TIERS - 1)
+        return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "more than 2^14 leaves per side");
+    const int tl = kTileRows / b;
+    spamm_tree* t = new (std::nothrow) spamm_tree();
+    if (!t) return SPAMM_ERR_OOM;
+    t->ctx = ctx;
+    t->A = A;
+    t->n = n;
+    t->lda = lda;
+    t->b = b;
+    t->d = d;
+    t->nb = (int64_t)1 << d;
+    t->nl = nl;
+    t->nlp = (nl + tl - 1) / tl * tl;
+    t->nodes = (((int64_t)1 << (2 * (d + 1))) - 1) / 3;
+    t->precision = ctx->cfg.precision;
+    cudaError_t e = cudaMalloc(&t->pyr, sizeof(double) * t->nodes);
+    if (e == cudaSuccess && precision_uses_tc(t->precision)) {
+        t->pack_bytes = pack_bytes_for(t->precision, t->nlp, b);
+        const int arrays = pack_arrays_for(t->precision);
+        for (int i = 0; i < arrays && e == cudaSuccess; ++i) {
+            e = cudaMalloc(&t->packA[i], t->pack_bytes);
+            if (e == cudaSuccess) e = cudaMalloc(&t->packB[i], t->pack_bytes);
+            if (e == cudaSuccess) e = cudaMemsetAsync(t->packA[i], 0, t->pack_bytes, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(t->packB[i], 0, t->pack_bytes, ctx->stream);
+        }
+    }
+    if (e != cudaSuccess) {
+        st = cuda_err(ctx, e, "tree allocation");
+        free_tree_storage(t);
+        delete t;
+        return st;
+    }
+    st = build_into(ctx, t);
+    if (st != SPAMM_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        free_tree_storage(t);
+        delete t;
+        return st;
+    }
+    *out = t;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_tree_rebuild(spamm_ctx* ctx, spamm_tree* t, const float* A, int64_t lda) {
+    if (!ctx || !t) return SPAMM_ERR_INVALID_ARG;
+    spamm_status st = check_matrix(ctx, A, t->n, lda);
+    if (st != SPAMM_OK) return st;
+    if (t->precision != ctx->cfg.precision || t->b != ctx->cfg.leaf)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tree built under another configuration");
+    t->A = A;
+    t->lda = lda;
+    return build_into(ctx, t);
+}
+
+spamm_status spamm_tree_destroy(spamm_tree* t) {
+    if (!t) return SPAMM_ERR_INVALID_ARG;
+    if (t->ctx) cudaStreamSynchronize(t->ctx->stream);
+    free_tree_storage(t);
+    delete t;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_tree_shape(const spamm_tree* t, int32_t* depth, int64_t* nodes) {
+    if (!t) return SPAMM_ERR_INVALID_ARG;
+    if (depth) *depth = t->d;
+    if (nodes) *nodes = t->nodes;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_tree_norms(spamm_ctx* ctx, const spamm_tree* t, double* host_out,
+                              int64_t count) {
+    if (!ctx || !t || !host_out || count < t->nodes) return SPAMM_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(host_out, t->pyr, sizeof(double) * t->nodes,
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return cuda_err(ctx, e, "norm copy");
+}
+
+static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
+                                         const spamm_tree* B, double tau, float alpha,
+                                         float beta, float* C, int64_t ldc) {
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
+    if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau);
+    if (e == cudaSuccess) e = launch_group(ctx, A);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
+    if (e == cudaSuccess) {
+        if (ctx->cfg.precision == SPAMM_PREC_FP32)
+            e = launch_leaf_simt(ctx, A, B, alpha, beta, C, ldc);
+        else
+            e = launch_leaf_tc(ctx, A, B, alpha, beta, C, ldc);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2], s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s);
+    ctx->timed = (e == cudaSuccess);
+    return cuda_err(ctx, e, "multiply launch");
+}
+
+static spamm_status status_from_ctl(spamm_ctx* ctx, const DevCtl& c) {
+    if (c.status & ST_NONFINITE)
+        return set_err(ctx, SPAMM_ERR_NONFINITE, "an operand holds Inf or NaN");
+    if (c.status & ST_TIMEOUT)
+        return set_err(ctx, SPAMM_ERR_TIMEOUT, "a device-side wait timed out");
+    if (c.status & ST_OVERFLOW)
+        return set_err(ctx, SPAMM_ERR_CAPACITY, "triple pool overflow");
+    return SPAMM_OK;
+}
+
+spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                            double tau, float alpha, float beta, float* C, int64_t ldc) {
+    if (!ctx || !A || !B || !C) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL argument");
+    if (!(tau >= 0.0) || !std::isfinite(tau))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tau must be finite and >= 0");
+    if (A->n != B->n || A->b != B->b || A->precision != B->precision)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "trees differ in n, leaf or precision");
+    if (A->precision != ctx->cfg.precision || A->b != ctx->cfg.leaf)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "trees built under another configuration");
+    if (ldc < A->n) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "ldc below n");
+    const int64_t tps = tiles_per_side(A);
+    spamm_status st = ensure_tiles(ctx, tps * tps);
+    if (st != SPAMM_OK) return st;
+    ctx->last_d = A->d;
+    ctx->last_b = A->b;
+    ctx->last_n = A->n;
+    ctx->last_prec = A->precision;
+    ctx->last_tau = tau;
+    ctx->last_tiles = tps * tps;
+    ctx->last_status = SPAMM_OK;
+    for (int attempt = 0;; ++attempt) {
+        st = launch_multiply_once(ctx, A, B, tau, alpha, beta, C, ldc);
+        if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
+        if (!ctx->cfg.checked) return SPAMM_OK;
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return (spamm_status)(ctx->last_status = cuda_err(ctx, e, "multiply"));
+        const DevCtl& c = *ctx->ctl_host;
+        if ((c.status & ST_OVERFLOW) && !(c.status & (ST_NONFINITE | ST_TIMEOUT)) && attempt < 8) {
+            const int64_t need = std::max<int64_t>(words_needed(c, A->d), 2 * ctx->pool_words);
+            st = alloc_pool(ctx, need * 8 + need * 2);  // 25% headroom
+            if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
+            continue;
+        }
+        return (spamm_status)(ctx->last_status = status_from_ctl(ctx, c));
+    }
+}
+
+spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
+    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "stats");
+    memset(out, 0, sizeof(*out));
+    const DevCtl& c = *ctx->ctl_host;
+    const int d = ctx->last_d;
+    out->depth = d;
+    out->n = ctx->last_n;
+    out->leaf = ctx->last_b;
+    out->precision = ctx->last_prec;
+    out->tau = ctx->last_tau;
+    for (int t = 0; t <= d && t < SPAMM_MAX_TIERS; ++t) {
+        out->tier_candidates[t] = (int64_t)c.tier_cand[t];
+        out->tier_kept[t] = (int64_t)c.tier_count[t];
+    }
+    out->leaf_triples = (int64_t)c.tier_count[d];
+    out->tie_band = (int64_t)c.tie_band;
+    out->active_steps = (int64_t)c.active_steps;
+    out->tiles = ctx->last_tiles;
+    const double b = ctx->last_b;
+    out->kept_flops = 2.0 * b * b * b * (double)out->leaf_triples;
+    out->dense_flops = 2.0 * (double)ctx->last_n * (double)ctx->last_n * (double)ctx->last_n;
+    out->pool_bytes = ctx->pool_words * 8;
+    out->pool_needed_bytes = words_needed(c, d) * 8;
+    if (ctx->timed) {
+        cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&out->ms_numeric, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&out->ms_total, ctx->ev[0], ctx->ev[2]);
+    }
+    spamm_status st = status_from_ctl(ctx, c);
+    if (ctx->last_status != SPAMM_OK && st == SPAMM_OK) st = (spamm_status)ctx->last_status;
+    out->status = st;
+    return st;
+}
+
+spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64_t* count) {
+    if (!ctx || !count || cap < 0 || (cap > 0 && !host_out)) return SPAMM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "triples");
+    const DevCtl& c = *ctx->ctl_host;
+    const int d = ctx->last_d;
+    const int64_t m = (int64_t)c.tier_count[d];
+    *count = m;
+    if (c.status & ST_OVERFLOW) return set_err(ctx, SPAMM_ERR_CAPACITY, "triple pool overflow");
+    const int64_t k = std::min(m, cap);
+    if (k <= 0) return SPAMM_OK;
+    std::vector<uint64_t> buf((size_t)k);
+    e = cudaMemcpy(buf.data(), ctx->pool + c.tier_off[d], sizeof(uint64_t) * k,
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "triples copy");
+    for (int64_t i = 0; i < k; ++i) {
+        host_out[3 * i + 0] = (int32_t)tri_I(buf[i]);
+        host_out[3 * i + 1] = (int32_t)tri_K(buf[i]);
+        host_out[3 * i + 2] = (int32_t)tri_J(buf[i]);
+    }
+    return SPAMM_OK;
+}
+
+spamm_status spamm_multiply_host(spamm_ctx* ctx, const float* A, const float* B, int64_t n,
+                                 double tau, float alpha, float beta, float* C) {
+    if (!ctx || !A || !C || n <= 0) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "bad argument");
+    const bool square = (B == nullptr || B == A);
+    const int64_t elems = n * n;
+    if (elems > ctx->stage_elems) {
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->hostTreeA) spamm_tree_destroy(ctx->hostTreeA);
+        if (ctx->hostTreeB) spamm_tree_destroy(ctx->hostTreeB);
+        ctx->hostTreeA = ctx->hostTreeB = nullptr;
+        cudaFree(ctx->dA);
+        cudaFree(ctx->dB);
+        cudaFree(ctx->dC);
+        ctx->dA = ctx->dB = ctx->dC = nullptr;
+        ctx->stage_elems = 0;
+        cudaError_t e = cudaMalloc(&ctx->dA, sizeof(float) * elems);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->dB, sizeof(float) * elems);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->dC, sizeof(float) * elems);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "staging allocation");
+        ctx->stage_elems = elems;
+    }
+    cudaStream_t s = ctx->stream;
+    const size_t bytes = sizeof(float) * elems;
+    cudaError_t e = cudaMemcpyAsync(ctx->dA, A, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !square) e = cudaMemcpyAsync(ctx->dB, B, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && beta != 0.f) e = cudaMemcpyAsync(ctx->dC, C, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "host to device copy");
+    spamm_status st;
+    auto tree_for = [&](spamm_tree** slot, const float* dev) -> spamm_status {
+        if (*slot && ((*slot)->n != n || (*slot)->precision != ctx->cfg.precision ||
+                      (*slot)->b != ctx->cfg.leaf)) {
+            spamm_tree_destroy(*slot);
+            *slot = nullptr;
+        }
+        if (*slot) return spamm_tree_rebuild(ctx, *slot, dev, n);
+        return spamm_build_norms(ctx, dev, n, n, slot);
+    };
+    st = tree_for(&ctx->hostTreeA, ctx->dA);
+    if (st != SPAMM_OK) return st;
+    const spamm_tree* tb = ctx->hostTreeA;
+    if (!square) {
+        st = tree_for(&ctx->hostTreeB, ctx->dB);
+        if (st != SPAMM_OK) return st;
+        tb = ctx->hostTreeB;
+    }
+    st = spamm_multiply(ctx, ctx->hostTreeA, tb, tau, alpha, beta, ctx->dC, n);
+    if (st != SPAMM_OK) return st;
+    e = cudaMemcpyAsync(C, ctx->dC, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "device to host copy");
+    return status_from_ctl(ctx, *ctx->ctl_host);
+}
+
+}  // extern "C"

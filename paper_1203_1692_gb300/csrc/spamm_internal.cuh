@@ -1,0 +1,139 @@
+// Internal declarations shared by the CUDA translation units of the engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/spamm.h"
+
+namespace spamm {
+
+// Triples (I, K, J) at tier t are packed into 64 bits, 21 bits per index.
+constexpr int kIdxBits = 21;
+constexpr uint64_t kIdxMask = (1ull << kIdxBits) - 1;
+__host__ __device__ inline uint64_t pack_triple(uint64_t I, uint64_t K, uint64_t J) {
+    return (I << (2 * kIdxBits)) | (K << kIdxBits) | J;
+}
+__host__ __device__ inline uint32_t tri_I(uint64_t p) { return (uint32_t)(p >> (2 * kIdxBits)); }
+__host__ __device__ inline uint32_t tri_K(uint64_t p) { return (uint32_t)((p >> kIdxBits) & kIdxMask); }
+__host__ __device__ inline uint32_t tri_J(uint64_t p) { return (uint32_t)(p & kIdxMask); }
+
+// A C tile is 128 x 128: TL = 128 / b leaves per side.  Each grouped
+// (tile, K) step carries a 64-bit mask, bit (y * 8 + x) = "product of row
+// leaf x and column leaf y of the tile is kept" (only TL x TL bits are used).
+constexpr int kTileRows = 128;
+constexpr int kMaxLeavesPerSide = 1 << 14;
+
+// Device status bits.
+constexpr uint32_t ST_OVERFLOW = 1u;
+constexpr uint32_t ST_NONFINITE = 2u;
+constexpr uint32_t ST_TIMEOUT = 4u;
+
+// Control block in device memory, zeroed before every multiply.  All pool
+// offsets are in 8-byte words.
+struct DevCtl {
+    unsigned long long tier_count[SPAMM_MAX_TIERS];  // true kept count per tier
+    unsigned long long tier_cand[SPAMM_MAX_TIERS];
+    unsigned long long tier_off[SPAMM_MAX_TIERS + 1];
+    unsigned long long tie_band;
+    unsigned long long active_steps;
+    unsigned long long ent_off;     // u32 entries (one per leaf triple)
+    unsigned long long pk_off;      // u32 K of each (tile, K) step
+    unsigned long long pm_off;      // u64 mask of each (tile, K) step
+    unsigned long long need_words;  // words the whole multiply needs
+    unsigned int status;
+    unsigned int pad;
+};
+
+// Words stored for tier t (a frontier that overflowed is truncated).
+__device__ inline unsigned long long stored_count(const DevCtl* c, int t, unsigned long long cap) {
+    unsigned long long off = c->tier_off[t];
+    if (off >= cap) return 0;
+    unsigned long long room = cap - off;
+    unsigned long long n = c->tier_count[t];
+    return n < room ? n : room;
+}
+
+struct Tree;
+
+}  // namespace spamm
+
+struct spamm_tree {
+    spamm_ctx* ctx;
+    const float* A;
+    int64_t n, lda;
+    int b, d;
+    int64_t nb;        // 2^d leaves per side (padded grid)
+    int64_t nl;        // ceil(n / b) leaves holding data
+    int64_t nlp;       // nl rounded up to a whole number of tiles (TL leaves)
+    double* pyr;       // squared norms, all tiers
+    int64_t nodes;
+    int precision;
+    // Tensor-core operand tiles, see norms.cu for the layout.  A-role tiles
+    // hold leaf (I,K) rows = i; B-role tiles hold leaf (K,J) transposed.
+    void* packA[2];    // hi, lo (lo only for split precisions)
+    void* packB[2];
+    size_t pack_bytes;  // bytes of one pack array
+};
+
+struct spamm_ctx {
+    cudaStream_t stream;
+    spamm_config cfg;
+    int device;
+    int sm_count;
+    // triple pool
+    uint64_t* pool;
+    int64_t pool_words;
+    // control block (device) and its pinned mirror
+    spamm::DevCtl* ctl;
+    spamm::DevCtl* ctl_host;
+    // per-tile arrays
+    uint32_t* tile_cnt;   // entries per tile, then fill cursors
+    uint32_t* tile_fill;
+    uint32_t* tile_off;   // exclusive scan, tiles + 1
+    uint32_t* tile_steps; // (tile, K) steps per tile
+    uint32_t* work_ctr;   // persistent-kernel work counter
+    int64_t tiles_cap;
+    // timing
+    cudaEvent_t ev[4];
+    bool timed;
+    // last multiply
+    int last_d, last_b, last_prec;
+    int64_t last_n, last_tiles;
+    double last_tau;
+    int last_status;
+    // host staging for spamm_multiply_host
+    float* dA; float* dB; float* dC;
+    int64_t stage_elems;
+    spamm_tree* hostTreeA;
+    spamm_tree* hostTreeB;
+    std::string err;
+};
+
+namespace spamm {
+
+spamm_status set_err(spamm_ctx* ctx, spamm_status st, const std::string& msg);
+spamm_status cuda_err(spamm_ctx* ctx, cudaError_t e, const char* what);
+
+int tiles_per_side(const spamm_tree* t);  // nlp / TL
+
+// norms.cu
+cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s);
+bool precision_uses_tc(int precision);
+size_t pack_bytes_for(int precision, int64_t nlp, int b);
+int pack_arrays_for(int precision);  // 1 or 2 per role
+
+// cull.cu
+cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau);
+cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A);
+
+// leaf_simt.cu
+cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                             float alpha, float beta, float* C, int64_t ldc);
+// leaf_tc.cu
+cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                           float alpha, float beta, float* C, int64_t ldc);
+
+}  // namespace spamm

@@ -1,0 +1,85 @@
+"""CPU-only checks of the boundary: the library builds for sm_103a, loads,
+and exports every function include/spamm.h declares; the Python binding
+covers the same names.  No compute calls (there is no GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spamm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(spamm_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1203_1692_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for need in ("spamm_create", "spamm_build_norms", "spamm_multiply", "spamm_stats",
+                 "spamm_destroy", "spamm_tree_destroy", "spamm_last_error"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (spamm_\w+)", out))
+    assert exported == set(declared_functions())
+
+
+def test_binding_covers_the_abi(libpath):
+    from paper_1203_1692_gb300 import _abi
+    assert set(_abi.SIGNATURES) == set(declared_functions())
+    _abi.lib()
+
+
+def test_config_default_through_the_abi(libpath):
+    from paper_1203_1692_gb300 import _abi
+    c = _abi.spamm_config_default()
+    assert (c.leaf, c.precision, c.checked) == (16, 0, 1)
+    assert c.tie_rel == 1e-6
+
+
+def test_create_rejects_bad_config_before_touching_the_gpu(libpath):
+    from paper_1203_1692_gb300 import _abi
+    L = _abi.lib()
+    h = ctypes.c_void_p()
+    c = _abi.spamm_config_default()
+    c.leaf = 24
+    assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_INVALID_ARG
+    c = _abi.spamm_config_default()
+    c.precision = 9
+    assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_INVALID_ARG
+    c = _abi.spamm_config_default()
+    c.precision = _abi.SPAMM_PREC_TF32X3
+    c.leaf = 128
+    assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_UNSUPPORTED
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):
+    from paper_1203_1692_gb300 import _abi
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _abi.lib()
+
+
+def test_kernels_target_sm103a(libpath):
+    """The build compiles SASS for sm_103a (checked through the build flags;
+    the binary itself is not inspected)."""
+    from paper_1203_1692_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
