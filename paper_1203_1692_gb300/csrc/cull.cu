@@ -13,12 +13,18 @@
 // host round trip between tiers.  A frontier that does not fit is truncated
 // and the overflow flag is raised.
 //
-// Grouping.  A C tile is 128 x 128 (TL = 128 / b leaves per side).  Each leaf
-// triple is counted per tile, the counts are scanned, the triples are
-// scattered into per-tile runs, and one block per tile ORs them into a
-// per-K 64-bit mask (bit y * 8 + x) in shared memory and emits the non-zero
-// (K, mask) steps in ascending K.  The leaf kernels walk these steps, which
-// fixes the accumulation order of every C block.
+// Grouping.  A C tile is 128 x 128, TL = 128 / b = 2^s leaves per side, which
+// is exactly one quadtree node at tier tt = d - s.  The tier-by-tier cull
+// therefore stops at tier tt; its triples (I', K', J') are counted per tile
+// (I', J'), scanned and scattered, and one block per tile finishes the cull
+// of the last s tiers inside its 2^s x 2^s x 2^s sub-cube for every K' in
+// ascending order: level by level in shared memory, a child is tested only
+// if its parent survived, with the same FP64 predicate.  The surviving leaf
+// triples of one (tile, K) are emitted as one step (K, 64-bit mask, bit
+// y * 8 + x for row leaf x and column leaf y of the tile), compacted with a
+// ballot into a coalesced list in ascending K.  This is the leaf-triple list
+// in tile-compressed form; the leaf kernels walk it, which fixes the
+// accumulation order of every C block.
 #include <algorithm>
 
 #include "spamm_internal.cuh"
@@ -99,13 +105,14 @@ __global__ void __launch_bounds__(256) k_cull_tier(int t, const double* __restri
     if (lane == 0 && tie) atomicAdd(&ctl->tie_band, tie);
 }
 
-__global__ void k_cull_finish(int d, DevCtl* ctl, unsigned long long cap) {
+__global__ void k_cull_finish(int tt, DevCtl* ctl, unsigned long long cap) {
     if (threadIdx.x || blockIdx.x) return;
-    for (int t = 0; t <= d; ++t)
+    for (int t = 0; t <= tt; ++t)
         if (ctl->tier_off[t] + ctl->tier_count[t] > cap) ctl->status |= ST_OVERFLOW;
 }
 
-cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau) {
+cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
+                        int tt) {
     cudaStream_t s = ctx->stream;
     const double tau2 = tau * tau;
     const double rel = ctx->cfg.tie_rel;
@@ -116,7 +123,7 @@ cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int blocks = ctx->sm_count * 4;
-    for (int t = 0; t < A->d; ++t) {
+    for (int t = 0; t < tt; ++t) {
         const int64_t off = (((int64_t)1 << (2 * (t + 1))) - 1) / 3;
         // Tier t + 1 has at most 8^(t+1) candidates: size small tiers' grids to them.
         int g = blocks;
@@ -129,31 +136,32 @@ cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_cull_finish<<<1, 32, 0, s>>>(A->d, ctx->ctl, cap);
+    k_cull_finish<<<1, 32, 0, s>>>(tt, ctx->ctl, cap);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- grouping
 
-__device__ inline uint32_t tile_of(uint64_t tri, int tl_shift, int tps) {
-    return (tri_I(tri) >> tl_shift) * (uint32_t)tps + (tri_J(tri) >> tl_shift);
+__device__ inline uint32_t tile_of(uint64_t tri, int tps) {
+    return tri_I(tri) * (uint32_t)tps + tri_J(tri);
 }
 
-__global__ void __launch_bounds__(256) k_group_count(int d, DevCtl* ctl,
-                                                     const uint64_t* __restrict__ pool,
-                                                     unsigned long long cap, int tl_shift, int tps,
+__global__ void __launch_bounds__(256) k_group_count(int tt, DevCtl* ctl,
+                                                     const uint64_t* __restrict__ pool, int tps,
                                                      uint32_t* __restrict__ tile_cnt) {
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
-    const unsigned long long off = ctl->tier_off[d];
-    const unsigned long long m = ctl->tier_count[d];
+    const unsigned long long off = ctl->tier_off[tt];
+    const unsigned long long m = ctl->tier_count[tt];
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < m;
          g += (unsigned long long)gridDim.x * blockDim.x)
-        atomicAdd(&tile_cnt[tile_of(pool[off + g], tl_shift, tps)], 1u);
+        atomicAdd(&tile_cnt[tile_of(pool[off + g], tps)], 1u);
 }
 
 // Exclusive scan of the tile counts (single block), and the pool layout of
-// the grouped arrays behind the leaf frontier.
-__global__ void __launch_bounds__(1024) k_group_scan(int d, DevCtl* ctl, unsigned long long cap,
+// the grouped arrays behind the tier-tt frontier: entries (u32, one per
+// tier-tt triple), then step K (u32) and step masks (u64), S per entry.
+__global__ void __launch_bounds__(1024) k_group_scan(int tt, int S, DevCtl* ctl,
+                                                     unsigned long long cap,
                                                      const uint32_t* __restrict__ cnt,
                                                      uint32_t* __restrict__ off, int tiles) {
     __shared__ uint32_t warp_tot[32];
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(1024) k_group_scan(int d, DevCtl* ctl, unsigne
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int base = 0; base < tiles; base += 1024) {
         const int i = base + threadIdx.x;
-        uint32_t v = i < tiles ? cnt[i] : 0u;
+        const uint32_t v = i < tiles ? cnt[i] : 0u;
         uint32_t x = v;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -188,136 +196,241 @@ __global__ void __launch_bounds__(1024) k_group_scan(int d, DevCtl* ctl, unsigne
     }
     if (threadIdx.x == 0) {
         off[tiles] = carry;
-        const unsigned long long m = ctl->tier_count[d];
-        const unsigned long long leaf_end = ctl->tier_off[d] + m;
-        const unsigned long long half = (m + 1) / 2;  // u32 arrays in 8-byte words
-        ctl->ent_off = leaf_end;
-        ctl->pk_off = leaf_end + half;
-        ctl->pm_off = leaf_end + 2 * half;
-        ctl->need_words = leaf_end + 2 * half + m;
-        if (ctl->need_words > cap) ctl->status |= ST_OVERFLOW;
+        const unsigned long long m = ctl->tier_count[tt];
+        const unsigned long long end = ctl->tier_off[tt] + m;
+        const unsigned long long ms = m * (unsigned long long)S;
+        ctl->ent_off = end;
+        ctl->pk_off = end + (m + 1) / 2;
+        ctl->pm_off = ctl->pk_off + (ms + 1) / 2;
+        ctl->need_words = ctl->pm_off + ms;
+        if (ctl->need_words > cap || m >= 0xffffffffull / (unsigned long long)S)
+            ctl->status |= ST_OVERFLOW;
     }
 }
 
-__global__ void __launch_bounds__(256) k_group_scatter(int d, DevCtl* ctl,
-                                                       uint64_t* __restrict__ pool, int tl_shift,
-                                                       int tps, const uint32_t* __restrict__ off,
+__global__ void __launch_bounds__(256) k_group_scatter(int tt, DevCtl* ctl,
+                                                       uint64_t* __restrict__ pool, int tps,
+                                                       const uint32_t* __restrict__ off,
                                                        uint32_t* __restrict__ fill) {
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
-    const unsigned long long loff = ctl->tier_off[d];
-    const unsigned long long m = ctl->tier_count[d];
+    const unsigned long long loff = ctl->tier_off[tt];
+    const unsigned long long m = ctl->tier_count[tt];
     uint32_t* ent = reinterpret_cast<uint32_t*>(pool + ctl->ent_off);
-    const uint32_t tmask = (1u << tl_shift) - 1u;
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < m;
          g += (unsigned long long)gridDim.x * blockDim.x) {
         const uint64_t tri = pool[loff + g];
-        const uint32_t u = tile_of(tri, tl_shift, tps);
-        const uint32_t pos = off[u] + atomicAdd(&fill[u], 1u);
-        const uint32_t x = tri_I(tri) & tmask, y = tri_J(tri) & tmask;
-        ent[pos] = (tri_K(tri) << 6) | (y << 3) | x;
+        const uint32_t u = tile_of(tri, tps);
+        ent[off[u] + atomicAdd(&fill[u], 1u)] = tri_K(tri);
     }
 }
 
-// One block per tile: per-K masks in shared memory over the K range the
-// tile touches, then the non-zero steps in ascending K.
-__global__ void __launch_bounds__(512) k_group_steps(DevCtl* ctl, const uint64_t* __restrict__ pool,
-                                                     const uint32_t* __restrict__ off,
-                                                     uint32_t* __restrict__ steps, int nkmax) {
-    extern __shared__ unsigned long long smask[];
-    __shared__ uint32_t kmin_s, kmax_s, warp_cnt[16], base_s;
+// Block-wide exclusive scan of one value per thread (blockDim = 512).
+__device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t t = lane < nw ? warp_sums[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_sums[lane] = t;
+        if (lane == nw - 1) *total = t;
+    }
+    __syncthreads();
+    const uint32_t r = (wid ? warp_sums[wid - 1] : 0u) + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Finish the cull of one tile's sub-cubes (DS = d - tt tiers below the tile
+// node) and emit its (K, mask) steps in ascending K.  blockDim = 512.
+template <int DS>
+__global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restrict__ pyrA,
+                                                   const double* __restrict__ pyrB, double tau2,
+                                                   double lo2, double hi2, DevCtl* ctl,
+                                                   uint64_t* __restrict__ pool,
+                                                   const uint32_t* __restrict__ off,
+                                                   uint32_t* __restrict__ steps, int tps) {
+    constexpr int S = 1 << DS;               // K leaves per tier-tt K'
+    constexpr int CUBE = S * S * S;          // leaf triples per sub-cube
+    constexpr int G = 512 / CUBE;            // sub-cubes per pass
+    extern __shared__ uint32_t dyn[];        // bitmap of K' (2^tt bits), then the K' list
+    __shared__ unsigned char keep_a[512], keep_b[512];
+    __shared__ unsigned long long masks[512];
+    __shared__ uint32_t warp_sums[16], total_s;
+    __shared__ unsigned long long st_cand[4], st_kept[4], st_tie;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
     const uint32_t u = blockIdx.x;
     const uint32_t e0 = off[u], e1 = off[u + 1];
-    const uint32_t* ent = reinterpret_cast<const uint32_t*>(pool + ctl->ent_off);
-    uint32_t* pk = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(pool) + ctl->pk_off);
-    unsigned long long* pm =
-        reinterpret_cast<unsigned long long*>(const_cast<uint64_t*>(pool) + ctl->pm_off);
     if (e0 == e1) {
         if (threadIdx.x == 0) steps[u] = 0;
         return;
     }
-    if (threadIdx.x == 0) {
-        kmin_s = 0xffffffffu;
-        kmax_s = 0;
+    const int tid = threadIdx.x;
+    const uint32_t I0 = u / tps, J0 = u % tps;
+    const uint32_t* ent = reinterpret_cast<const uint32_t*>(pool + ctl->ent_off);
+    uint32_t* pk = reinterpret_cast<uint32_t*>(pool + ctl->pk_off);
+    unsigned long long* pm = reinterpret_cast<unsigned long long*>(pool + ctl->pm_off);
+    const int words = ((1 << tt) + 31) >> 5;
+    uint32_t* bitmap = dyn;
+    uint32_t* klist = dyn + words;
+    for (int w = tid; w < words; w += blockDim.x) bitmap[w] = 0u;
+    if (tid < 4) st_cand[tid] = st_kept[tid] = 0ull;
+    if (tid == 0) st_tie = 0ull;
+    __syncthreads();
+    for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
+        const uint32_t k = ent[e];
+        atomicOr(&bitmap[k >> 5], 1u << (k & 31));
     }
     __syncthreads();
-    uint32_t lo = 0xffffffffu, hi = 0;
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const uint32_t K = ent[e] >> 6;
-        lo = min(lo, K);
-        hi = max(hi, K);
+    // ascending K' list
+    for (int w0 = 0, base = 0; w0 < words; w0 += blockDim.x) {
+        const int w = w0 + tid;
+        const uint32_t bits = w < words ? bitmap[w] : 0u;
+        const uint32_t r = block_excl_scan(__popc(bits), warp_sums, &total_s);
+        uint32_t b = bits, pos = base + r;
+        while (b) {
+            const int q = __ffs(b) - 1;
+            b &= b - 1;
+            klist[pos++] = (uint32_t)(w * 32 + q);
+        }
+        base += total_s;
+        __syncthreads();
     }
-    atomicMin(&kmin_s, lo);
-    atomicMax(&kmax_s, hi);
-    __syncthreads();
-    const uint32_t k0 = kmin_s;
-    const int span = (int)(kmax_s - k0 + 1);
-    // process the K range in windows of nkmax entries
+    const int nk = (int)(e1 - e0);
+    const uint32_t obase = e0 * S;
     uint32_t written = 0;
-    for (int w0 = 0; w0 < span; w0 += nkmax) {
-        const int wn = min(nkmax, span - w0);
-        for (int i = threadIdx.x; i < wn; i += blockDim.x) smask[i] = 0ull;
-        __syncthreads();
-        for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const uint32_t v = ent[e];
-            const int kk = (int)((v >> 6) - k0) - w0;
-            if (kk >= 0 && kk < wn) atomicOr(&smask[kk], 1ull << (v & 63));
+    unsigned long long cand[4] = {0, 0, 0, 0}, kept[4] = {0, 0, 0, 0}, tie = 0;
+    for (int g0 = 0; g0 < nk; g0 += G) {
+        unsigned char* prev = keep_a;
+        unsigned char* cur = keep_b;
+        if (DS == 0) {
+            // the tile is one leaf: every tier-d entry is a kept leaf triple
+            if (tid < G) cur[tid] = (g0 + tid < nk) ? 1 : 0;
         }
-        __syncthreads();
-        // ordered compaction of the non-zero masks
-        for (int c0 = 0; c0 < wn; c0 += blockDim.x) {
-            const int i = c0 + threadIdx.x;
-            const unsigned long long m = i < wn ? smask[i] : 0ull;
-            const unsigned bal = __ballot_sync(0xffffffffu, m != 0ull);
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-            if (lane == 0) warp_cnt[wid] = __popc(bal);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t acc = written;
-                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-                    const uint32_t c = warp_cnt[q];
-                    warp_cnt[q] = acc;
-                    acc += c;
+#pragma unroll
+        for (int l = 1; l <= DS; ++l) {
+            const int side = 1 << l;
+            const int per = side * side * side;
+            const int t = tt + l;
+            const int64_t w = (int64_t)1 << t;
+            const double* na = pyrA + ((((int64_t)1 << (2 * t)) - 1) / 3);
+            const double* nb = pyrB + ((((int64_t)1 << (2 * t)) - 1) / 3);
+            if (tid < G * per) {
+                const int g = tid / per, loc = tid % per;
+                const int xi = loc % side, yi = (loc / side) % side, ki = loc / (side * side);
+                unsigned char kp = 0;
+                bool par = (g0 + g < nk);
+                if (par && l > 1) {
+                    const int ps = side >> 1;
+                    const int ploc = ((ki >> 1) * ps + (yi >> 1)) * ps + (xi >> 1);
+                    par = prev[g * (per >> 3) + ploc] != 0;
                 }
-                base_s = acc;
+                if (par) {
+                    const int64_t i = (int64_t)I0 * side + xi;
+                    const int64_t k = (int64_t)klist[g0 + g] * side + ki;
+                    const int64_t j = (int64_t)J0 * side + yi;
+                    const double a = na[i * w + k];
+                    const double b = nb[k * w + j];
+                    const double p = a * b;
+                    const bool nz = a > 0.0 && b > 0.0;
+                    kp = (nz && p >= tau2) ? 1 : 0;
+                    cand[l - 1] += 1;
+                    kept[l - 1] += kp;
+                    tie += (nz && p >= lo2 && p <= hi2) ? 1 : 0;
+                }
+                cur[tid] = kp;
             }
             __syncthreads();
-            if (m) {
-                const uint32_t pos = e0 + warp_cnt[wid] + __popc(bal & ((1u << lane) - 1u));
-                pk[pos] = k0 + (uint32_t)(w0 + i);
-                pm[pos] = m;
-            }
-            __syncthreads();
-            written = base_s;
+            unsigned char* tmp = prev;
+            prev = cur;
+            cur = tmp;
         }
+        unsigned char* leaf = DS == 0 ? cur : prev;
+        // masks of the G * S leaf-level K values of this pass
+        if (tid < G * S) masks[tid] = 0ull;
+        __syncthreads();
+        if (tid < G * CUBE && leaf[tid]) {
+            const int g = tid / CUBE, loc = tid % CUBE;
+            const int xi = loc % S, yi = (loc / S) % S, ki = loc / (S * S);
+            atomicOr(&masks[g * S + ki], 1ull << (yi * 8 + xi));
+        }
+        __syncthreads();
+        const unsigned long long m = tid < G * S ? masks[tid] : 0ull;
+        const uint32_t r = block_excl_scan(m ? 1u : 0u, warp_sums, &total_s);
+        if (m) {
+            const int g = tid / S, ki = tid % S;
+            pk[obase + written + r] = klist[g0 + g] * S + ki;
+            pm[obase + written + r] = m;
+        }
+        written += total_s;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    // statistics of the tiers below the tile node
+#pragma unroll
+    for (int l = 0; l < DS; ++l) {
+        if (cand[l]) atomicAdd(&st_cand[l], cand[l]);
+        if (kept[l]) atomicAdd(&st_kept[l], kept[l]);
+    }
+    if (tie) atomicAdd(&st_tie, tie);
+    __syncthreads();
+    if (tid == 0) {
         steps[u] = written;
         atomicAdd(&ctl->active_steps, (unsigned long long)written);
+        for (int l = 0; l < DS; ++l) {
+            atomicAdd(&ctl->tier_cand[tt + 1 + l], st_cand[l]);
+            atomicAdd(&ctl->tier_count[tt + 1 + l], st_kept[l]);
+        }
+        if (st_tie) atomicAdd(&ctl->tie_band, st_tie);
     }
 }
 
-cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A) {
+cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
+                         int tt) {
     cudaStream_t s = ctx->stream;
     const int tps = tiles_per_side(A);
     const int tiles = tps * tps;
-    const int tl = kTileRows / A->b;
-    int tl_shift = 0;
-    while ((1 << tl_shift) < tl) ++tl_shift;
+    const int ds = A->d - tt;
+    const int S = 1 << ds;
     const unsigned long long cap = (unsigned long long)ctx->pool_words;
+    const double tau2 = tau * tau;
+    const double rel = ctx->cfg.tie_rel;
+    const double lo2 = tau2 * (1.0 - rel) * (1.0 - rel);
+    const double hi2 = tau2 * (1.0 + rel) * (1.0 + rel);
     cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(uint32_t) * tiles, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tile_fill, 0, sizeof(uint32_t) * tiles, s);
     if (e != cudaSuccess) return e;
     const int blocks = ctx->sm_count * 4;
-    k_group_count<<<blocks, 256, 0, s>>>(A->d, ctx->ctl, ctx->pool, cap, tl_shift, tps,
-                                         ctx->tile_cnt);
-    k_group_scan<<<1, 1024, 0, s>>>(A->d, ctx->ctl, cap, ctx->tile_cnt, ctx->tile_off, tiles);
-    k_group_scatter<<<blocks, 256, 0, s>>>(A->d, ctx->ctl, ctx->pool, tl_shift, tps,
-                                           ctx->tile_off, ctx->tile_fill);
-    const int nkmax = 4096;  // 32 KB of masks per window
-    k_group_steps<<<tiles, 512, nkmax * sizeof(unsigned long long), s>>>(
-        ctx->ctl, ctx->pool, ctx->tile_off, ctx->tile_steps, nkmax);
+    k_group_count<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tps, ctx->tile_cnt);
+    k_group_scan<<<1, 1024, 0, s>>>(tt, S, ctx->ctl, cap, ctx->tile_cnt, ctx->tile_off, tiles);
+    k_group_scatter<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tps, ctx->tile_off,
+                                           ctx->tile_fill);
+    const int words = ((1 << tt) + 31) / 32;
+    const size_t dsm = sizeof(uint32_t) * (words + ((size_t)1 << tt));
+#define SPAMM_TC(DSV)                                                                          \
+    do {                                                                                       \
+        if (dsm > 48 * 1024)                                                                   \
+            cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)dsm);                                                    \
+        k_tile_cull<DSV><<<tiles, 512, dsm, s>>>(tt, A->pyr, B->pyr, tau2, lo2, hi2, ctx->ctl, \
+                                                 ctx->pool, ctx->tile_off, ctx->tile_steps,    \
+                                                 tps);                                         \
+    } while (0)
+    switch (ds) {
+        case 0: SPAMM_TC(0); break;
+        case 1: SPAMM_TC(1); break;
+        case 2: SPAMM_TC(2); break;
+        default: SPAMM_TC(3); break;
+    }
+#undef SPAMM_TC
     return cudaGetLastError();
 }
 

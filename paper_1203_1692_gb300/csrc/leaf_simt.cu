@@ -16,7 +16,8 @@ namespace spamm {
 __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, int64_t lda,
                                                    const float* __restrict__ B, int64_t ldb,
                                                    float* __restrict__ C, int64_t ldc, int64_t n,
-                                                   int b, int tps, float alpha, float beta,
+                                                   int b, int tps, int S, float alpha,
+                                                   float beta,
                                                    const DevCtl* __restrict__ ctl,
                                                    const uint64_t* __restrict__ pool,
                                                    const uint32_t* __restrict__ off,
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
     const uint32_t ns = steps[u];
-    const uint32_t base = off[u];
+    const uint32_t base = off[u] * (uint32_t)S;
     const uint32_t* pk = reinterpret_cast<const uint32_t*>(pool + ctl->pk_off);
     const unsigned long long* pm = reinterpret_cast<const unsigned long long*>(pool + ctl->pm_off);
     const int chunks = b >> 4;
@@ -97,7 +98,8 @@ cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tr
                              float alpha, float beta, float* C, int64_t ldc) {
     const int tps = tiles_per_side(A);
     k_leaf_simt<<<tps * tps, 256, 0, ctx->stream>>>(A->A, A->lda, B->A, B->lda, C, ldc, A->n,
-                                                    A->b, tps, alpha, beta, ctx->ctl, ctx->pool,
+                                                    A->b, tps, ctx->last_S, alpha, beta,
+                                                    ctx->ctl, ctx->pool,
                                                     ctx->tile_off, ctx->tile_steps);
     return cudaGetLastError();
 }

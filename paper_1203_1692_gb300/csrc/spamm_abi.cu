@@ -32,6 +32,12 @@ int tiles_per_side(const spamm_tree* t) {
     return (int)(t->nlp / (kTileRows / t->b));
 }
 
+int tile_tier(const spamm_tree* t) {
+    int s = 0;
+    while ((1 << s) < kTileRows / t->b) ++s;
+    return t->d > s ? t->d - s : 0;
+}
+
 }  // namespace spamm
 
 namespace {
@@ -51,7 +57,7 @@ spamm_status alloc_pool(spamm_ctx* ctx, int64_t bytes) {
         ctx->pool = nullptr;
         ctx->pool_words = 0;
     }
-    bytes = std::max<int64_t>(bytes, 1 << 20);
+    bytes = std::max<int64_t>(bytes, 4096);
     bytes = (bytes + 255) / 256 * 256;
     cudaError_t e = cudaMalloc(&ctx->pool, (size_t)bytes);
     if (e != cudaSuccess) return cuda_err(ctx, e, "pool allocation");
@@ -95,11 +101,14 @@ spamm_status check_matrix(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda
     return SPAMM_OK;
 }
 
-int64_t words_needed(const DevCtl& c, int d) {
+// Pool words a multiply needs: the frontiers of tiers 0..tt, then one u32
+// entry per tier-tt triple and S steps (u32 K + u64 mask) per entry.
+int64_t words_needed(const DevCtl& c, int tt, int S) {
     unsigned long long s = 0;
-    for (int t = 0; t <= d; ++t) s += c.tier_count[t];
-    const unsigned long long m = c.tier_count[d];
-    return (int64_t)(s + 2 * ((m + 1) / 2) + m);
+    for (int t = 0; t <= tt; ++t) s += c.tier_count[t];
+    const unsigned long long m = c.tier_count[tt];
+    const unsigned long long ms = m * (unsigned long long)S;
+    return (int64_t)(s + (m + 1) / 2 + (ms + 1) / 2 + ms);
 }
 
 }  // namespace
@@ -299,8 +308,9 @@ static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
-    if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau);
-    if (e == cudaSuccess) e = launch_group(ctx, A);
+    const int tt = tile_tier(A);
+    if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau, tt);
+    if (e == cudaSuccess) e = launch_group(ctx, A, B, tau, tt);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
     if (e == cudaSuccess) {
         if (ctx->cfg.precision == SPAMM_PREC_FP32)
@@ -315,6 +325,10 @@ static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
     return cuda_err(ctx, e, "multiply launch");
 }
 
+static spamm_status status_from_ctl(spamm_ctx* ctx, const DevCtl& c);
+static spamm_status status_from_ctl_pub(spamm_ctx* ctx, const DevCtl& c) {
+    return status_from_ctl(ctx, c);
+}
 static spamm_status status_from_ctl(spamm_ctx* ctx, const DevCtl& c) {
     if (c.status & ST_NONFINITE)
         return set_err(ctx, SPAMM_ERR_NONFINITE, "an operand holds Inf or NaN");
@@ -344,6 +358,8 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
     ctx->last_prec = A->precision;
     ctx->last_tau = tau;
     ctx->last_tiles = tps * tps;
+    ctx->last_tt = tile_tier(A);
+    ctx->last_S = 1 << (A->d - ctx->last_tt);
     ctx->last_status = SPAMM_OK;
     for (int attempt = 0;; ++attempt) {
         st = launch_multiply_once(ctx, A, B, tau, alpha, beta, C, ldc);
@@ -353,7 +369,8 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
         if (e != cudaSuccess) return (spamm_status)(ctx->last_status = cuda_err(ctx, e, "multiply"));
         const DevCtl& c = *ctx->ctl_host;
         if ((c.status & ST_OVERFLOW) && !(c.status & (ST_NONFINITE | ST_TIMEOUT)) && attempt < 8) {
-            const int64_t need = std::max<int64_t>(words_needed(c, A->d), 2 * ctx->pool_words);
+            const int64_t need = std::max<int64_t>(words_needed(c, ctx->last_tt, ctx->last_S),
+                                                   2 * ctx->pool_words);
             st = alloc_pool(ctx, need * 8 + need * 2);  // 25% headroom
             if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
             continue;
@@ -386,7 +403,7 @@ spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     out->kept_flops = 2.0 * b * b * b * (double)out->leaf_triples;
     out->dense_flops = 2.0 * (double)ctx->last_n * (double)ctx->last_n * (double)ctx->last_n;
     out->pool_bytes = ctx->pool_words * 8;
-    out->pool_needed_bytes = words_needed(c, d) * 8;
+    out->pool_needed_bytes = words_needed(c, ctx->last_tt, ctx->last_S) * 8;
     if (ctx->timed) {
         cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&out->ms_numeric, ctx->ev[1], ctx->ev[2]);
@@ -406,17 +423,42 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     const int d = ctx->last_d;
     const int64_t m = (int64_t)c.tier_count[d];
     *count = m;
-    if (c.status & ST_OVERFLOW) return set_err(ctx, SPAMM_ERR_CAPACITY, "triple pool overflow");
-    const int64_t k = std::min(m, cap);
-    if (k <= 0) return SPAMM_OK;
-    std::vector<uint64_t> buf((size_t)k);
-    e = cudaMemcpy(buf.data(), ctx->pool + c.tier_off[d], sizeof(uint64_t) * k,
-                   cudaMemcpyDeviceToHost);
+    if (c.status & (ST_OVERFLOW | ST_NONFINITE)) {
+        *count = 0;
+        return status_from_ctl_pub(ctx, c);
+    }
+    if (cap <= 0 || m == 0) return SPAMM_OK;
+    // expand the tile-compressed steps (K, mask) into (I, K, J) rows
+    const int64_t tiles = ctx->last_tiles;
+    const int tps = (int)std::lround(std::sqrt((double)tiles));
+    const int tl = kTileRows / ctx->last_b;
+    const uint64_t msteps = (uint64_t)c.tier_count[ctx->last_tt] * ctx->last_S;
+    std::vector<uint32_t> off((size_t)tiles + 1), nst((size_t)tiles), pk((size_t)msteps);
+    std::vector<uint64_t> pm((size_t)msteps);
+    e = cudaMemcpy(off.data(), ctx->tile_off, sizeof(uint32_t) * (tiles + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(nst.data(), ctx->tile_steps, sizeof(uint32_t) * tiles, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && msteps)
+        e = cudaMemcpy(pk.data(), reinterpret_cast<uint32_t*>(ctx->pool + c.pk_off),
+                       sizeof(uint32_t) * msteps, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && msteps)
+        e = cudaMemcpy(pm.data(), ctx->pool + c.pm_off, sizeof(uint64_t) * msteps,
+                       cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(ctx, e, "triples copy");
-    for (int64_t i = 0; i < k; ++i) {
-        host_out[3 * i + 0] = (int32_t)tri_I(buf[i]);
-        host_out[3 * i + 1] = (int32_t)tri_K(buf[i]);
-        host_out[3 * i + 2] = (int32_t)tri_J(buf[i]);
+    int64_t k = 0;
+    for (int64_t u = 0; u < tiles && k < cap; ++u) {
+        const uint64_t base = (uint64_t)off[u] * ctx->last_S;
+        for (uint32_t q = 0; q < nst[u] && k < cap; ++q) {
+            uint64_t mk = pm[base + q];
+            while (mk && k < cap) {
+                const int bit = __builtin_ctzll(mk);
+                mk &= mk - 1;
+                host_out[3 * k + 0] = (int32_t)((u / tps) * tl + (bit & 7));
+                host_out[3 * k + 1] = (int32_t)pk[base + q];
+                host_out[3 * k + 2] = (int32_t)((u % tps) * tl + (bit >> 3));
+                ++k;
+            }
+        }
     }
     return SPAMM_OK;
 }

@@ -39,7 +39,7 @@ struct DevCtl {
     unsigned long long tier_off[SPAMM_MAX_TIERS + 1];
     unsigned long long tie_band;
     unsigned long long active_steps;
-    unsigned long long ent_off;     // u32 entries (one per leaf triple)
+    unsigned long long ent_off;     // u32 K of each tier-tt triple, grouped by tile
     unsigned long long pk_off;      // u32 K of each (tile, K) step
     unsigned long long pm_off;      // u64 mask of each (tile, K) step
     unsigned long long need_words;  // words the whole multiply needs
@@ -100,7 +100,7 @@ struct spamm_ctx {
     cudaEvent_t ev[4];
     bool timed;
     // last multiply
-    int last_d, last_b, last_prec;
+    int last_d, last_b, last_prec, last_tt, last_S;
     int64_t last_n, last_tiles;
     double last_tau;
     int last_status;
@@ -126,8 +126,12 @@ size_t pack_bytes_for(int precision, int64_t nlp, int b);
 int pack_arrays_for(int precision);  // 1 or 2 per role
 
 // cull.cu
-cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau);
-cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A);
+// tt = tier of the tile nodes (a tile is 128 / b leaves per side)
+int tile_tier(const spamm_tree* t);
+cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
+                        int tt);
+cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
+                         int tt);
 
 // leaf_simt.cu
 cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,

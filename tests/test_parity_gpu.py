@@ -176,21 +176,22 @@ def test_invalid_arguments():
 
 def test_pool_overflow_checked_and_unchecked():
     P = _spamm()
-    n, b = 512, 16
+    n, b = 1024, 16
     A = gen.uniform_dense(n, seed=1)
     dA = _dev(A)
     ref = O.multiply(A, A, b, 0.0)
     # unchecked: tiny pool -> CAPACITY through stats, C untouched
-    ctx = P.Context(leaf=b, pool_bytes=1 << 20, checked=False)
+    ctx = P.Context(leaf=b, pool_bytes=16384, checked=False)
     t = ctx.build_norms(dA)
     C = torch.zeros((n, n), dtype=torch.float32, device="cuda")
     ctx.multiply(t, t, 0.0, C=C)
     with pytest.raises(P.SpammError, match="CAPACITY"):
         ctx.stats()
     need = ctx.stats(raise_on_error=False)["pool_needed_bytes"]
-    assert need > (1 << 20)
+    assert need > 16384
+    assert not C.any()
     # checked: grows the pool and re-runs
-    ctx2 = P.Context(leaf=b, pool_bytes=1 << 20, checked=True)
+    ctx2 = P.Context(leaf=b, pool_bytes=16384, checked=True)
     t2 = ctx2.build_norms(dA)
     C2 = ctx2.multiply(t2, t2, 0.0)
     assert rel_max_err(C2.cpu().numpy(), ref.C) <= 1e-5
