@@ -252,7 +252,7 @@ def main():
                           "ms": st["ms_total"]})
             if err <= err_sgemm and tau is None:
                 tau = t
-        if tau is None:
+        if tau is None:        # no tau on the grid reaches SGEMM's error
             tau = TAU_GRID[-1]
     else:
         tau = float(args.tau)

@@ -6,9 +6,11 @@
 // tile's (K, mask) steps in ascending K; for each step it stages A's
 // 128 x 16 and B's 16 x 128 slices per 16-wide K chunk in shared memory
 // (zero outside the n x n matrix) and a thread runs its 8 x 8 x 16 FFMA
-// block only when its leaf pair's bit is set.  Per C element the products
-// are added in ascending K, then ascending k, so the result is
-// deterministic.
+// block only when its leaf pair's bit is set.  Like the numeric multiply of
+// the method, each leaf product is formed on its own (an FFMA chain over its
+// b values of k, starting from zero) and then added to the C block, in
+// ascending K: one rounding into C per kept product instead of one per k,
+// and a fixed order, so the result is deterministic.
 #include "spamm_internal.cuh"
 
 namespace spamm {
@@ -47,6 +49,11 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
         const int64_t K = pk[base + st];
         const unsigned long long mask = pm[base + st];
         const bool mine = (mask >> bit) & 1ull;
+        float part[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part[i][j] = 0.f;
         for (int ch = 0; ch < chunks; ++ch) {
             const int64_t c0 = K * b + 16 * ch;
 #pragma unroll
@@ -72,10 +79,16 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                        for (int j = 0; j < 8; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
                 }
             }
             __syncthreads();
+        }
+        if (mine) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
         }
     }
 #pragma unroll

@@ -1,0 +1,115 @@
+"""Parity of the tcgen05 leaf kernel with the FP64 oracle, through the C ABI.
+
+The symbolic stages are shared with the FP32 path, so the surviving-triple
+set must match the oracle exactly as there.  Tolerances on
+max|dC| / max|C| follow from each precision's operand splitting:
+  tf32x3  a = hi + lo + r with |r| <= 2^-22 |a|; dropped lo*lo and r terms
+          give ~3 * 2^-22 = 7e-7 per product, plus FP32 accumulation -> 1e-5
+          (the FP32 bar);
+  bf16x3  |r| <= 2^-18 |a|, ~3 * 2^-18 = 1.1e-5 per product, times a
+          condition sum |a||b| / max|C| of a few -> 1e-4;
+  tf32    one pass, |a - hi| <= 2^-11 |a| per operand, ~2^-10 per product
+          -> 5e-3.
+"""
+import numpy as np
+import pytest
+
+import spamm_inputs as gen
+from oracle import oracle as O
+from tests.spamm_check import (as_set, blocks_from, compare_triples, rel_max_err,
+                               sample_blocks)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4, "tf32": 5e-3}
+
+
+def _run(A, B, b, tau, precision, alpha=1.0, beta=0.0, C0=None):
+    import paper_1203_1692_gb300 as P
+    ctx = P.Context(leaf=b, precision=precision)
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    ta = ctx.build_norms(dA)
+    if B is A:
+        tb = ta
+    else:
+        dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+        tb = ctx.build_norms(dB)
+    C = torch.from_numpy(np.ascontiguousarray(C0)).cuda() if C0 is not None else None
+    C = ctx.multiply(ta, tb, tau, alpha, beta, C)
+    torch.cuda.synchronize()
+    return ctx, C.cpu().numpy()
+
+
+def _matrix(kind, n, seed=0):
+    if kind == "exp":
+        return gen.exp_decay(n, 0.9, seed=seed)
+    if kind == "alg":
+        return gen.algebraic_decay(n, seed=seed)
+    if kind == "water":
+        return gen.water_like(n // 25, 25, seed=seed)
+    return gen.uniform_dense(n, seed=seed, symmetric=False)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32"])
+def test_single_tile(prec):
+    n, b = 128, 16
+    A = _matrix("exp", n)
+    ctx, C = _run(A, A, b, 1e-6, prec)
+    ref = O.multiply(A, A, b, 1e-6)
+    assert as_set(ctx.triples()) == as_set(ref.triples)
+    assert rel_max_err(C, ref.C) <= TOL[prec]
+
+
+CASES = [
+    (1024, 16, "exp", 1e-6),
+    (1000, 16, "exp", 1e-4),
+    (700, 32, "water", 1e-3),
+    (515, 16, "alg", 1e-5),
+    (333, 16, "dense", 0.0),
+    (333, 32, "dense", 0.0),
+    (600, 32, "exp", 1e-5),
+]
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32"])
+@pytest.mark.parametrize("n,b,kind,tau", CASES)
+def test_tc_parity_with_oracle(prec, n, b, kind, tau):
+    A = _matrix(kind, n)
+    B = _matrix("exp", n, seed=1) if kind == "dense" else A
+    ctx, C = _run(A, B, b, tau, prec)
+    ref = O.multiply(A, B, b, tau)
+    d = O.depth(n, b)
+    compare_triples(ctx.triples(), ref.triples, O.pyramid(A, b), O.pyramid(B, b), d, tau)
+    assert rel_max_err(C, ref.C) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tc_alpha_beta(prec):
+    n, b = 260, 16
+    A = gen.exp_decay_nonsym(n, 0.85, seed=2)
+    B = gen.exp_decay_nonsym(n, 0.85, seed=3)
+    C0 = gen.uniform_dense(n, seed=4, symmetric=False)
+    _, C = _run(A, B, b, 1e-4, prec, alpha=0.5, beta=-2.0, C0=C0)
+    ref = O.multiply(A, B, b, 1e-4, alpha=0.5, beta=-2.0, C=C0.astype(np.float64))
+    assert rel_max_err(C, ref.C) <= TOL[prec]
+
+
+def test_tc_deterministic():
+    A = _matrix("exp", 1024)
+    _, C1 = _run(A, A, 16, 1e-6, "tf32x3")
+    _, C2 = _run(A, A, 16, 1e-6, "tf32x3")
+    np.testing.assert_array_equal(C1, C2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tc_water_like_n7500_sampled(prec):
+    A = gen.water_like()
+    n, b, tau = A.shape[0], 16, 1e-6
+    ctx, C = _run(A, A, b, tau, prec)
+    ij = sample_blocks(n, b, 24)
+    pa = O.pyramid(A, b)
+    ref, _ = O.blocks(A, A, b, tau, ij, pa, pa)
+    got = blocks_from(C, ij, b, n)
+    assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL[prec]
