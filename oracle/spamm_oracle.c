@@ -12,7 +12,7 @@
  *   - per-node Frobenius norms, bottom-up ........ Sec. II.B, Eq. (norm)
  *   - recursive product under the SpAMM condition  Eqs. (product), (norm_condition)
  *   - linear (Morton) index, k-value blocks, norm
- *     sort and convolution of the linkless tree .. Sec. III.E.1-2, Algorithm 1,
+ *     sort and convolution of the linkless tree .. Sec. III.D.1-2, Algorithm 1,
  *                                                  Eqs. (linear_index), (convolution)
  *   - numeric multiply C_ij += A_ik B_kj ......... Algorithm 1 (numeric part)
  *   - SGEMM-style alpha/beta epilogue ............ Sec. II (problem statement)
@@ -194,7 +194,7 @@ void oracle_morton_decode(uint64_t l, uint32_t *i, uint32_t *j)
     *j = compress_even(l);
 }
 
-/* The masks of Sec. III.E.2: the k digits of l_A(ik) are its even bits and
+/* The masks of Sec. III.D.2: the k digits of l_A(ik) are its even bits and
  * those of l_B(kj) its odd bits; Eq. (convolution) assembles l_C(ij) from
  * the odd bits of l_A and the even bits of l_B. */
 uint64_t oracle_k_key_A(uint64_t lA) { return lA & EVEN_BITS; }

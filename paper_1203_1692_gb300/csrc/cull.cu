@@ -252,6 +252,14 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 
 // Finish the cull of one tile's sub-cubes (DS = d - tt tiers below the tile
 // node) and emit its (K, mask) steps in ascending K.  blockDim = 512.
+//
+// One warp evaluates one (K', kk) slice of a sub-cube: the S x S leaf pairs
+// (x, y) of leaf column K = K' * S + kk.  A lane tests its leaf triples and
+// all their ancestors below the tile node with the FP64 predicate (a leaf
+// survives iff every ancestor does, which is the level-by-level cull), and
+// the warp ORs the survivors into the 64-bit mask of that K.  Slices are
+// independent, so no block-wide synchronisation is needed between tiers;
+// the masks of a window of K values are then compacted in ascending K.
 template <int DS>
 __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restrict__ pyrA,
                                                    const double* __restrict__ pyrB, double tau2,
@@ -260,11 +268,11 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
                                                    const uint32_t* __restrict__ off,
                                                    uint32_t* __restrict__ steps, int tps) {
     constexpr int S = 1 << DS;               // K leaves per tier-tt K'
-    constexpr int CUBE = S * S * S;          // leaf triples per sub-cube
-    constexpr int G = 512 / CUBE;            // sub-cubes per pass
+    constexpr int PAIRS = S * S;             // leaf pairs (x, y) of one slice
+    constexpr int WIN = 4096;                // masks per window (32 KB)
+    constexpr int KPW = WIN / S;             // K' per window
     extern __shared__ uint32_t dyn[];        // bitmap of K' (2^tt bits), then the K' list
-    __shared__ unsigned char keep_a[512], keep_b[512];
-    __shared__ unsigned long long masks[512];
+    __shared__ unsigned long long masks[WIN];
     __shared__ uint32_t warp_sums[16], total_s;
     __shared__ unsigned long long st_cand[4], st_kept[4], st_tie;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
         if (threadIdx.x == 0) steps[u] = 0;
         return;
     }
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t I0 = u / tps, J0 = u % tps;
     const uint32_t* ent = reinterpret_cast<const uint32_t*>(pool + ctl->ent_off);
     uint32_t* pk = reinterpret_cast<uint32_t*>(pool + ctl->pk_off);
@@ -309,78 +317,79 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
     const uint32_t obase = e0 * S;
     uint32_t written = 0;
     unsigned long long cand[4] = {0, 0, 0, 0}, kept[4] = {0, 0, 0, 0}, tie = 0;
-    for (int g0 = 0; g0 < nk; g0 += G) {
-        unsigned char* prev = keep_a;
-        unsigned char* cur = keep_b;
-        if (DS == 0) {
-            // the tile is one leaf: every tier-d entry is a kept leaf triple
-            if (tid < G) cur[tid] = (g0 + tid < nk) ? 1 : 0;
-        }
+    const int64_t wd = (int64_t)1 << (tt + DS);
+    for (int kw = 0; kw < nk; kw += KPW) {
+        const int kn = min(KPW, nk - kw);
+        // phase 1: one warp per (K', kk) slice
+        for (int item = warp; item < kn * S; item += 16) {
+            const int g = item / S, kk = item % S;
+            const uint32_t Kp = klist[kw + g];
+            unsigned long long bits = 0ull;
 #pragma unroll
-        for (int l = 1; l <= DS; ++l) {
-            const int side = 1 << l;
-            const int per = side * side * side;
-            const int t = tt + l;
-            const int64_t w = (int64_t)1 << t;
-            const double* na = pyrA + ((((int64_t)1 << (2 * t)) - 1) / 3);
-            const double* nb = pyrB + ((((int64_t)1 << (2 * t)) - 1) / 3);
-            if (tid < G * per) {
-                const int g = tid / per, loc = tid % per;
-                const int xi = loc % side, yi = (loc / side) % side, ki = loc / (side * side);
-                unsigned char kp = 0;
-                bool par = (g0 + g < nk);
-                if (par && l > 1) {
-                    const int ps = side >> 1;
-                    const int ploc = ((ki >> 1) * ps + (yi >> 1)) * ps + (xi >> 1);
-                    par = prev[g * (per >> 3) + ploc] != 0;
+            for (int h = 0; h < (PAIRS + 31) / 32; ++h) {
+                const int pidx = lane + 32 * h;
+                if (pidx < PAIRS) {
+                    const int x = pidx % S, y = pidx / S;
+                    bool alive = true;
+#pragma unroll
+                    for (int l = 1; l <= DS; ++l) {
+                        const int sh = DS - l;
+                        const int t = tt + l;
+                        const int64_t w = (int64_t)1 << t;
+                        const int64_t off_t = (((int64_t)1 << (2 * t)) - 1) / 3;
+                        const int64_t i = ((int64_t)I0 << l) + (x >> sh);
+                        const int64_t k = ((int64_t)Kp << l) + (kk >> sh);
+                        const int64_t j = ((int64_t)J0 << l) + (y >> sh);
+                        const double a = pyrA[off_t + i * w + k];
+                        const double b = pyrB[off_t + k * w + j];
+                        const double p = a * b;
+                        const bool nz = a > 0.0 && b > 0.0;
+                        const bool ok = nz && p >= tau2;
+                        // count each tier-t triple once: at its first leaf
+                        const int rep = (1 << sh) - 1;
+                        if (alive && ((x | y | kk) & rep) == 0) {
+                            cand[l - 1] += 1;
+                            kept[l - 1] += ok ? 1 : 0;
+                            tie += (nz && p >= lo2 && p <= hi2) ? 1 : 0;
+                        }
+                        alive = alive && ok;
+                    }
+                    if (DS == 0) alive = true;   // the tier-d entry itself was kept
+                    if (alive) bits |= 1ull << (y * 8 + x);
                 }
-                if (par) {
-                    const int64_t i = (int64_t)I0 * side + xi;
-                    const int64_t k = (int64_t)klist[g0 + g] * side + ki;
-                    const int64_t j = (int64_t)J0 * side + yi;
-                    const double a = na[i * w + k];
-                    const double b = nb[k * w + j];
-                    const double p = a * b;
-                    const bool nz = a > 0.0 && b > 0.0;
-                    kp = (nz && p >= tau2) ? 1 : 0;
-                    cand[l - 1] += 1;
-                    kept[l - 1] += kp;
-                    tie += (nz && p >= lo2 && p <= hi2) ? 1 : 0;
-                }
-                cur[tid] = kp;
             }
-            __syncthreads();
-            unsigned char* tmp = prev;
-            prev = cur;
-            cur = tmp;
-        }
-        unsigned char* leaf = DS == 0 ? cur : prev;
-        // masks of the G * S leaf-level K values of this pass
-        if (tid < G * S) masks[tid] = 0ull;
-        __syncthreads();
-        if (tid < G * CUBE && leaf[tid]) {
-            const int g = tid / CUBE, loc = tid % CUBE;
-            const int xi = loc % S, yi = (loc / S) % S, ki = loc / (S * S);
-            atomicOr(&masks[g * S + ki], 1ull << (yi * 8 + xi));
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)bits);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(bits >> 32));
+            if (lane == 0) masks[item] = ((unsigned long long)hi << 32) | lo;
         }
         __syncthreads();
-        const unsigned long long m = tid < G * S ? masks[tid] : 0ull;
-        const uint32_t r = block_excl_scan(m ? 1u : 0u, warp_sums, &total_s);
-        if (m) {
-            const int g = tid / S, ki = tid % S;
-            pk[obase + written + r] = klist[g0 + g] * S + ki;
-            pm[obase + written + r] = m;
+        // phase 2: ordered compaction of the window's masks (ascending K)
+        for (int c0 = 0; c0 < kn * S; c0 += blockDim.x) {
+            const int i = c0 + tid;
+            const unsigned long long m = i < kn * S ? masks[i] : 0ull;
+            const uint32_t r = block_excl_scan(m ? 1u : 0u, warp_sums, &total_s);
+            if (m) {
+                const int g = i / S, kk = i % S;
+                pk[obase + written + r] = klist[kw + g] * S + kk;
+                pm[obase + written + r] = m;
+            }
+            written += total_s;
         }
-        written += total_s;
         __syncthreads();
     }
+    (void)wd;
     // statistics of the tiers below the tile node
 #pragma unroll
     for (int l = 0; l < DS; ++l) {
-        if (cand[l]) atomicAdd(&st_cand[l], cand[l]);
-        if (kept[l]) atomicAdd(&st_kept[l], kept[l]);
+        for (int o = 16; o > 0; o >>= 1) {
+            cand[l] += __shfl_xor_sync(0xffffffffu, cand[l], o);
+            kept[l] += __shfl_xor_sync(0xffffffffu, kept[l], o);
+        }
+        if (lane == 0 && cand[l]) atomicAdd(&st_cand[l], cand[l]);
+        if (lane == 0 && kept[l]) atomicAdd(&st_kept[l], kept[l]);
     }
-    if (tie) atomicAdd(&st_tie, tie);
+    for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
+    if (lane == 0 && tie) atomicAdd(&st_tie, tie);
     __syncthreads();
     if (tid == 0) {
         steps[u] = written;

@@ -10,7 +10,9 @@
 // the method, each leaf product is formed on its own (an FFMA chain over its
 // b values of k, starting from zero) and then added to the C block, in
 // ascending K: one rounding into C per kept product instead of one per k,
-// and a fixed order, so the result is deterministic.
+// and a fixed order, so the result is deterministic.  The running sum of the
+// C tile lives in shared memory (each thread owns its 8 x 8 patch there),
+// which keeps registers low enough for two blocks per SM.
 #include "spamm_internal.cuh"
 
 namespace spamm {
@@ -26,6 +28,7 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
                                                    const uint32_t* __restrict__ steps) {
     __shared__ __align__(16) float As[16][132];  // [k][row]
     __shared__ __align__(16) float Bs[16][128];  // [k][col]
+    extern __shared__ __align__(16) float accS[];  // [128][132] running C tile
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
     const uint32_t u = blockIdx.x;
     const int64_t R0 = (int64_t)(u / tps) * kTileRows;
@@ -34,11 +37,13 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
     const int ty = tid >> 4, tx = tid & 15;
     const int x = (8 * ty) / b, y = (8 * tx) / b;
     const int bit = y * 8 + x;
-    float acc[8][8];
+    constexpr int LDS = 132;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int i = 0; i < 8; ++i) {
+        float4* a = reinterpret_cast<float4*>(&accS[(8 * ty + i) * LDS + 8 * tx]);
+        a[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     const uint32_t ns = steps[u];
     const uint32_t base = off[u] * (uint32_t)S;
@@ -86,9 +91,14 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
         }
         if (mine) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
+            for (int i = 0; i < 8; ++i) {
+                float4* a = reinterpret_cast<float4*>(&accS[(8 * ty + i) * LDS + 8 * tx]);
+                float4 v0 = a[0], v1 = a[1];
+                v0.x += part[i][0]; v0.y += part[i][1]; v0.z += part[i][2]; v0.w += part[i][3];
+                v1.x += part[i][4]; v1.y += part[i][5]; v1.z += part[i][6]; v1.w += part[i][7];
+                a[0] = v0;
+                a[1] = v1;
+            }
         }
     }
 #pragma unroll
@@ -99,7 +109,7 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
         for (int j = 0; j < 8; ++j) {
             const int64_t gc = C0 + 8 * tx + j;
             if (gc < n) {
-                float v = alpha * acc[i][j];
+                float v = alpha * accS[(8 * ty + i) * LDS + 8 * tx + j];
                 if (beta != 0.f) v = fmaf(beta, C[gr * ldc + gc], v);
                 C[gr * ldc + gc] = v;
             }
@@ -110,7 +120,11 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
 cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                              float alpha, float beta, float* C, int64_t ldc) {
     const int tps = tiles_per_side(A);
-    k_leaf_simt<<<tps * tps, 256, 0, ctx->stream>>>(A->A, A->lda, B->A, B->lda, C, ldc, A->n,
+    const size_t dsm = sizeof(float) * 128 * 132;
+    cudaError_t e = cudaFuncSetAttribute(k_leaf_simt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dsm);
+    if (e != cudaSuccess) return e;
+    k_leaf_simt<<<tps * tps, 256, dsm, ctx->stream>>>(A->A, A->lda, B->A, B->lda, C, ldc, A->n,
                                                     A->b, tps, ctx->last_S, alpha, beta,
                                                     ctx->ctl, ctx->pool,
                                                     ctx->tile_off, ctx->tile_steps);

@@ -22,10 +22,22 @@
 // BF16X3 does the same with bfloat16 parts on kind::f16.  All accumulate in
 // FP32.
 //
+// Two-level accumulation: the tensor core's FP32 accumulation rounds less
+// carefully than an IEEE add, and a C tile can chain thousands of MMAs.  So
+// the MMAs of a tile are cut into chunks of at most kChunkIters K-chunks;
+// every chunk starts from a zeroed TMEM accumulator, and the epilogue warps
+// add the finished chunk into a master FP32 accumulator held in registers
+// (one row of 128 values per thread) with round-to-nearest adds.  Chunks are
+// added in ascending K, so the result stays deterministic.
+//
+// Tile order: consecutive work items walk down a group of kGroupRows tile
+// rows before moving one tile column right, so the tiles in flight at once
+// share A slices (same rows) and B slices (same columns) in L2.
+//
 // Roles (192 threads): warp 0 lane 0 issues the bulk copies into a ring of
 // shared-memory stages; warp 1 owns the TMEM allocation and its lane 0
 // issues the MMAs and commits; warps 2-5 move the double-buffered 128 x 128
-// accumulator out of TMEM, apply alpha/beta and store C.  Every wait on an
+// chunk accumulators out of TMEM, sum them, apply alpha/beta and store C.  Every wait on an
 // mbarrier gives up after one second, raises the timeout status and lets
 // the block drain its copies and MMAs, free TMEM and exit.
 #include <cuda_bf16.h>
@@ -36,6 +48,8 @@ namespace spamm {
 namespace {
 
 constexpr int kThreads = 192;
+constexpr int kChunkIters = 8;  // K-chunks of 16 per TMEM accumulation chunk
+constexpr int kGroupRows = 8;   // tile rows walked together (L2 reuse)
 constexpr uint32_t kZeroBytes = 4096;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
@@ -120,6 +134,20 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
 __device__ __forceinline__ uint32_t make_idesc(uint32_t ab, int M, int N) {
     return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+
+// Work item k -> tile index (row-major over tps x tps tiles), grouped by
+// kGroupRows tile rows.
+__device__ __forceinline__ int tile_at(int k, int tps) {
+    const int span = kGroupRows * tps;
+    const int g = k / span;
+    const int rows = min(kGroupRows, tps - g * kGroupRows);
+    const int w = k - g * span;
+    return (g * kGroupRows + w % rows) * tps + w / rows;
+}
+
+__device__ __forceinline__ uint32_t chunks_of(uint32_t iters) {
+    return iters == 0 ? 1u : (iters + kChunkIters - 1) / kChunkIters;
 }
 
 template <int PREC>
@@ -241,7 +269,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
         if (lane == 0) {
             unsigned long long it = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < p.tiles && ok; u += gridDim.x) {
+            for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
+                const int u = tile_at(k, p.tps);
                 const int64_t srow = (int64_t)(u / p.tps) * TL;
                 const int64_t scol = (int64_t)(u % p.tps) * TL;
                 const uint32_t ns = p.steps[u];
@@ -280,26 +309,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
             unsigned long long it = 0;
-            uint32_t tcount = 0;
+            uint32_t ccount = 0;  // chunks issued so far (selects the TMEM buffer)
             bool ok = true;
             const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
             const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
-            for (int u = blockIdx.x; u < p.tiles && ok; u += gridDim.x, ++tcount) {
-                const uint32_t ab = tcount & 1;
-                const uint32_t aph = (tcount >> 1) & 1;
-                if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t dacc = tmem + ab * 128;
-                // clear the accumulator: 0 * 0 with the input accumulator off
-                mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 128), dis0, 0u);
+            for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
+                const int u = tile_at(k, p.tps);
                 const uint32_t ns = p.steps[u];
                 const uint64_t sb = (uint64_t)p.off[u] * p.S;
-                for (uint32_t st = 0; st < ns && ok; ++st) {
-                    const unsigned long long mask = pm[sb + st];
-                    for (int kc = 0; kc < CHUNKS; ++kc, ++it) {
+                const uint32_t iters = ns * CHUNKS;
+                const uint32_t nch = chunks_of(iters);
+                uint32_t st = 0;
+                int kc = 0;
+                for (uint32_t c = 0; c < nch && ok; ++c, ++ccount) {
+                    const uint32_t ab = ccount & 1;
+                    const uint32_t aph = (ccount >> 1) & 1;
+                    if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dacc = tmem + ab * 128;
+                    // clear the chunk accumulator: 0 * 0 with the input accumulator off
+                    mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 128), dis0, 0u);
+                    const uint32_t last = min(iters, (c + 1) * kChunkIters);
+                    for (uint32_t i = c * kChunkIters; i < last && ok; ++i, ++it) {
+                        const unsigned long long mask = pm[sb + st];
                         const int s = (int)(it % ST);
                         const uint32_t ph = (uint32_t)((it / ST) & 1);
                         if (!wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status)) {
@@ -320,7 +355,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                                 continue;
                             }
                             int len = 1;
-                            while (y + len < TL && ((uint32_t)(mask >> (8 * (y + len))) & 0xFFu) == xm)
+                            while (y + len < TL &&
+                                   ((uint32_t)(mask >> (8 * (y + len))) & 0xFFu) == xm)
                                 ++len;
                             uint32_t dis[4];
 #pragma unroll
@@ -344,7 +380,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                                 const uint64_t bh = make_desc(b_hi + boff + koff, 128, T::kSBO);
                                 if (PREC != SPAMM_PREC_TF32) {
                                     const uint64_t al = make_desc(a_lo + koff, 128, T::kSBO);
-                                    const uint64_t bl = make_desc(b_lo + boff + koff, 128, T::kSBO);
+                                    const uint64_t bl =
+                                        make_desc(b_lo + boff + koff, 128, T::kSBO);
                                     mma<PREC>(d, al, bh, idesc, dis, 1u);
                                     mma<PREC>(d, ah, bl, idesc, dis, 1u);
                                 }
@@ -353,9 +390,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                             y += len;
                         }
                         tc_commit(smem_u32(&bar_empty[s]));
+                        if (++kc == CHUNKS) {
+                            kc = 0;
+                            ++st;
+                        }
                     }
+                    if (ok) tc_commit(smem_u32(&bar_accf[ab]));
                 }
-                if (ok) tc_commit(smem_u32(&bar_accf[ab]));
             }
             // drain: every MMA issued so far has completed before TMEM is freed
             tc_commit(smem_u32(&bar_drain));
@@ -364,55 +405,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     } else {
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        uint32_t tcount = 0;
-        for (int u = blockIdx.x; u < p.tiles; u += gridDim.x, ++tcount) {
-            const uint32_t ab = tcount & 1;
-            const uint32_t aph = (tcount >> 1) & 1;
-            if (!wait_bar(smem_u32(&bar_accf[ab]), aph, &abort_flag, status)) break;
-            tc_fence_after();
+        uint32_t ccount = 0;
+        bool ok = true;
+        for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
+            const int u = tile_at(k, p.tps);
+            const uint32_t nch = chunks_of(p.steps[u] * CHUNKS);
+            float master[128];
+#pragma unroll
+            for (int v = 0; v < 128; ++v) master[v] = 0.f;
+            for (uint32_t c = 0; c < nch; ++c, ++ccount) {
+                const uint32_t ab = ccount & 1;
+                const uint32_t aph = (ccount >> 1) & 1;
+                if (!wait_bar(smem_u32(&bar_accf[ab]), aph, &abort_flag, status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + ab * 128;
+#pragma unroll
+                for (int cc = 0; cc < 128; cc += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)cc, r);
+#pragma unroll
+                    for (int v = 0; v < 32; ++v) master[cc + v] += __uint_as_float(r[v]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
+            }
+            if (!ok) break;
             const int64_t row = (int64_t)(u / p.tps) * 128 + q * 32 + lane;
             const int64_t col0 = (int64_t)(u % p.tps) * 128;
-            float* crow = p.C + row * p.ldc;
-            const bool vec = ((p.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0);
-#pragma unroll 1
-            for (int c = 0; c < 128; c += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab * 128 + (uint32_t)c, r);
-                if (row < p.n) {
-                    const int64_t cb = col0 + c;
-                    if (vec && cb + 32 <= p.n) {
+            if (row < p.n) {
+                float* crow = p.C + row * p.ldc + col0;
+                const bool vec = ((p.ldc & 3) == 0) &&
+                                 ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0) &&
+                                 (col0 + 128 <= p.n);
+                if (vec) {
 #pragma unroll
-                        for (int v = 0; v < 8; ++v) {
-                            float4 o;
-                            o.x = p.alpha * __uint_as_float(r[4 * v + 0]);
-                            o.y = p.alpha * __uint_as_float(r[4 * v + 1]);
-                            o.z = p.alpha * __uint_as_float(r[4 * v + 2]);
-                            o.w = p.alpha * __uint_as_float(r[4 * v + 3]);
-                            float4* dst = reinterpret_cast<float4*>(crow + cb + 4 * v);
-                            if (p.beta != 0.f) {
-                                const float4 old = *dst;
-                                o.x = fmaf(p.beta, old.x, o.x);
-                                o.y = fmaf(p.beta, old.y, o.y);
-                                o.z = fmaf(p.beta, old.z, o.z);
-                                o.w = fmaf(p.beta, old.w, o.w);
-                            }
-                            *dst = o;
+                    for (int v = 0; v < 32; ++v) {
+                        float4 o = make_float4(p.alpha * master[4 * v], p.alpha * master[4 * v + 1],
+                                               p.alpha * master[4 * v + 2],
+                                               p.alpha * master[4 * v + 3]);
+                        float4* dst = reinterpret_cast<float4*>(crow) + v;
+                        if (p.beta != 0.f) {
+                            const float4 old = *dst;
+                            o.x = fmaf(p.beta, old.x, o.x);
+                            o.y = fmaf(p.beta, old.y, o.y);
+                            o.z = fmaf(p.beta, old.z, o.z);
+                            o.w = fmaf(p.beta, old.w, o.w);
                         }
-                    } else {
+                        *dst = o;
+                    }
+                } else {
 #pragma unroll
-                        for (int v = 0; v < 32; ++v) {
-                            if (cb + v < p.n) {
-                                float o = p.alpha * __uint_as_float(r[v]);
-                                if (p.beta != 0.f) o = fmaf(p.beta, crow[cb + v], o);
-                                crow[cb + v] = o;
-                            }
+                    for (int v = 0; v < 128; ++v) {
+                        if (col0 + v < p.n) {
+                            float o = p.alpha * master[v];
+                            if (p.beta != 0.f) o = fmaf(p.beta, crow[v], o);
+                            crow[v] = o;
                         }
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
         }
     }
 

@@ -277,7 +277,7 @@ def test_algebraic_pm1_counts_are_sign_free():
             assert _as_set(O.cull_recursive(pa, pa, d, tau)[0]) == ref
 
 
-# ------------------------------------------------ Morton, Sec. III.E.1-2
+# ------------------------------------------------ Morton, Sec. III.D.1-2
 
 def test_morton_hand_values():
     # l = sum_m i_m 2^(2m+1) + j_m 2^(2m)
