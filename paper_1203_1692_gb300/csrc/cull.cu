@@ -32,8 +32,7 @@
 namespace spamm {
 
 __global__ void k_cull_root(const double* __restrict__ pa, const double* __restrict__ pb,
-                            double tau2, double lo2, double hi2, DevCtl* ctl,
-                            uint64_t* __restrict__ pool) {
+                            Thresh th, DevCtl* ctl, uint64_t* __restrict__ pool) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double na = pa[0], nb = pb[0];
     ctl->tier_off[0] = 0;
@@ -44,17 +43,17 @@ __global__ void k_cull_root(const double* __restrict__ pa, const double* __restr
         ctl->tier_count[0] = 0;
         return;
     }
-    const double p = na * nb;
-    const bool keep = na > 0.0 && nb > 0.0 && p >= tau2;
-    if (na > 0.0 && nb > 0.0 && p >= lo2 && p <= hi2) ctl->tie_band += 1;
+    bool tie;
+    const bool keep = spamm_keep(na, nb, th, &tie);
+    if (tie) ctl->tie_band += 1;
     ctl->tier_count[0] = keep ? 1 : 0;
     if (keep) pool[0] = pack_triple(0, 0, 0);
 }
 
 // Expand tier t into tier t + 1.  na/nb are the tier-(t+1) norm grids.
 __global__ void __launch_bounds__(256) k_cull_tier(int t, const double* __restrict__ na,
-                                                   const double* __restrict__ nb, double tau2,
-                                                   double lo2, double hi2, DevCtl* ctl,
+                                                   const double* __restrict__ nb, Thresh th,
+                                                   DevCtl* ctl,
                                                    uint64_t* __restrict__ pool,
                                                    unsigned long long cap) {
     const unsigned long long in_off = ctl->tier_off[t];
@@ -81,12 +80,9 @@ __global__ void __launch_bounds__(256) k_cull_tier(int t, const double* __restri
             const uint64_t i = 2ull * tri_I(par) + ((q >> 2) & 1);
             const uint64_t k = 2ull * tri_K(par) + ((q >> 1) & 1);
             const uint64_t j = 2ull * tri_J(par) + (q & 1);
-            const double a = na[i * w + k];
-            const double b = nb[k * w + j];
-            const double p = a * b;
-            const bool nz = a > 0.0 && b > 0.0;
-            keep = nz && p >= tau2;
-            tie += (nz && p >= lo2 && p <= hi2) ? 1 : 0;
+            bool tb;
+            keep = spamm_keep(na[i * w + k], nb[k * w + j], th, &tb);
+            tie += tb ? 1 : 0;
             child = pack_triple(i, k, j);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -114,12 +110,9 @@ __global__ void k_cull_finish(int tt, DevCtl* ctl, unsigned long long cap) {
 cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
                         int tt) {
     cudaStream_t s = ctx->stream;
-    const double tau2 = tau * tau;
-    const double rel = ctx->cfg.tie_rel;
-    const double lo2 = tau2 * (1.0 - rel) * (1.0 - rel);
-    const double hi2 = tau2 * (1.0 + rel) * (1.0 + rel);
+    const Thresh th = make_thresh(tau, ctx->cfg.tie_rel);
     const unsigned long long cap = (unsigned long long)ctx->pool_words;
-    k_cull_root<<<1, 32, 0, s>>>(A->pyr, B->pyr, tau2, lo2, hi2, ctx->ctl, ctx->pool);
+    k_cull_root<<<1, 32, 0, s>>>(A->pyr, B->pyr, th, ctx->ctl, ctx->pool);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int blocks = ctx->sm_count * 4;
@@ -131,8 +124,8 @@ cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B
             const int64_t cand = (int64_t)1 << (3 * (t + 1));
             g = (int)std::min<int64_t>(blocks, (cand + 255) / 256);
         }
-        k_cull_tier<<<g, 256, 0, s>>>(t, A->pyr + off, B->pyr + off, tau2, lo2, hi2, ctx->ctl,
-                                      ctx->pool, cap);
+        k_cull_tier<<<g, 256, 0, s>>>(t, A->pyr + off, B->pyr + off, th, ctx->ctl, ctx->pool,
+                                      cap);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -262,8 +255,8 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 // the masks of a window of K values are then compacted in ascending K.
 template <int DS>
 __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restrict__ pyrA,
-                                                   const double* __restrict__ pyrB, double tau2,
-                                                   double lo2, double hi2, DevCtl* ctl,
+                                                   const double* __restrict__ pyrB, Thresh th,
+                                                   DevCtl* ctl,
                                                    uint64_t* __restrict__ pool,
                                                    const uint32_t* __restrict__ off,
                                                    uint32_t* __restrict__ steps, int tps) {
@@ -340,17 +333,15 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
                         const int64_t i = ((int64_t)I0 << l) + (x >> sh);
                         const int64_t k = ((int64_t)Kp << l) + (kk >> sh);
                         const int64_t j = ((int64_t)J0 << l) + (y >> sh);
-                        const double a = pyrA[off_t + i * w + k];
-                        const double b = pyrB[off_t + k * w + j];
-                        const double p = a * b;
-                        const bool nz = a > 0.0 && b > 0.0;
-                        const bool ok = nz && p >= tau2;
+                        bool tb;
+                        const bool ok = spamm_keep(pyrA[off_t + i * w + k],
+                                                   pyrB[off_t + k * w + j], th, &tb);
                         // count each tier-t triple once: at its first leaf
                         const int rep = (1 << sh) - 1;
                         if (alive && ((x | y | kk) & rep) == 0) {
                             cand[l - 1] += 1;
                             kept[l - 1] += ok ? 1 : 0;
-                            tie += (nz && p >= lo2 && p <= hi2) ? 1 : 0;
+                            tie += tb ? 1 : 0;
                         }
                         alive = alive && ok;
                     }
@@ -410,10 +401,7 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
     const int ds = A->d - tt;
     const int S = 1 << ds;
     const unsigned long long cap = (unsigned long long)ctx->pool_words;
-    const double tau2 = tau * tau;
-    const double rel = ctx->cfg.tie_rel;
-    const double lo2 = tau2 * (1.0 - rel) * (1.0 - rel);
-    const double hi2 = tau2 * (1.0 + rel) * (1.0 + rel);
+    const Thresh th = make_thresh(tau, ctx->cfg.tie_rel);
     cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(uint32_t) * tiles, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tile_fill, 0, sizeof(uint32_t) * tiles, s);
     if (e != cudaSuccess) return e;
@@ -429,7 +417,7 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
         if (dsm > 48 * 1024)                                                                   \
             cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)dsm);                                                    \
-        k_tile_cull<DSV><<<tiles, 512, dsm, s>>>(tt, A->pyr, B->pyr, tau2, lo2, hi2, ctx->ctl, \
+        k_tile_cull<DSV><<<tiles, 512, dsm, s>>>(tt, A->pyr, B->pyr, th, ctx->ctl,             \
                                                  ctx->pool, ctx->tile_off, ctx->tile_steps,    \
                                                  tps);                                         \
     } while (0)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <string>
 
 #include "../../include/spamm.h"
@@ -56,7 +58,45 @@ __device__ inline unsigned long long stored_count(const DevCtl* c, int t, unsign
     return n < room ? n : room;
 }
 
-struct Tree;
+// Squared-form thresholds of the SpAMM condition: keep iff fl(nA2 * nB2) >=
+// tau2 (FP64) with both norms non-zero; the tie band is [lo2, hi2].
+struct Thresh {
+    double tau2, lo2, hi2;
+    int e_lo, e_hi;  // biased FP64 exponents of lo2 and hi2
+};
+
+// Exact keep decision for finite non-negative squared norms a, b, and the
+// tie-band flag.  On GB300 the FP64 pipe is narrow, so the exponent fields
+// settle every pair whose product lies clearly outside [lo2, hi2] with
+// integer operations: 2^(s-1023) <= a*b < 2^(s+1-1023+1) for s = ea + eb -
+// 1023.  Only products within a factor of about four of the band are formed
+// in FP64, exactly as the oracle forms them.
+__device__ __forceinline__ bool spamm_keep(double a, double b, const Thresh& th, bool* tie) {
+    const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+    *tie = false;
+    if (ua == 0ull || ub == 0ull) return false;  // a NULL block never multiplies
+    const int s = (int)(ua >> 52) + (int)(ub >> 52) - 1023;
+    if (s >= 1 && s >= th.e_hi + 1) return true;  // fl(a*b) >= 2^(s-1023) > hi2 >= tau2
+    if (s + 2 < th.e_lo) return false;            // fl(a*b) <= 2^(s+2-1023) < lo2 <= tau2
+    const double p = a * b;
+    *tie = p >= th.lo2 && p <= th.hi2;
+    return p >= th.tau2;
+}
+
+inline Thresh make_thresh(double tau, double rel) {
+    Thresh t;
+    t.tau2 = tau * tau;
+    t.lo2 = t.tau2 * (1.0 - rel) * (1.0 - rel);
+    t.hi2 = t.tau2 * (1.0 + rel) * (1.0 + rel);
+    unsigned long long ul, uh;
+    static_assert(sizeof(double) == 8, "");
+    memcpy(&ul, &t.lo2, 8);
+    memcpy(&uh, &t.hi2, 8);
+    t.e_lo = (int)(ul >> 52);
+    t.e_hi = (int)(uh >> 52);
+    return t;
+}
 
 }  // namespace spamm
 
