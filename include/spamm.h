@@ -188,6 +188,29 @@ spamm_status spamm_stats(spamm_ctx *ctx, spamm_stats_t *out);
  * written).  Synchronises. */
 spamm_status spamm_triples(spamm_ctx *ctx, int32_t *host_out, int64_t cap, int64_t *count);
 
+/* No counterpart in the paper: a convenience for callers that cannot
+ * allocate device memory (a host framework or plugin that owns all device
+ * memory through its own allocator or memory cap, or a loop that must not
+ * pay cudaMalloc's implicit synchronisation).
+ * Computes the same C = alpha * SpAMM(A, B; tau) + beta * C as
+ * spamm_build_norms + spamm_multiply with leaf 16 and SPAMM_PREC_FP32, on
+ * DEVICE matrices (row-major, lda/ldb/ldc >= n) and the cudaStream_t
+ * `stream`, without allocating anything: every scratch buffer lives in one
+ * static 6 MiB device array that each GPU loading this library holds until
+ * exit, sized for the worst case at n <= 4096.  The first call on each
+ * device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each
+ * call clears what must start at zero); calls that overlap on the GPU race
+ * on it, so order them on one stream.  Asynchronous; when status_dev (a
+ * device uint32) is not NULL it receives the device status word
+ * (0 = OK, 2 = non-finite input).  Returns INVALID_ARG (NULL pointer,
+ * n <= 0, leading dimension < n, tau < 0 or not finite), UNSUPPORTED
+ * (n > 4096: beyond the static scratch), CUDA. */
+spamm_status spamm_multiply_static(const float *A, int64_t lda, const float *B, int64_t ldb,
+                                   int64_t n, double tau, float alpha, float beta, float *C,
+                                   int64_t ldc, void *stream, uint32_t *status_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,8 @@ SIGNATURES = {
     "spamm_multiply_host": (_i32, [_vp, _vp, _vp, _i64, _dbl, _flt, _flt, _vp]),
     "spamm_stats": (_i32, [_vp, ctypes.POINTER(spamm_stats_t)]),
     "spamm_triples": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "spamm_multiply_static": (_i32, [_vp, _i64, _vp, _i64, _i64, _dbl, _flt, _flt, _vp, _i64,
+                                     _vp, _vp]),
 }
 
 _lib = None
@@ -190,3 +192,13 @@ def spamm_triples(ctx, out_ptr: int, cap: int) -> int:
     cnt = _i64()
     check(lib().spamm_triples(ctx, _vp(out_ptr), cap, ctypes.byref(cnt)), ctx)
     return cnt.value
+
+
+def spamm_multiply_static(A_ptr: int, lda: int, B_ptr: int, ldb: int, n: int, tau: float,
+                          alpha: float, beta: float, C_ptr: int, ldc: int, stream: int,
+                          status_ptr: int = 0) -> None:
+    """The allocation-free FP32 product (all scratch in a static device
+    array, n <= 4096); see include/spamm.h."""
+    check(lib().spamm_multiply_static(_vp(A_ptr), lda, _vp(B_ptr), ldb, n, float(tau),
+                                      float(alpha), float(beta), _vp(C_ptr), ldc,
+                                      _vp(stream), _vp(status_ptr) if status_ptr else None))
