@@ -56,18 +56,22 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="spamm", choices=["spamm", "reference"])
     p.add_argument("--workload", default="water7500", choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "tf32", "bf16x3"])
+    p.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "tf32", "bf16x3"])
     p.add_argument("--leaf", type=int, default=16)
     p.add_argument("--tau", default="auto")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--sites", type=int, default=300,
+                   help="water-like workload: number of sites (n = 25 x sites)")
+    p.add_argument("--quick", action="store_true",
+                   help="time the SpAMM step only at a fixed --tau (for profiling)")
     return p.parse_args()
 
 
-def make_matrix(name):
+def make_matrix(name, sites=300):
     if name == "water7500":
-        return gen.water_like(300, 25, 0.1, seed=0)
+        return gen.water_like(sites, 25, 0.1, seed=0)
     if name == "exp1024":
         return gen.exp_decay(1024, 0.9, seed=0)
     return gen.algebraic_decay(16384, seed=0)
@@ -185,6 +189,35 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ GPU arm
 
+def run_quick(args, P, A, n, b, stream):
+    """Time the SpAMM step alone at a fixed tau (no reference products)."""
+    import torch
+    tau = 1e-4 if args.tau == "auto" else float(args.tau)
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+    tree = ctx.build_norms(A)
+    C = torch.empty_like(A)
+    ctx.multiply(tree, tree, tau, C=C)
+    ctx.set_checked(False)
+    for _ in range(args.warmup):
+        tree.rebuild(A)
+        ctx.multiply(tree, tree, tau, C=C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tree.rebuild(A)
+        ctx.multiply(tree, tree, tau, C=C)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "quick", "n": n, "leaf": b, "tau": tau,
+                      "precision": args.precision, "ms_per_step": ms,
+                      "kept_tflops": st["kept_flops"] / (ms * 1e-3) / 1e12,
+                      "ms_symbolic": st["ms_symbolic"], "ms_numeric": st["ms_numeric"],
+                      "leaf_triples": st["leaf_triples"]}), flush=True)
+
+
 def kernels_per_step(d, leaf):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
@@ -209,11 +242,14 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    A_h = make_matrix(args.workload)
+    A_h = make_matrix(args.workload, args.sites)
     n = A_h.shape[0]
     b = args.leaf
     A = torch.from_numpy(A_h).to(dev)
     stream = torch.cuda.current_stream()
+    if args.quick:
+        run_quick(args, P, A, n, b, stream)
+        return
 
     # --- equal-error tau against cuBLAS SGEMM (not timed) ----------------
     torch.backends.cuda.matmul.allow_tf32 = False

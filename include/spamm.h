@@ -196,7 +196,7 @@ spamm_status spamm_triples(spamm_ctx *ctx, int32_t *host_out, int64_t cap, int64
  * spamm_build_norms + spamm_multiply with leaf 16 and SPAMM_PREC_FP32, on
  * DEVICE matrices (row-major, lda/ldb/ldc >= n) and the cudaStream_t
  * `stream`, without allocating anything: every scratch buffer lives in one
- * static 6 MiB device array that each GPU loading this library holds until
+ * static 8 MiB device array that each GPU loading this library holds until
  * exit, sized for the worst case at n <= 4096.  The first call on each
  * device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

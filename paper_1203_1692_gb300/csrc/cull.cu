@@ -13,18 +13,18 @@
 // host round trip between tiers.  A frontier that does not fit is truncated
 // and the overflow flag is raised.
 //
-// Grouping.  A C tile is 128 x 128, TL = 128 / b = 2^s leaves per side, which
-// is exactly one quadtree node at tier tt = d - s.  The tier-by-tier cull
-// therefore stops at tier tt; its triples (I', K', J') are counted per tile
-// (I', J'), scanned and scattered, and one block per tile finishes the cull
-// of the last s tiers inside its 2^s x 2^s x 2^s sub-cube for every K' in
-// ascending order: level by level in shared memory, a child is tested only
-// if its parent survived, with the same FP64 predicate.  The surviving leaf
-// triples of one (tile, K) are emitted as one step (K, 64-bit mask, bit
-// y * 8 + x for row leaf x and column leaf y of the tile), compacted with a
-// ballot into a coalesced list in ascending K.  This is the leaf-triple list
-// in tile-compressed form; the leaf kernels walk it, which fixes the
-// accumulation order of every C block.
+// Grouping.  A C tile is 128 rows x 256 columns: with TL = 128 / b = 2^s it is
+// two horizontally adjacent quadtree nodes of tier tt = d - s (its two
+// halves).  The tier-by-tier cull therefore stops at tier tt; its triples
+// (I', K', J') are counted per tile (I', J' / 2), scanned and scattered as
+// entries (K', half), and one block per tile finishes the cull of the last s
+// tiers inside the 2^s x 2^s x 2^s sub-cubes of every K' in ascending order:
+// a leaf triple survives iff every ancestor below the tile node does, with
+// the same FP64 predicate.  The surviving leaf triples of one (tile, K) are
+// emitted as one step (K, two 64-bit masks, bit y * 8 + x for row leaf x and
+// column leaf y of each half), compacted into a coalesced list in ascending
+// K.  This is the leaf-triple list in tile-compressed form; the leaf kernels
+// walk it, which fixes the accumulation order of every C block.
 #include <algorithm>
 
 #include "spamm_internal.cuh"
@@ -135,24 +135,24 @@ cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B
 
 // ------------------------------------------------------------- grouping
 
-__device__ inline uint32_t tile_of(uint64_t tri, int tps) {
-    return tri_I(tri) * (uint32_t)tps + tri_J(tri);
+__device__ inline uint32_t tile_of(uint64_t tri, int tc) {
+    return tri_I(tri) * (uint32_t)tc + (tri_J(tri) >> 1);
 }
 
 __global__ void __launch_bounds__(256) k_group_count(int tt, DevCtl* ctl,
-                                                     const uint64_t* __restrict__ pool, int tps,
+                                                     const uint64_t* __restrict__ pool, int tc,
                                                      uint32_t* __restrict__ tile_cnt) {
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
     const unsigned long long off = ctl->tier_off[tt];
     const unsigned long long m = ctl->tier_count[tt];
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < m;
          g += (unsigned long long)gridDim.x * blockDim.x)
-        atomicAdd(&tile_cnt[tile_of(pool[off + g], tps)], 1u);
+        atomicAdd(&tile_cnt[tile_of(pool[off + g], tc)], 1u);
 }
 
 // Exclusive scan of the tile counts (single block), and the pool layout of
 // the grouped arrays behind the tier-tt frontier: entries (u32, one per
-// tier-tt triple), then step K (u32) and step masks (u64), S per entry.
+// tier-tt triple), then step K (u32) and step masks (2 x u64), S per entry.
 __global__ void __launch_bounds__(1024) k_group_scan(int tt, int S, DevCtl* ctl,
                                                      unsigned long long cap,
                                                      const uint32_t* __restrict__ cnt,
@@ -195,14 +195,14 @@ __global__ void __launch_bounds__(1024) k_group_scan(int tt, int S, DevCtl* ctl,
         ctl->ent_off = end;
         ctl->pk_off = end + (m + 1) / 2;
         ctl->pm_off = ctl->pk_off + (ms + 1) / 2;
-        ctl->need_words = ctl->pm_off + ms;
+        ctl->need_words = ctl->pm_off + 2 * ms;
         if (ctl->need_words > cap || m >= 0xffffffffull / (unsigned long long)S)
             ctl->status |= ST_OVERFLOW;
     }
 }
 
 __global__ void __launch_bounds__(256) k_group_scatter(int tt, DevCtl* ctl,
-                                                       uint64_t* __restrict__ pool, int tps,
+                                                       uint64_t* __restrict__ pool, int tc,
                                                        const uint32_t* __restrict__ off,
                                                        uint32_t* __restrict__ fill) {
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(256) k_group_scatter(int tt, DevCtl* ctl,
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < m;
          g += (unsigned long long)gridDim.x * blockDim.x) {
         const uint64_t tri = pool[loff + g];
-        const uint32_t u = tile_of(tri, tps);
-        ent[off[u] + atomicAdd(&fill[u], 1u)] = tri_K(tri);
+        const uint32_t u = tile_of(tri, tc);
+        ent[off[u] + atomicAdd(&fill[u], 1u)] = (tri_K(tri) << 1) | (tri_J(tri) & 1u);
     }
 }
 
@@ -244,28 +244,28 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 }
 
 // Finish the cull of one tile's sub-cubes (DS = d - tt tiers below the tile
-// node) and emit its (K, mask) steps in ascending K.  blockDim = 512.
+// nodes) and emit its (K, masks) steps in ascending K.  blockDim = 512.
 //
-// One warp evaluates one (K', kk) slice of a sub-cube: the S x S leaf pairs
-// (x, y) of leaf column K = K' * S + kk.  A lane tests its leaf triples and
-// all their ancestors below the tile node with the FP64 predicate (a leaf
-// survives iff every ancestor does, which is the level-by-level cull), and
-// the warp ORs the survivors into the 64-bit mask of that K.  Slices are
-// independent, so no block-wide synchronisation is needed between tiers;
-// the masks of a window of K values are then compacted in ascending K.
+// One warp evaluates one (K', kk) slice: the S x S leaf pairs (x, y) of
+// leaf column K = K' * S + kk in each half whose node has the entry
+// (K', half).  A lane tests its leaf triples and all their ancestors below
+// the tile node with the FP64 predicate (a leaf survives iff every ancestor
+// does, which is the level-by-level cull), and the warp ORs the survivors
+// into the two 64-bit masks of that K.  Slices are independent, so no
+// block-wide synchronisation is needed between tiers; the masks of a window
+// of K values are then compacted in ascending K.
 template <int DS>
 __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restrict__ pyrA,
                                                    const double* __restrict__ pyrB, Thresh th,
-                                                   DevCtl* ctl,
-                                                   uint64_t* __restrict__ pool,
+                                                   DevCtl* ctl, uint64_t* __restrict__ pool,
                                                    const uint32_t* __restrict__ off,
-                                                   uint32_t* __restrict__ steps, int tps) {
+                                                   uint32_t* __restrict__ steps, int tc) {
     constexpr int S = 1 << DS;               // K leaves per tier-tt K'
-    constexpr int PAIRS = S * S;             // leaf pairs (x, y) of one slice
-    constexpr int WIN = 4096;                // masks per window (32 KB)
+    constexpr int PAIRS = S * S;             // leaf pairs (x, y) of one slice and half
+    constexpr int WIN = 2048;                // steps per window (32 KB of masks)
     constexpr int KPW = WIN / S;             // K' per window
-    extern __shared__ uint32_t dyn[];        // bitmap of K' (2^tt bits), then the K' list
-    __shared__ unsigned long long masks[WIN];
+    extern __shared__ uint32_t dyn[];        // K' bitmaps of both halves, then the K' list
+    __shared__ unsigned long long masks[WIN][2];
     __shared__ uint32_t warp_sums[16], total_s;
     __shared__ unsigned long long st_cand[4], st_kept[4], st_tie;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
@@ -276,26 +276,28 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
         return;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t I0 = u / tps, J0 = u % tps;
+    const uint32_t I0 = u / tc, Jp = u % tc;
     const uint32_t* ent = reinterpret_cast<const uint32_t*>(pool + ctl->ent_off);
     uint32_t* pk = reinterpret_cast<uint32_t*>(pool + ctl->pk_off);
     unsigned long long* pm = reinterpret_cast<unsigned long long*>(pool + ctl->pm_off);
     const int words = ((1 << tt) + 31) >> 5;
-    uint32_t* bitmap = dyn;
-    uint32_t* klist = dyn + words;
-    for (int w = tid; w < words; w += blockDim.x) bitmap[w] = 0u;
+    uint32_t* bm0 = dyn;
+    uint32_t* bm1 = dyn + words;
+    uint32_t* klist = dyn + 2 * words;
+    for (int w = tid; w < 2 * words; w += blockDim.x) dyn[w] = 0u;
     if (tid < 4) st_cand[tid] = st_kept[tid] = 0ull;
     if (tid == 0) st_tie = 0ull;
     __syncthreads();
     for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
-        const uint32_t k = ent[e];
-        atomicOr(&bitmap[k >> 5], 1u << (k & 31));
+        const uint32_t v = ent[e], k = v >> 1;
+        atomicOr(&((v & 1u) ? bm1 : bm0)[k >> 5], 1u << (k & 31));
     }
     __syncthreads();
-    // ascending K' list
+    // ascending list of the K' present in either half
+    int nk = 0;
     for (int w0 = 0, base = 0; w0 < words; w0 += blockDim.x) {
         const int w = w0 + tid;
-        const uint32_t bits = w < words ? bitmap[w] : 0u;
+        const uint32_t bits = w < words ? (bm0[w] | bm1[w]) : 0u;
         const uint32_t r = block_excl_scan(__popc(bits), warp_sums, &total_s);
         uint32_t b = bits, pos = base + r;
         while (b) {
@@ -304,25 +306,29 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
             klist[pos++] = (uint32_t)(w * 32 + q);
         }
         base += total_s;
+        nk = base;
         __syncthreads();
     }
-    const int nk = (int)(e1 - e0);
     const uint32_t obase = e0 * S;
     uint32_t written = 0;
     unsigned long long cand[4] = {0, 0, 0, 0}, kept[4] = {0, 0, 0, 0}, tie = 0;
-    const int64_t wd = (int64_t)1 << (tt + DS);
     for (int kw = 0; kw < nk; kw += KPW) {
         const int kn = min(KPW, nk - kw);
-        // phase 1: one warp per (K', kk) slice
+        // phase 1: one warp per (K', kk) slice, both halves
         for (int item = warp; item < kn * S; item += 16) {
             const int g = item / S, kk = item % S;
             const uint32_t Kp = klist[kw + g];
-            unsigned long long bits = 0ull;
+            const bool has0 = ((bm0[Kp >> 5] >> (Kp & 31)) & 1u) != 0;
+            const bool has1 = ((bm1[Kp >> 5] >> (Kp & 31)) & 1u) != 0;
+            unsigned long long bits0 = 0ull, bits1 = 0ull;
 #pragma unroll
-            for (int h = 0; h < (PAIRS + 31) / 32; ++h) {
-                const int pidx = lane + 32 * h;
-                if (pidx < PAIRS) {
-                    const int x = pidx % S, y = pidx / S;
+            for (int hh = 0; hh < (2 * PAIRS + 31) / 32; ++hh) {
+                const int pidx = lane + 32 * hh;
+                const int half = pidx / PAIRS;
+                if (pidx < 2 * PAIRS && (half ? has1 : has0)) {
+                    const int q = pidx % PAIRS;
+                    const int x = q % S, y = q / S;
+                    const uint32_t J0 = Jp * 2 + half;
                     bool alive = true;
 #pragma unroll
                     for (int l = 1; l <= DS; ++l) {
@@ -345,31 +351,41 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
                         }
                         alive = alive && ok;
                     }
-                    if (DS == 0) alive = true;   // the tier-d entry itself was kept
-                    if (alive) bits |= 1ull << (y * 8 + x);
+                    if (alive) {
+                        if (half) bits1 |= 1ull << (y * 8 + x);
+                        else bits0 |= 1ull << (y * 8 + x);
+                    }
                 }
             }
-            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)bits);
-            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(bits >> 32));
-            if (lane == 0) masks[item] = ((unsigned long long)hi << 32) | lo;
+            const uint32_t lo0 = __reduce_or_sync(0xffffffffu, (uint32_t)bits0);
+            const uint32_t hi0 = __reduce_or_sync(0xffffffffu, (uint32_t)(bits0 >> 32));
+            const uint32_t lo1 = __reduce_or_sync(0xffffffffu, (uint32_t)bits1);
+            const uint32_t hi1 = __reduce_or_sync(0xffffffffu, (uint32_t)(bits1 >> 32));
+            if (lane == 0) {
+                masks[item][0] = ((unsigned long long)hi0 << 32) | lo0;
+                masks[item][1] = ((unsigned long long)hi1 << 32) | lo1;
+            }
         }
         __syncthreads();
         // phase 2: ordered compaction of the window's masks (ascending K)
         for (int c0 = 0; c0 < kn * S; c0 += blockDim.x) {
             const int i = c0 + tid;
-            const unsigned long long m = i < kn * S ? masks[i] : 0ull;
-            const uint32_t r = block_excl_scan(m ? 1u : 0u, warp_sums, &total_s);
-            if (m) {
+            const unsigned long long m0 = i < kn * S ? masks[i][0] : 0ull;
+            const unsigned long long m1 = i < kn * S ? masks[i][1] : 0ull;
+            const bool any = (m0 | m1) != 0ull;
+            const uint32_t r = block_excl_scan(any ? 1u : 0u, warp_sums, &total_s);
+            if (any) {
                 const int g = i / S, kk = i % S;
-                pk[obase + written + r] = klist[kw + g] * S + kk;
-                pm[obase + written + r] = m;
+                const uint32_t pos = obase + written + r;
+                pk[pos] = klist[kw + g] * S + kk;
+                pm[2 * (size_t)pos] = m0;
+                pm[2 * (size_t)pos + 1] = m1;
             }
             written += total_s;
         }
         __syncthreads();
     }
-    (void)wd;
-    // statistics of the tiers below the tile node
+    // statistics of the tiers below the tile nodes
 #pragma unroll
     for (int l = 0; l < DS; ++l) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -396,8 +412,8 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
 cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
                          int tt) {
     cudaStream_t s = ctx->stream;
-    const int tps = tiles_per_side(A);
-    const int tiles = tps * tps;
+    const int tc = tile_cols(A);
+    const int tiles = tile_rows(A) * tc;
     const int ds = A->d - tt;
     const int S = 1 << ds;
     const unsigned long long cap = (unsigned long long)ctx->pool_words;
@@ -406,12 +422,12 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tile_fill, 0, sizeof(uint32_t) * tiles, s);
     if (e != cudaSuccess) return e;
     const int blocks = ctx->sm_count * 4;
-    k_group_count<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tps, ctx->tile_cnt);
+    k_group_count<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tc, ctx->tile_cnt);
     k_group_scan<<<1, 1024, 0, s>>>(tt, S, ctx->ctl, cap, ctx->tile_cnt, ctx->tile_off, tiles);
-    k_group_scatter<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tps, ctx->tile_off,
+    k_group_scatter<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tc, ctx->tile_off,
                                            ctx->tile_fill);
     const int words = ((1 << tt) + 31) / 32;
-    const size_t dsm = sizeof(uint32_t) * (words + ((size_t)1 << tt));
+    const size_t dsm = sizeof(uint32_t) * (2 * words + ((size_t)1 << tt));
 #define SPAMM_TC(DSV)                                                                          \
     do {                                                                                       \
         if (dsm > 48 * 1024)                                                                   \
@@ -419,7 +435,7 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
                                  (int)dsm);                                                    \
         k_tile_cull<DSV><<<tiles, 512, dsm, s>>>(tt, A->pyr, B->pyr, th, ctx->ctl,             \
                                                  ctx->pool, ctx->tile_off, ctx->tile_steps,    \
-                                                 tps);                                         \
+                                                 tc);                                          \
     } while (0)
     switch (ds) {
         case 0: SPAMM_TC(0); break;

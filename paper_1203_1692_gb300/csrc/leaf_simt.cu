@@ -1,9 +1,10 @@
 // Stage 4, FP32 on the CUDA cores: C_IJ = alpha * sum_{kept K, ascending}
 // A_IK B_KJ + beta * C_IJ (Algorithm 1, numeric part).
 //
-// One block per 128 x 128 C tile, 256 threads, each owning an 8 x 8 patch
-// (which lies inside one leaf pair (x, y) for b >= 8).  The block walks the
-// tile's (K, mask) steps in ascending K; for each step it stages A's
+// One block per 128 x 128 half of a C tile, 256 threads, each owning an 8 x 8
+// patch (which lies inside one leaf pair (x, y) for b >= 8).  The block
+// walks the tile's steps in ascending K, with that half's mask; for each
+// step with kept products it stages A's
 // 128 x 16 and B's 16 x 128 slices per 16-wide K chunk in shared memory
 // (zero outside the n x n matrix) and a thread runs its 8 x 8 x 16 FFMA
 // block only when its leaf pair's bit is set.  Like the numeric multiply of
@@ -20,7 +21,7 @@ namespace spamm {
 __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, int64_t lda,
                                                    const float* __restrict__ B, int64_t ldb,
                                                    float* __restrict__ C, int64_t ldc, int64_t n,
-                                                   int b, int tps, int S, float alpha,
+                                                   int b, int tc, int S, float alpha,
                                                    float beta,
                                                    const DevCtl* __restrict__ ctl,
                                                    const uint64_t* __restrict__ pool,
@@ -30,9 +31,10 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
     __shared__ __align__(16) float Bs[16][128];  // [k][col]
     extern __shared__ __align__(16) float accS[];  // [128][132] running C tile
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
-    const uint32_t u = blockIdx.x;
-    const int64_t R0 = (int64_t)(u / tps) * kTileRows;
-    const int64_t C0 = (int64_t)(u % tps) * kTileRows;
+    const uint32_t u = blockIdx.x >> 1;
+    const int half = blockIdx.x & 1;
+    const int64_t R0 = (int64_t)(u / tc) * kTileRows;
+    const int64_t C0 = ((int64_t)(u % tc) * kTileHalves + half) * kTileRows;
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
     const int x = (8 * ty) / b, y = (8 * tx) / b;
@@ -51,8 +53,9 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
     const unsigned long long* pm = reinterpret_cast<const unsigned long long*>(pool + ctl->pm_off);
     const int chunks = b >> 4;
     for (uint32_t st = 0; st < ns; ++st) {
+        const unsigned long long mask = pm[2 * (size_t)(base + st) + half];
+        if (mask == 0ull) continue;  // no kept product of this half at this K
         const int64_t K = pk[base + st];
-        const unsigned long long mask = pm[base + st];
         const bool mine = (mask >> bit) & 1ull;
         float part[8][8];
 #pragma unroll
@@ -119,13 +122,14 @@ __global__ void __launch_bounds__(256) k_leaf_simt(const float* __restrict__ A, 
 
 cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                              float alpha, float beta, float* C, int64_t ldc) {
-    const int tps = tiles_per_side(A);
+    const int tc = tile_cols(A);
+    const int tiles = tile_rows(A) * tc;
     const size_t dsm = sizeof(float) * 128 * 132;
     cudaError_t e = cudaFuncSetAttribute(k_leaf_simt, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dsm);
     if (e != cudaSuccess) return e;
-    k_leaf_simt<<<tps * tps, 256, dsm, ctx->stream>>>(A->A, A->lda, B->A, B->lda, C, ldc, A->n,
-                                                    A->b, tps, ctx->last_S, alpha, beta,
+    k_leaf_simt<<<tiles * kTileHalves, 256, dsm, ctx->stream>>>(A->A, A->lda, B->A, B->lda, C,
+                                                    ldc, A->n, A->b, tc, ctx->last_S, alpha, beta,
                                                     ctx->ctl, ctx->pool,
                                                     ctx->tile_off, ctx->tile_steps);
     return cudaGetLastError();

@@ -2,20 +2,23 @@
 // A_IK B_KJ + beta * C_IJ (Algorithm 1, numeric part), with FP32
 // accumulation in tensor memory.
 //
-// Work unit: one 128 x 128 C tile = TL x TL leaf pairs (TL = 128 / b), and the
-// tile's steps (K, mask) in ascending K from the grouping stage.  For every
-// step and every 16-wide K chunk the tile needs A's 128 x 16 slice (the TL
-// row leaves of the tile, column leaf K) and B's 16 x 128 slice; both were
-// stored by the norm build as contiguous runs already in the no-swizzle
-// K-major layout of tcgen05 (8-row x 16-byte core matrices), so one 1-D bulk
-// copy per operand moves them into shared memory.
+// Work unit: one 128 x 256 C tile = TL row leaves x 2 TL column leaves
+// (TL = 128 / b), and the tile's steps (K, two half masks) in ascending K
+// from the grouping stage.  For every step and every 16-wide K chunk the
+// tile needs A's 128 x 16 slice (its row leaves at column leaf K) and B's
+// 16 x 256 slice; both were stored by the norm build as contiguous runs
+// already in the no-swizzle K-major layout of tcgen05 (8-row x 16-byte core
+// matrices), so one 1-D bulk copy per operand part moves them into shared
+// memory.  A 256-wide tile halves the MMA instructions per flop compared
+// with 128 x 128: on this part an MMA's issue cost, not its arithmetic,
+// dominates at N = 128.
 //
 // Exactness of the cull: a kept leaf product (x, K, y) must be added and a
 // culled one must not.  One MMA over a run of consecutive column leaves
 // y0..y0+len-1 that share the same set of kept row leaves uses the MMA's
 // disable-output-lane mask to leave the accumulator rows (TMEM lanes) of the
 // culled row leaves untouched, so the tensor core adds exactly the kept
-// products.  N = len * b (16..128), M = 128.
+// products.  N = len * b (16..256), M = 128.
 //
 // Precisions: TF32X3 splits each operand into a TF32 high part and a TF32
 // low part (a - hi) and adds lo*hi + hi*lo + hi*hi; TF32 uses hi*hi only;
@@ -34,10 +37,12 @@
 // rows before moving one tile column right, so the tiles in flight at once
 // share A slices (same rows) and B slices (same columns) in L2.
 //
-// Roles (192 threads): warp 0 lane 0 issues the bulk copies into a ring of
-// shared-memory stages; warp 1 owns the TMEM allocation and its lane 0
-// issues the MMAs and commits; warps 2-5 move the double-buffered 128 x 128
-// chunk accumulators out of TMEM, sum them, apply alpha/beta and store C.  Every wait on an
+// Roles (320 threads): warp 0 lane 0 issues the bulk copies into a ring of
+// shared-memory stages; warp 1 owns the TMEM allocation (all 512 columns)
+// and its lane 0 issues the MMAs and commits; warps 2-9 move the
+// double-buffered 128 x 256 chunk accumulators out of TMEM (two warps per
+// TMEM lane quarter, 128 columns each), sum them, apply alpha/beta and store
+// C.  Every wait on an
 // mbarrier gives up after one second, raises the timeout status and lets
 // the block drain its copies and MMAs, free TMEM and exit.
 #include <cuda_bf16.h>
@@ -47,10 +52,11 @@
 namespace spamm {
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
 constexpr int kChunkIters = 8;  // K-chunks of 16 per TMEM accumulation chunk
 constexpr int kGroupRows = 8;   // tile rows walked together (L2 reuse)
-constexpr uint32_t kZeroBytes = 4096;
+constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -136,14 +142,14 @@ __device__ __forceinline__ uint32_t make_idesc(uint32_t ab, int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
-// Work item k -> tile index (row-major over tps x tps tiles), grouped by
+// Work item k -> tile index (row-major over tr x tc tiles), grouped by
 // kGroupRows tile rows.
-__device__ __forceinline__ int tile_at(int k, int tps) {
-    const int span = kGroupRows * tps;
+__device__ __forceinline__ int tile_at(int k, int tr, int tc) {
+    const int span = kGroupRows * tc;
     const int g = k / span;
-    const int rows = min(kGroupRows, tps - g * kGroupRows);
+    const int rows = min(kGroupRows, tr - g * kGroupRows);
     const int w = k - g * span;
-    return (g * kGroupRows + w % rows) * tps + w / rows;
+    return (g * kGroupRows + w % rows) * tc + w / rows;
 }
 
 __device__ __forceinline__ uint32_t chunks_of(uint32_t iters) {
@@ -190,8 +196,8 @@ struct PrecTraits {
     static constexpr int kEsize = PREC == SPAMM_PREC_BF16X3 ? 2 : 4;
     static constexpr int kParts = PREC == SPAMM_PREC_TF32 ? 1 : 2;      // arrays per role
     static constexpr int kSlice = 128 * 16 * kEsize;                   // bytes of one 128x16 slice
-    static constexpr int kStage = 2 * kParts * kSlice;                  // A and B slices
-    static constexpr int kStages = PREC == SPAMM_PREC_TF32X3 ? 4 : 6;
+    static constexpr int kStage = 3 * kParts * kSlice;                  // A (128) + B (256) rows
+    static constexpr int kStages = PREC == SPAMM_PREC_TF32X3 ? 4 : 8;
     static constexpr int kKInstr = PREC == SPAMM_PREC_BF16X3 ? 16 : 8;  // K per MMA
     static constexpr uint32_t kSBO = 8 * 16 * kEsize;                   // row-group stride
     static constexpr uint32_t kAB = PREC == SPAMM_PREC_BF16X3 ? 1u : 2u;
@@ -208,13 +214,14 @@ struct TcArgs {
     const uint64_t* pool;
     const uint32_t* off;
     const uint32_t* steps;
-    int tps, tiles, S;
+    int tr, tc, tiles, S;
 };
 
 template <int LEAF, int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     using T = PrecTraits<PREC>;
-    constexpr int TL = 128 / LEAF;
+    constexpr int TL = 128 / LEAF;      // row leaves = column leaves per half
+    constexpr int TLC = 2 * TL;         // column leaves of the tile
     constexpr int CHUNKS = LEAF / 16;
     constexpr int ST = T::kStages;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bar_accf[b]), 1);
-            mbar_init(smem_u32(&bar_acce[b]), 4);
+            mbar_init(smem_u32(&bar_acce[b]), kEpiWarps);
         }
         mbar_init(smem_u32(&bar_drain), 1);
         abort_flag = 0;
@@ -252,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(256u)
+                     "r"(512u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -266,149 +273,225 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
 
     if (warp == 0) {
         // ---------------------------------------------------------- producer
-        if (lane == 0) {
-            unsigned long long it = 0;
-            bool ok = true;
-            for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-                const int u = tile_at(k, p.tps);
-                const int64_t srow = (int64_t)(u / p.tps) * TL;
-                const int64_t scol = (int64_t)(u % p.tps) * TL;
-                const uint32_t ns = p.steps[u];
-                const uint64_t sb = (uint64_t)p.off[u] * p.S;
-                for (uint32_t st = 0; st < ns && ok; ++st) {
-                    const int64_t K = pk[sb + st];
+        // The whole warp walks the step list: each lane loads one K of a
+        // batch of 32 (the next batch is prefetched while this one is
+        // issued), and lane 0 issues the copies for each entry in turn.
+        unsigned long long it = 0;
+        bool ok = true;
+        for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
+            const int u = tile_at(k, p.tr, p.tc);
+            const int64_t srow = (int64_t)(u / p.tc) * TL;
+            const int64_t scol = (int64_t)(u % p.tc) * TLC;
+            const uint32_t ns = p.steps[u];
+            const uint64_t sb = (uint64_t)p.off[u] * p.S;
+            uint32_t cur = lane < (int)ns ? pk[sb + lane] : 0u;
+            for (uint32_t base = 0; base < ns && ok; base += 32) {
+                const uint32_t nxt = base + 32 + lane < ns ? pk[sb + base + 32 + lane] : 0u;
+                const uint32_t cnt = ns - base < 32 ? ns - base : 32;
+                for (uint32_t j = 0; j < cnt && ok; ++j) {
+                    const int64_t K = __shfl_sync(0xffffffffu, cur, j);
                     for (int kc = 0; kc < CHUNKS && ok; ++kc, ++it) {
-                        const int s = (int)(it % ST);
-                        const uint32_t ph = (uint32_t)((it / ST) & 1);
-                        if (!wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status)) {
-                            ok = false;
-                            break;
-                        }
-                        const uint32_t full = smem_u32(&bar_full[s]);
-                        mbar_expect_tx(full, T::kStage);
-                        const int64_t row = (K * CHUNKS + kc) * p.nlp;
-                        unsigned char* sbuf = stages + (size_t)s * T::kStage;
-                        const size_t piece = (size_t)LEAF * 16 * T::kEsize;
+                        if (lane == 0) {
+                            const int s = (int)(it % ST);
+                            const uint32_t ph = (uint32_t)((it / ST) & 1);
+                            if (wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status)) {
+                                const uint32_t full = smem_u32(&bar_full[s]);
+                                mbar_expect_tx(full, T::kStage);
+                                const int64_t row = (K * CHUNKS + kc) * p.nlp;
+                                unsigned char* sbuf = stages + (size_t)s * T::kStage;
+                                const size_t piece = (size_t)LEAF * 16 * T::kEsize;
 #pragma unroll
-                        for (int part = 0; part < T::kParts; ++part) {
-                            bulk_g2s(smem_u32(sbuf + part * T::kSlice),
-                                     static_cast<const unsigned char*>(p.pa[part]) +
-                                         (size_t)(row + srow) * piece,
-                                     T::kSlice, full);
-                            bulk_g2s(smem_u32(sbuf + (T::kParts + part) * T::kSlice),
-                                     static_cast<const unsigned char*>(p.pb[part]) +
-                                         (size_t)(row + scol) * piece,
-                                     T::kSlice, full);
+                                for (int part = 0; part < T::kParts; ++part) {
+                                    bulk_g2s(smem_u32(sbuf + part * T::kSlice),
+                                             static_cast<const unsigned char*>(p.pa[part]) +
+                                                 (size_t)(row + srow) * piece,
+                                             T::kSlice, full);
+                                    bulk_g2s(smem_u32(sbuf + (T::kParts + 2 * part) * T::kSlice),
+                                             static_cast<const unsigned char*>(p.pb[part]) +
+                                                 (size_t)(row + scol) * piece,
+                                             2 * T::kSlice, full);
+                                }
+                                issued_s = it + 1;
+                            } else {
+                                ok = false;
+                            }
                         }
-                        issued_s = it + 1;
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
                     }
                 }
+                cur = nxt;
             }
         }
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA
-        if (lane == 0) {
-            unsigned long long it = 0;
-            uint32_t ccount = 0;  // chunks issued so far (selects the TMEM buffer)
-            bool ok = true;
-            const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
-            const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
-            for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-                const int u = tile_at(k, p.tps);
-                const uint32_t ns = p.steps[u];
-                const uint64_t sb = (uint64_t)p.off[u] * p.S;
-                const uint32_t iters = ns * CHUNKS;
-                const uint32_t nch = chunks_of(iters);
-                uint32_t st = 0;
-                int kc = 0;
-                for (uint32_t c = 0; c < nch && ok; ++c, ++ccount) {
-                    const uint32_t ab = ccount & 1;
-                    const uint32_t aph = (ccount >> 1) & 1;
-                    if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t dacc = tmem + ab * 128;
-                    // clear the chunk accumulator: 0 * 0 with the input accumulator off
-                    mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 128), dis0, 0u);
-                    const uint32_t last = min(iters, (c + 1) * kChunkIters);
-                    for (uint32_t i = c * kChunkIters; i < last && ok; ++i, ++it) {
-                        const unsigned long long mask = pm[sb + st];
-                        const int s = (int)(it % ST);
-                        const uint32_t ph = (uint32_t)((it / ST) & 1);
-                        if (!wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status)) {
-                            ok = false;
-                            break;
-                        }
-                        consumed_s = it + 1;
+        // Same batching of the step masks; lane 0 issues.  Iteration i of a
+        // tile (step i / CHUNKS, K-chunk i % CHUNKS) opens a new TMEM chunk
+        // when i % kChunkIters == 0 and closes it at the chunk's last
+        // iteration; a tile without steps gets one empty (zeroed) chunk.
+        unsigned long long it = 0;
+        uint32_t ccount = 0;  // chunks opened so far (selects the TMEM buffer)
+        bool ok = true;
+        const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
+        const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
+        uint32_t dacc = tmem;
+        for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
+            const int u = tile_at(k, p.tr, p.tc);
+            const uint32_t ns = p.steps[u];
+            const uint64_t sb = (uint64_t)p.off[u] * p.S;
+            const uint32_t iters = ns * CHUNKS;
+            if (iters == 0) {
+                if (lane == 0) {
+                    const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
+                    if (wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
                         tc_fence_after();
-                        const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
-                        const uint32_t a_hi = sbuf, a_lo = sbuf + T::kSlice;
-                        const uint32_t b_hi = sbuf + T::kParts * T::kSlice;
-                        const uint32_t b_lo = b_hi + T::kSlice;
-                        int y = 0;
-                        while (y < TL) {
-                            const uint32_t xm = (uint32_t)(mask >> (8 * y)) & 0xFFu;
-                            if (!xm) {
-                                ++y;
-                                continue;
-                            }
-                            int len = 1;
-                            while (y + len < TL &&
-                                   ((uint32_t)(mask >> (8 * (y + len))) & 0xFFu) == xm)
-                                ++len;
-                            uint32_t dis[4];
-#pragma unroll
-                            for (int w = 0; w < 4; ++w) {
-                                uint32_t v = 0;
-#pragma unroll
-                                for (int q = 0; q < 32 / LEAF; ++q) {
-                                    const int x = w * (32 / LEAF) + q;
-                                    if (!((xm >> x) & 1u))
-                                        v |= (LEAF == 32 ? 0xFFFFFFFFu : (0xFFFFu << (16 * q)));
-                                }
-                                dis[w] = v;
-                            }
-                            const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
-                            const uint32_t d = dacc + (uint32_t)(y * LEAF);
-                            const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
-#pragma unroll
-                            for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                const uint32_t koff = (uint32_t)kk * 256u;
-                                const uint64_t ah = make_desc(a_hi + koff, 128, T::kSBO);
-                                const uint64_t bh = make_desc(b_hi + boff + koff, 128, T::kSBO);
-                                if (PREC != SPAMM_PREC_TF32) {
-                                    const uint64_t al = make_desc(a_lo + koff, 128, T::kSBO);
-                                    const uint64_t bl =
-                                        make_desc(b_lo + boff + koff, 128, T::kSBO);
-                                    mma<PREC>(d, al, bh, idesc, dis, 1u);
-                                    mma<PREC>(d, ah, bl, idesc, dis, 1u);
-                                }
-                                mma<PREC>(d, ah, bh, idesc, dis, 1u);
-                            }
-                            y += len;
-                        }
-                        tc_commit(smem_u32(&bar_empty[s]));
-                        if (++kc == CHUNKS) {
-                            kc = 0;
-                            ++st;
-                        }
+                        mma<PREC>(tmem + ab * 256, zdesc, zdesc, make_idesc(T::kAB, 128, 256),
+                                  dis0, 0u);
+                        tc_commit(smem_u32(&bar_accf[ab]));
+                    } else {
+                        ok = false;
                     }
-                    if (ok) tc_commit(smem_u32(&bar_accf[ab]));
+                    ++ccount;
                 }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                continue;
             }
-            // drain: every MMA issued so far has completed before TMEM is freed
+            uint32_t i = 0;
+            unsigned long long cur0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
+            unsigned long long cur1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
+            for (uint32_t base = 0; base < ns && ok; base += 32) {
+                const bool more = base + 32 + lane < ns;
+                const unsigned long long nxt0 = more ? pm[2 * (sb + base + 32 + lane)] : 0ull;
+                const unsigned long long nxt1 = more ? pm[2 * (sb + base + 32 + lane) + 1] : 0ull;
+                const uint32_t cnt = ns - base < 32 ? ns - base : 32;
+                for (uint32_t j = 0; j < cnt && ok; ++j) {
+                    const unsigned long long mask0 = __shfl_sync(0xffffffffu, cur0, j);
+                    const unsigned long long mask1 = __shfl_sync(0xffffffffu, cur1, j);
+                    for (int kc = 0; kc < CHUNKS && ok; ++kc, ++i, ++it) {
+                        if (lane == 0) {
+                            if (i % kChunkIters == 0) {
+                                const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
+                                if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag,
+                                              status))
+                                    ok = false;
+                                tc_fence_after();
+                                dacc = tmem + ab * 256;
+                                // clear the chunk accumulator: 0 * 0, input accumulator off
+                                if (ok)
+                                    mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256),
+                                              dis0, 0u);
+                            }
+                            const int s = (int)(it % ST);
+                            const uint32_t ph = (uint32_t)((it / ST) & 1);
+                            if (ok && !wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status))
+                                ok = false;
+                            if (ok) {
+                                consumed_s = it + 1;
+                                tc_fence_after();
+                                const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
+                                const uint32_t a_hi = sbuf, a_lo = sbuf + T::kSlice;
+                                const uint32_t b_hi = sbuf + T::kParts * T::kSlice;
+                                const uint32_t b_lo = b_hi + 2 * T::kSlice;
+                                // Runs of column leaves with the same kept row leaves:
+                                // a column y starts a run when its row mask is non-zero
+                                // and differs from column y-1's.  Uniform halves (the
+                                // common case on dense blocks) give one run directly.
+                                constexpr unsigned long long kRep =
+                                    TL == 8 ? 0x0101010101010101ull : 0x0000000001010101ull;
+                                const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
+                                const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
+                                const bool u0 = mask0 == (unsigned long long)x0 * kRep;
+                                const bool u1 = mask1 == (unsigned long long)x1 * kRep;
+                                uint32_t starts, nz;
+                                if (u0 && u1) {
+                                    starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
+                                    nz = (x0 ? (1u << TL) - 1u : 0u) |
+                                         (x1 ? ((1u << TL) - 1u) << TL : 0u);
+                                } else {
+                                    starts = 0u;
+                                    nz = 0u;
+                                    uint32_t prev = 0u;
+#pragma unroll
+                                    for (int yy = 0; yy < TLC; ++yy) {
+                                        const uint32_t xm =
+                                            yy < TL ? (uint32_t)(mask0 >> (8 * yy)) & 0xFFu
+                                                    : (uint32_t)(mask1 >> (8 * (yy - TL))) & 0xFFu;
+                                        if (xm) nz |= 1u << yy;
+                                        if (xm && xm != prev) starts |= 1u << yy;
+                                        prev = xm;
+                                    }
+                                }
+                                uint64_t ah[2], al[2];
+#pragma unroll
+                                for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                    ah[kk] = make_desc(a_hi + (uint32_t)kk * 256u, 128, T::kSBO);
+                                    al[kk] = make_desc(a_lo + (uint32_t)kk * 256u, 128, T::kSBO);
+                                }
+                                while (starts) {
+                                    const int y = __ffs(starts) - 1;
+                                    starts &= starts - 1;
+                                    const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
+                                    const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
+                                    const int len = yend - y;
+                                    const uint32_t xm = y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
+                                                               : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
+                                    uint32_t dis[4];
+#pragma unroll
+                                    for (int w = 0; w < 4; ++w) {
+                                        uint32_t v = 0;
+#pragma unroll
+                                        for (int q = 0; q < 32 / LEAF; ++q) {
+                                            const int x = w * (32 / LEAF) + q;
+                                            if (!((xm >> x) & 1u))
+                                                v |= (LEAF == 32 ? 0xFFFFFFFFu
+                                                                 : (0xFFFFu << (16 * q)));
+                                        }
+                                        dis[w] = v;
+                                    }
+                                    const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
+                                    const uint32_t d = dacc + (uint32_t)(y * LEAF);
+                                    const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
+#pragma unroll
+                                    for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                        const uint32_t koff = (uint32_t)kk * 256u;
+                                        const uint64_t bh =
+                                            make_desc(b_hi + boff + koff, 128, T::kSBO);
+                                        if (PREC != SPAMM_PREC_TF32) {
+                                            const uint64_t bl =
+                                                make_desc(b_lo + boff + koff, 128, T::kSBO);
+                                            mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
+                                            mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
+                                        }
+                                        mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
+                                    }
+                                }
+                                tc_commit(smem_u32(&bar_empty[s]));
+                                if (i % kChunkIters == kChunkIters - 1 || i == iters - 1) {
+                                    tc_commit(smem_u32(&bar_accf[ccount & 1]));
+                                    ++ccount;
+                                }
+                            }
+                        }
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                    }
+                }
+                cur0 = nxt0;
+                cur1 = nxt1;
+            }
+        }
+        // drain: every MMA issued so far has completed before TMEM is freed
+        if (lane == 0) {
             tc_commit(smem_u32(&bar_drain));
             wait_bar(smem_u32(&bar_drain), 0, &abort_flag, status);
         }
+        __syncwarp();
     } else {
         // ---------------------------------------------------------- epilogue
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const int q = warp & 3;                  // TMEM lane quarter this warp may access
+        const int hcol = (warp - 2) >> 2;        // which 128 columns of the 256
         uint32_t ccount = 0;
         bool ok = true;
         for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-            const int u = tile_at(k, p.tps);
+            const int u = tile_at(k, p.tr, p.tc);
             const uint32_t nch = chunks_of(p.steps[u] * CHUNKS);
             float master[128];
 #pragma unroll
@@ -421,7 +504,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + ab * 128;
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(q * 32) << 16) + ab * 256 + (uint32_t)(hcol * 128);
 #pragma unroll
                 for (int cc = 0; cc < 128; cc += 32) {
                     uint32_t r[32];
@@ -434,9 +518,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                 if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
             }
             if (!ok) break;
-            const int64_t row = (int64_t)(u / p.tps) * 128 + q * 32 + lane;
-            const int64_t col0 = (int64_t)(u % p.tps) * 128;
-            if (row < p.n) {
+            const int64_t row = (int64_t)(u / p.tc) * 128 + q * 32 + lane;
+            const int64_t col0 = (int64_t)(u % p.tc) * 256 + hcol * 128;
+            if (row < p.n && col0 < p.n) {
                 float* crow = p.C + row * p.ldc + col0;
                 const bool vec = ((p.ldc & 3) == 0) &&
                                  ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0) &&
@@ -486,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     __syncthreads();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                      : "memory");
     }
 }
@@ -522,8 +606,9 @@ cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree
     a.pool = ctx->pool;
     a.off = ctx->tile_off;
     a.steps = ctx->tile_steps;
-    a.tps = tiles_per_side(A);
-    a.tiles = a.tps * a.tps;
+    a.tr = tile_rows(A);
+    a.tc = tile_cols(A);
+    a.tiles = a.tr * a.tc;
     a.S = ctx->last_S;
     const int p = A->precision;
     if (A->b == 16) {

@@ -6,6 +6,7 @@
 // lanes that share a leaf combine their partial sums with a segmented
 // xor-shuffle reduction.  The kernel reads each element of A once, with
 // 16-byte loads when A and lda allow it, so it is bound by HBM bandwidth.
+// With tensor-core packs the same sums come from k_leaf_pack below.
 // The upper tiers come from a second kernel that builds five tiers per pass
 // in shared memory, each node the sum of its four children in the order
 // A11 + A12 + A21 + A22.
@@ -47,35 +48,24 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// PK: 0 none, 1 tf32 hi, 2 tf32 hi+lo, 3 bf16 hi+lo
-template <int PK, bool VEC>
+// Leaf squared norms only (FP32 leaf products need no packs).
+template <bool VEC>
 __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A, int64_t n,
                                                     int64_t lda, int b, int64_t nb, int64_t nl,
-                                                    int64_t nlp, double* __restrict__ leaf,
-                                                    void* __restrict__ pa0, void* __restrict__ pa1,
-                                                    void* __restrict__ pb0, void* __restrict__ pb1) {
+                                                    double* __restrict__ leaf) {
     const int64_t I = blockIdx.y;                       // leaf row
     const int64_t col0 = (int64_t)blockIdx.x * 512 + 4 * threadIdx.x;
     const int64_t K = col0 / b;                          // leaf column
     const int lanes = b >> 2;                            // lanes per leaf
     double s = 0.0;
     const int64_t r0 = I * b;
-    const int kk = (int)(col0 - K * b);                  // column inside the leaf
-    const int chunks = b >> 4;
-    const size_t piece_elems = (size_t)b * 16;
     for (int r = 0; r < b; ++r) {
         const int64_t row = r0 + r;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < n) {
             const float* p = A + row * lda + col0;
-            if (VEC) {
-                if (col0 + 3 < n) {
-                    v = __ldg(reinterpret_cast<const float4*>(p));
-                } else {
-                    if (col0 + 0 < n) v.x = __ldg(p + 0);
-                    if (col0 + 1 < n) v.y = __ldg(p + 1);
-                    if (col0 + 2 < n) v.z = __ldg(p + 2);
-                }
+            if (VEC && col0 + 3 < n) {
+                v = __ldg(reinterpret_cast<const float4*>(p));
             } else {
                 if (col0 + 0 < n) v.x = __ldg(p + 0);
                 if (col0 + 1 < n) v.y = __ldg(p + 1);
@@ -88,67 +78,145 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
         s += y * y;
         s += z * z;
         s += w * w;
-        if (PK != 0 && K < nl) {
-            // A role: leaf (I, K), row r, chunk k' = kk.
-            const int kc = kk >> 4, kq = kk & 15;
-            const size_t pieceA = ((size_t)(K * chunks + kc) * nlp + I) * piece_elems;
-            // B role: leaf (K=I, J=K): n-index = kk..kk+3, k index = r.
-            const int bkc = r >> 4, bkq = r & 15;
-            const size_t pieceB = ((size_t)(I * chunks + bkc) * nlp + K) * piece_elems;
-            if (PK == 1 || PK == 2) {
-                uint32_t h[4], l[4];
-                const float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    h[q] = to_tf32(f[q]);
-                    l[q] = to_tf32(f[q] - __uint_as_float(h[q]));
-                }
-                // element offset inside a TF32 piece: row g, k q ->
-                // (g%8)*4 + (g/8)*128 + (q%4) + (q/4)*32   (in 4-byte words)
-                const size_t offA = pieceA + (r & 7) * 4 + (r >> 3) * 128 + (kq >> 2) * 32;
-                reinterpret_cast<uint4*>(pa0)[offA >> 2] = make_uint4(h[0], h[1], h[2], h[3]);
-                if (PK == 2)
-                    reinterpret_cast<uint4*>(pa1)[offA >> 2] = make_uint4(l[0], l[1], l[2], l[3]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int nn = kk + q;
-                    const size_t offB = pieceB + (nn & 7) * 4 + (nn >> 3) * 128 + (bkq & 3) +
-                                        (bkq >> 2) * 32;
-                    reinterpret_cast<uint32_t*>(pb0)[offB] = h[q];
-                    if (PK == 2) reinterpret_cast<uint32_t*>(pb1)[offB] = l[q];
-                }
-            } else {  // BF16 hi/lo, core matrix = 8 rows x 8 elements
-                __nv_bfloat16 h[4], l[4];
-                const float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    h[q] = __float2bfloat16_rn(f[q]);
-                    l[q] = __float2bfloat16_rn(f[q] - __bfloat162float(h[q]));
-                }
-                // element offset inside a BF16 piece: row g, k q ->
-                // (g%8)*8 + (g/8)*128 + (q%8) + (q/8)*64   (in 2-byte elements)
-                const size_t offA = pieceA + (r & 7) * 8 + (r >> 3) * 128 + (kq & 7) + (kq >> 3) * 64;
-                uint2 hv, lv;
-                hv.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
-                hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
-                lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
-                lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
-                reinterpret_cast<uint2*>(pa0)[offA >> 2] = hv;
-                reinterpret_cast<uint2*>(pa1)[offA >> 2] = lv;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int nn = kk + q;
-                    const size_t offB = pieceB + (nn & 7) * 8 + (nn >> 3) * 128 + (bkq & 7) +
-                                        (bkq >> 3) * 64;
-                    reinterpret_cast<__nv_bfloat16*>(pb0)[offB] = h[q];
-                    reinterpret_cast<__nv_bfloat16*>(pb1)[offB] = l[q];
-                }
-            }
-        }
     }
     // segmented reduction over the lanes of one leaf
     for (int off = lanes >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if ((threadIdx.x & (lanes - 1)) == 0 && K < nl) leaf[I * nb + K] = s;
+}
+
+// Leaf norms plus tensor-core packs.  A block owns one leaf row-strip (b
+// rows) x 128 columns (TL leaves): it stages the strip in shared memory,
+// forms the leaf squared norms (FP64), splits every element into hi/lo
+// parts, writes them into shared-memory copies of the A-role and B-role
+// pieces, and then streams the pieces out with 16-byte stores: the A-role
+// pieces of one leaf and the B-role pieces of one K-chunk are contiguous in
+// HBM, so every global write is coalesced.  PK: 1 tf32 hi, 2 tf32 hi+lo,
+// 3 bf16 hi+lo.
+template <int PK, int LEAF>
+__global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, int64_t n,
+                                                   int64_t lda, int64_t nb, int64_t nl, int64_t nlp,
+                                                   double* __restrict__ leaf,
+                                                   void* __restrict__ pa0, void* __restrict__ pa1,
+                                                   void* __restrict__ pb0, void* __restrict__ pb1) {
+    constexpr int TL = 128 / LEAF;
+    constexpr int CH = LEAF / 16;
+    constexpr int ES = PK == 3 ? 2 : 4;                  // element bytes
+    constexpr int PIECE = LEAF * 16 * ES;                // bytes of one piece
+    constexpr int BUF = TL * CH * PIECE;                 // = 128 * LEAF * ES
+    constexpr int NBUF = PK == 1 ? 2 : 4;                // A hi, (A lo), B hi, (B lo)
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double part[4][TL];
+    const int64_t I = blockIdx.y;                        // leaf row
+    const int64_t Q0 = (int64_t)blockIdx.x * TL;         // first leaf column
+    const int64_t r0 = I * LEAF, c0 = Q0 * LEAF;
+    const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
+    unsigned char* bufA0 = sm;
+    unsigned char* bufA1 = sm + BUF;
+    unsigned char* bufB0 = sm + (NBUF / 2) * BUF;
+    unsigned char* bufB1 = bufB0 + BUF;
+    // thread t owns columns 4*(t%32)..+3 of rows t/32, t/32+4, ...
+    const int cq = 4 * lane;
+    const int x = cq / LEAF, kk = cq % LEAF;            // leaf, column inside it
+    double s = 0.0;
+#pragma unroll 4
+    for (int r = warp; r < LEAF; r += 4) {
+        const int64_t row = r0 + r, col = c0 + cq;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < n) {
+            const float* p = A + row * lda + col;
+            if (vec && col + 3 < n) {
+                v = __ldg(reinterpret_cast<const float4*>(p));
+            } else {
+                if (col + 0 < n) v.x = __ldg(p + 0);
+                if (col + 1 < n) v.y = __ldg(p + 1);
+                if (col + 2 < n) v.z = __ldg(p + 2);
+                if (col + 3 < n) v.w = __ldg(p + 3);
+            }
+        }
+        const double dx = v.x, dy = v.y, dz = v.z, dw = v.w;
+        s += dx * dx;
+        s += dy * dy;
+        s += dz * dz;
+        s += dw * dw;
+        const float f[4] = {v.x, v.y, v.z, v.w};
+        const int kc = kk >> 4, kq = kk & 15;            // A role: row r, k = kk
+        const int bkc = r >> 4, bkq = r & 15;            // B role: n = kk + q, k = r
+        if (PK != 3) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] = to_tf32(f[q]);
+                l[q] = to_tf32(f[q] - __uint_as_float(h[q]));
+            }
+            const int offA = (x * CH + kc) * PIECE + ((r & 7) * 4 + (r >> 3) * 128 + (kq >> 2) * 32) * 4;
+            *reinterpret_cast<uint4*>(bufA0 + offA) = make_uint4(h[0], h[1], h[2], h[3]);
+            if (PK == 2) *reinterpret_cast<uint4*>(bufA1 + offA) = make_uint4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int nn = kk + q;
+                const int offB = (bkc * TL + x) * PIECE +
+                                 ((nn & 7) * 4 + (nn >> 3) * 128 + (bkq & 3) + (bkq >> 2) * 32) * 4;
+                *reinterpret_cast<uint32_t*>(bufB0 + offB) = h[q];
+                if (PK == 2) *reinterpret_cast<uint32_t*>(bufB1 + offB) = l[q];
+            }
+        } else {
+            __nv_bfloat16 h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] = __float2bfloat16_rn(f[q]);
+                l[q] = __float2bfloat16_rn(f[q] - __bfloat162float(h[q]));
+            }
+            const int offA = (x * CH + kc) * PIECE + ((r & 7) * 8 + (r >> 3) * 128 + (kq & 7) + (kq >> 3) * 64) * 2;
+            uint2 hv, lv;
+            hv.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+            hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+            lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+            lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+            *reinterpret_cast<uint2*>(bufA0 + offA) = hv;
+            *reinterpret_cast<uint2*>(bufA1 + offA) = lv;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int nn = kk + q;
+                const int offB = (bkc * TL + x) * PIECE +
+                                 ((nn & 7) * 8 + (nn >> 3) * 128 + (bkq & 7) + (bkq >> 3) * 64) * 2;
+                *reinterpret_cast<__nv_bfloat16*>(bufB0 + offB) = h[q];
+                *reinterpret_cast<__nv_bfloat16*>(bufB1 + offB) = l[q];
+            }
+        }
+    }
+    // leaf squared norms: lanes of one leaf, then the four warps, fixed order
+    constexpr int LPL = LEAF / 4;                        // lanes per leaf
+    if (LPL <= 32) {
+        for (int o = (LPL < 32 ? LPL : 32) >> 1; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (LEAF <= 128 && (lane % LPL) == 0) part[warp][x] = s;
+    __syncthreads();
+    if (t < TL) {
+        const double v = ((part[0][t] + part[1][t]) + part[2][t]) + part[3][t];
+        if (Q0 + t < nl) leaf[I * nb + Q0 + t] = v;
+    }
+    // stream the pieces out with 16-byte stores
+    const size_t piece = PIECE;
+    for (int w = 0; w < NBUF / 2; ++w) {
+        const unsigned char* srcA = w ? bufA1 : bufA0;
+        const unsigned char* srcB = w ? bufB1 : bufB0;
+        unsigned char* dA = static_cast<unsigned char*>(w ? pa1 : pa0);
+        unsigned char* dB = static_cast<unsigned char*>(w ? pb1 : pb0);
+        for (int e = t; e < BUF / 16; e += 128) {
+            const int pc = (e * 16) / PIECE, inner = (e * 16) % PIECE;
+            // A role: piece (leaf x, chunk kc) -> ((Q * CH + kc) * nlp + I)
+            const int xa = pc / CH, kca = pc % CH;
+            const size_t ga = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * piece + inner;
+            *reinterpret_cast<uint4*>(dA + ga) = *reinterpret_cast<const uint4*>(srcA + e * 16);
+            // B role: piece (chunk kc, leaf x) -> ((I * CH + kc) * nlp + Q)
+            const int kcb = pc / TL, xb = pc % TL;
+            const size_t gb = ((size_t)(I * CH + kcb) * nlp + (Q0 + xb)) * piece + inner;
+            *reinterpret_cast<uint4*>(dB + gb) = *reinterpret_cast<const uint4*>(srcB + e * 16);
+        }
+    }
 }
 
 // Five tiers per pass: a block reduces a (up to) 32 x 32 patch of tier L.
@@ -195,34 +263,44 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(leaf, 0, sizeof(double) * t->nb * t->nb, s);
     if (e != cudaSuccess) return e;
     const bool vec = ((reinterpret_cast<uintptr_t>(t->A) & 15) == 0) && (t->lda % 4 == 0);
-    dim3 grid((unsigned)((t->nl * t->b + 511) / 512), (unsigned)t->nl);
     void* pa0 = t->packA[0];
     void* pa1 = t->packA[1];
     void* pb0 = t->packB[0];
     void* pb1 = t->packB[1];
-#define SPAMM_LN(PK, V)                                                                      \
-    k_leaf_norms<PK, V><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->b, t->nb, t->nl, t->nlp, \
-                                             leaf, pa0, pa1, pb0, pb1)
     const int pk = t->precision == SPAMM_PREC_FP32    ? 0
                    : t->precision == SPAMM_PREC_TF32  ? 1
                    : t->precision == SPAMM_PREC_TF32X3 ? 2
                                                        : 3;
-    if (vec) {
-        switch (pk) {
-            case 0: SPAMM_LN(0, true); break;
-            case 1: SPAMM_LN(1, true); break;
-            case 2: SPAMM_LN(2, true); break;
-            default: SPAMM_LN(3, true); break;
-        }
+    if (pk == 0) {
+        dim3 grid((unsigned)((t->nl * t->b + 511) / 512), (unsigned)t->nl);
+        if (vec)
+            k_leaf_norms<true><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->b, t->nb, t->nl, leaf);
+        else
+            k_leaf_norms<false><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->b, t->nb, t->nl, leaf);
     } else {
-        switch (pk) {
-            case 0: SPAMM_LN(0, false); break;
-            case 1: SPAMM_LN(1, false); break;
-            case 2: SPAMM_LN(2, false); break;
-            default: SPAMM_LN(3, false); break;
+        const int tl = 128 / t->b;
+        dim3 grid((unsigned)(t->nlp / tl), (unsigned)t->nl);
+        const int es = pk == 3 ? 2 : 4;
+        const int nbuf = pk == 1 ? 2 : 4;
+        const size_t dsm = (size_t)nbuf * 128 * t->b * es;
+#define SPAMM_LP(PKV, LV)                                                                     \
+    do {                                                                                      \
+        cudaFuncSetAttribute(k_leaf_pack<PKV, LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)dsm);                                                       \
+        k_leaf_pack<PKV, LV><<<grid, 128, dsm, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp,   \
+                                                    leaf, pa0, pa1, pb0, pb1);                \
+    } while (0)
+        if (t->b == 16) {
+            if (pk == 1) SPAMM_LP(1, 16);
+            else if (pk == 2) SPAMM_LP(2, 16);
+            else SPAMM_LP(3, 16);
+        } else {
+            if (pk == 1) SPAMM_LP(1, 32);
+            else if (pk == 2) SPAMM_LP(2, 32);
+            else SPAMM_LP(3, 32);
         }
+#undef SPAMM_LP
     }
-#undef SPAMM_LN
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int L = t->d;

@@ -28,8 +28,10 @@ spamm_status cuda_err(spamm_ctx* ctx, cudaError_t e, const char* what) {
     return set_err(ctx, st, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-int tiles_per_side(const spamm_tree* t) {
-    return (int)(t->nlp / (kTileRows / t->b));
+int tile_rows(const spamm_tree* t) { return (int)(t->nlp / (kTileRows / t->b)); }
+
+int tile_cols(const spamm_tree* t) {
+    return (int)(t->nlp / (kTileHalves * (kTileRows / t->b)));
 }
 
 int tile_tier(const spamm_tree* t) {
@@ -102,13 +104,13 @@ spamm_status check_matrix(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda
 }
 
 // Pool words a multiply needs: the frontiers of tiers 0..tt, then one u32
-// entry per tier-tt triple and S steps (u32 K + u64 mask) per entry.
+// entry per tier-tt triple and S steps (u32 K + two u64 masks) per entry.
 int64_t words_needed(const DevCtl& c, int tt, int S) {
     unsigned long long s = 0;
     for (int t = 0; t <= tt; ++t) s += c.tier_count[t];
     const unsigned long long m = c.tier_count[tt];
     const unsigned long long ms = m * (unsigned long long)S;
-    return (int64_t)(s + (m + 1) / 2 + (ms + 1) / 2 + ms);
+    return (int64_t)(s + (m + 1) / 2 + (ms + 1) / 2 + 2 * ms);
 }
 
 }  // namespace
@@ -236,7 +238,7 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
     t->d = d;
     t->nb = (int64_t)1 << d;
     t->nl = nl;
-    t->nlp = (nl + tl - 1) / tl * tl;
+    t->nlp = (nl + 2 * tl - 1) / (2 * tl) * (2 * tl);
     t->nodes = (((int64_t)1 << (2 * (d + 1))) - 1) / 3;
     t->precision = ctx->cfg.precision;
     cudaError_t e = cudaMalloc(&t->pyr, sizeof(double) * t->nodes);
@@ -349,15 +351,17 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
     if (A->precision != ctx->cfg.precision || A->b != ctx->cfg.leaf)
         return set_err(ctx, SPAMM_ERR_INVALID_ARG, "trees built under another configuration");
     if (ldc < A->n) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "ldc below n");
-    const int64_t tps = tiles_per_side(A);
-    spamm_status st = ensure_tiles(ctx, tps * tps);
+    const int64_t tiles = (int64_t)tile_rows(A) * tile_cols(A);
+    spamm_status st = ensure_tiles(ctx, tiles);
     if (st != SPAMM_OK) return st;
     ctx->last_d = A->d;
     ctx->last_b = A->b;
     ctx->last_n = A->n;
     ctx->last_prec = A->precision;
     ctx->last_tau = tau;
-    ctx->last_tiles = tps * tps;
+    ctx->last_tiles = tiles;
+    ctx->last_tr = tile_rows(A);
+    ctx->last_tc = tile_cols(A);
     ctx->last_tt = tile_tier(A);
     ctx->last_S = 1 << (A->d - ctx->last_tt);
     ctx->last_status = SPAMM_OK;
@@ -430,11 +434,11 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     if (cap <= 0 || m == 0) return SPAMM_OK;
     // expand the tile-compressed steps (K, mask) into (I, K, J) rows
     const int64_t tiles = ctx->last_tiles;
-    const int tps = (int)std::lround(std::sqrt((double)tiles));
+    const int tc = ctx->last_tc;
     const int tl = kTileRows / ctx->last_b;
     const uint64_t msteps = (uint64_t)c.tier_count[ctx->last_tt] * ctx->last_S;
     std::vector<uint32_t> off((size_t)tiles + 1), nst((size_t)tiles), pk((size_t)msteps);
-    std::vector<uint64_t> pm((size_t)msteps);
+    std::vector<uint64_t> pm((size_t)(2 * msteps));
     e = cudaMemcpy(off.data(), ctx->tile_off, sizeof(uint32_t) * (tiles + 1), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
         e = cudaMemcpy(nst.data(), ctx->tile_steps, sizeof(uint32_t) * tiles, cudaMemcpyDeviceToHost);
@@ -442,21 +446,23 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
         e = cudaMemcpy(pk.data(), reinterpret_cast<uint32_t*>(ctx->pool + c.pk_off),
                        sizeof(uint32_t) * msteps, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && msteps)
-        e = cudaMemcpy(pm.data(), ctx->pool + c.pm_off, sizeof(uint64_t) * msteps,
+        e = cudaMemcpy(pm.data(), ctx->pool + c.pm_off, sizeof(uint64_t) * 2 * msteps,
                        cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(ctx, e, "triples copy");
     int64_t k = 0;
     for (int64_t u = 0; u < tiles && k < cap; ++u) {
         const uint64_t base = (uint64_t)off[u] * ctx->last_S;
         for (uint32_t q = 0; q < nst[u] && k < cap; ++q) {
-            uint64_t mk = pm[base + q];
-            while (mk && k < cap) {
-                const int bit = __builtin_ctzll(mk);
-                mk &= mk - 1;
-                host_out[3 * k + 0] = (int32_t)((u / tps) * tl + (bit & 7));
-                host_out[3 * k + 1] = (int32_t)pk[base + q];
-                host_out[3 * k + 2] = (int32_t)((u % tps) * tl + (bit >> 3));
-                ++k;
+            for (int h = 0; h < kTileHalves; ++h) {
+                uint64_t mk = pm[2 * (base + q) + h];
+                while (mk && k < cap) {
+                    const int bit = __builtin_ctzll(mk);
+                    mk &= mk - 1;
+                    host_out[3 * k + 0] = (int32_t)((u / tc) * tl + (bit & 7));
+                    host_out[3 * k + 1] = (int32_t)pk[base + q];
+                    host_out[3 * k + 2] = (int32_t)(((u % tc) * kTileHalves + h) * tl + (bit >> 3));
+                    ++k;
+                }
             }
         }
     }

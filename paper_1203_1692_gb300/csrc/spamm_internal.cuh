@@ -22,10 +22,13 @@ __host__ __device__ inline uint32_t tri_I(uint64_t p) { return (uint32_t)(p >> (
 __host__ __device__ inline uint32_t tri_K(uint64_t p) { return (uint32_t)((p >> kIdxBits) & kIdxMask); }
 __host__ __device__ inline uint32_t tri_J(uint64_t p) { return (uint32_t)(p & kIdxMask); }
 
-// A C tile is 128 x 128: TL = 128 / b leaves per side.  Each grouped
-// (tile, K) step carries a 64-bit mask, bit (y * 8 + x) = "product of row
-// leaf x and column leaf y of the tile is kept" (only TL x TL bits are used).
+// A C tile is 128 rows x 256 columns: TL = 128 / b row leaves and 2 TL
+// column leaves, i.e. one quadtree node of TL x TL leaves (tier tt) and its
+// right-hand neighbour.  Each grouped (tile, K) step carries two 64-bit
+// masks, one per half (node); bit (y * 8 + x) = "the product of row leaf x
+// and column leaf y of that half is kept" (only TL x TL bits are used).
 constexpr int kTileRows = 128;
+constexpr int kTileHalves = 2;
 constexpr int kMaxLeavesPerSide = 1 << 14;
 
 // Device status bits.
@@ -43,7 +46,7 @@ struct DevCtl {
     unsigned long long active_steps;
     unsigned long long ent_off;     // u32 K of each tier-tt triple, grouped by tile
     unsigned long long pk_off;      // u32 K of each (tile, K) step
-    unsigned long long pm_off;      // u64 mask of each (tile, K) step
+    unsigned long long pm_off;      // two u64 masks (left, right half) of each step
     unsigned long long need_words;  // words the whole multiply needs
     unsigned int status;
     unsigned int pad;
@@ -107,7 +110,7 @@ struct spamm_tree {
     int b, d;
     int64_t nb;        // 2^d leaves per side (padded grid)
     int64_t nl;        // ceil(n / b) leaves holding data
-    int64_t nlp;       // nl rounded up to a whole number of tiles (TL leaves)
+    int64_t nlp;       // nl rounded up to whole tile widths (2 TL leaves)
     double* pyr;       // squared norms, all tiers
     int64_t nodes;
     int precision;
@@ -140,7 +143,7 @@ struct spamm_ctx {
     cudaEvent_t ev[4];
     bool timed;
     // last multiply
-    int last_d, last_b, last_prec, last_tt, last_S;
+    int last_d, last_b, last_prec, last_tt, last_S, last_tr, last_tc;
     int64_t last_n, last_tiles;
     double last_tau;
     int last_status;
@@ -157,7 +160,8 @@ namespace spamm {
 spamm_status set_err(spamm_ctx* ctx, spamm_status st, const std::string& msg);
 spamm_status cuda_err(spamm_ctx* ctx, cudaError_t e, const char* what);
 
-int tiles_per_side(const spamm_tree* t);  // nlp / TL
+int tile_rows(const spamm_tree* t);  // nlp / TL
+int tile_cols(const spamm_tree* t);  // nlp / (2 TL)
 
 // norms.cu
 cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s);

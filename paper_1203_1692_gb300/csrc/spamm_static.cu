@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kStaticLeaf = 16;
 constexpr int64_t kStaticMaxN = 4096;
-constexpr size_t kStaticBytes = (size_t)6 << 20;  // 6 MiB
+constexpr size_t kStaticBytes = (size_t)8 << 20;  // 8 MiB
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
@@ -44,7 +44,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // Bytes the worst case (every triple kept) needs for an n x n product.
 struct StaticPlan {
     int d, tt, S;
-    int64_t nb, nl, nlp, nodes, tiles;
+    int64_t nb, nl, nlp, nodes, tiles, tr, tc;
     size_t off_pyrA, off_pyrB, off_ctl, off_tiles, off_pool, pool_words, total;
 };
 
@@ -55,19 +55,20 @@ StaticPlan plan_for(int64_t n) {
     p.d = d;
     p.nb = (int64_t)1 << d;
     p.nl = (n + kStaticLeaf - 1) / kStaticLeaf;
-    const int tl = kTileRows / kStaticLeaf;  // 8 leaves per tile side
-    p.nlp = (p.nl + tl - 1) / tl * tl;
+    const int tl = kTileRows / kStaticLeaf;  // 8 leaves per tile half
+    p.nlp = (p.nl + 2 * tl - 1) / (2 * tl) * (2 * tl);
     p.nodes = (((int64_t)1 << (2 * (d + 1))) - 1) / 3;
     p.tt = d > 3 ? d - 3 : 0;
     p.S = 1 << (d - p.tt);
-    const int64_t tps = p.nlp / tl;
-    p.tiles = tps * tps;
+    p.tr = p.nlp / tl;
+    p.tc = p.nlp / (2 * tl);
+    p.tiles = p.tr * p.tc;
     // worst-case pool: every frontier full, every tier-tt entry with S steps
     int64_t words = 0;
     for (int t = 0; t <= p.tt; ++t) words += (int64_t)1 << (3 * t);
     const int64_t m = (int64_t)1 << (3 * p.tt);
     const int64_t ms = m * p.S;
-    words += (m + 1) / 2 + (ms + 1) / 2 + ms;
+    words += (m + 1) / 2 + (ms + 1) / 2 + 2 * ms;
     p.pool_words = (size_t)words;
     size_t o = 0;
     p.off_pyrA = o; o = align256(o + sizeof(double) * p.nodes);
@@ -136,6 +137,8 @@ extern "C" spamm_status spamm_multiply_static(const float* A, int64_t lda, const
     ctx.tiles_cap = p.tiles;
     ctx.last_S = p.S;
     ctx.last_tt = p.tt;
+    ctx.last_tr = (int)p.tr;
+    ctx.last_tc = (int)p.tc;
 
     spamm_tree ta{}, tb{};
     spamm_tree* trees[2] = {&ta, &tb};

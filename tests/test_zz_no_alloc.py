@@ -89,9 +89,18 @@ def test_static_allocates_no_device_memory_after_setup():
     assert _rel(C.cpu().numpy(), ref) <= TOL
 
 
-def test_static_rejects_sizes_beyond_its_scratch():
+def test_static_accepts_its_maximum_and_rejects_beyond():
     from paper_1203_1692_gb300 import _abi
     L = _abi.lib()
+    n = 4096                                   # the stated maximum
+    Z = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    C = torch.ones((n, n), dtype=torch.float32, device="cuda")
+    st = L.spamm_multiply_static(ctypes.c_void_p(Z.data_ptr()), n, ctypes.c_void_p(Z.data_ptr()),
+                                 n, n, 1e-6, 1.0, 0.5, ctypes.c_void_p(C.data_ptr()), n,
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), None)
+    torch.cuda.synchronize()
+    assert st == _abi.SPAMM_OK
+    assert float(C.max()) == 0.5 and float(C.min()) == 0.5   # A = 0: C = beta * C
     x = torch.zeros((1,), dtype=torch.float32, device="cuda")
     p = ctypes.c_void_p(x.data_ptr())
     n = 4097
