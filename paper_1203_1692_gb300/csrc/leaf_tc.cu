@@ -54,7 +54,7 @@ namespace {
 
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
-constexpr int kChunkIters = 8;  // K-chunks of 16 per TMEM accumulation chunk
+constexpr int kChunkIters = 16;  // K-chunks of 16 per TMEM accumulation chunk
 constexpr int kGroupRows = 8;   // tile rows walked together (L2 reuse)
 constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
@@ -196,8 +196,10 @@ struct PrecTraits {
     static constexpr int kEsize = PREC == SPAMM_PREC_BF16X3 ? 2 : 4;
     static constexpr int kParts = PREC == SPAMM_PREC_TF32 ? 1 : 2;      // arrays per role
     static constexpr int kSlice = 128 * 16 * kEsize;                   // bytes of one 128x16 slice
-    static constexpr int kStage = 3 * kParts * kSlice;                  // A (128) + B (256) rows
-    static constexpr int kStages = PREC == SPAMM_PREC_TF32X3 ? 4 : 8;
+    static constexpr int kIter = 3 * kParts * kSlice;                   // A (128) + B (256) rows
+    static constexpr int kSPS = kIter <= 24576 ? 4 : 2;                 // K-chunks per stage
+    static constexpr int kStage = kSPS * kIter;                         // 96 KB
+    static constexpr int kStages = 2;
     static constexpr int kKInstr = PREC == SPAMM_PREC_BF16X3 ? 16 : 8;  // K per MMA
     static constexpr uint32_t kSBO = 8 * 16 * kEsize;                   // row-group stride
     static constexpr uint32_t kAB = PREC == SPAMM_PREC_BF16X3 ? 1u : 2u;
@@ -228,6 +230,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2],
         bar_drain;
     __shared__ uint32_t tmem_slot;
+    __shared__ unsigned long long st_mask[ST][T::kSPS][2];  // masks of each stage slot
+    __shared__ uint32_t st_count[ST];                        // filled slots of each stage
     __shared__ volatile int abort_flag;
     __shared__ unsigned long long issued_s, consumed_s;
 
@@ -273,74 +277,108 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
 
     if (warp == 0) {
         // ---------------------------------------------------------- producer
-        // The whole warp walks the step list: each lane loads one K of a
-        // batch of 32 (the next batch is prefetched while this one is
-        // issued), and lane 0 issues the copies for each entry in turn.
-        unsigned long long it = 0;
+        // The whole warp walks the step list in batches of 32 (each lane
+        // loads one step's K and masks; the next batch is prefetched while
+        // this one is issued) and lane 0 fills the stages: up to kSPS
+        // K-chunk slots per stage, never across tiles.  For every slot it
+        // adds the slot's bytes to the stage's expected transaction count
+        // and issues the bulk copies; closing a stage records the slots'
+        // masks and count in shared memory and arrives on the full barrier.
+        unsigned long long stage_it = 0;
+        int fill = 0;
+        int s = 0;
         bool ok = true;
+        const size_t piece = (size_t)LEAF * 16 * T::kEsize;
         for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
             const int u = tile_at(k, p.tr, p.tc);
             const int64_t srow = (int64_t)(u / p.tc) * TL;
             const int64_t scol = (int64_t)(u % p.tc) * TLC;
             const uint32_t ns = p.steps[u];
             const uint64_t sb = (uint64_t)p.off[u] * p.S;
-            uint32_t cur = lane < (int)ns ? pk[sb + lane] : 0u;
+            uint32_t ck = lane < (int)ns ? pk[sb + lane] : 0u;
+            unsigned long long cm0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
+            unsigned long long cm1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
             for (uint32_t base = 0; base < ns && ok; base += 32) {
-                const uint32_t nxt = base + 32 + lane < ns ? pk[sb + base + 32 + lane] : 0u;
+                const bool more = base + 32 + lane < ns;
+                const uint32_t nk = more ? pk[sb + base + 32 + lane] : 0u;
+                const unsigned long long nm0 = more ? pm[2 * (sb + base + 32 + lane)] : 0ull;
+                const unsigned long long nm1 = more ? pm[2 * (sb + base + 32 + lane) + 1] : 0ull;
                 const uint32_t cnt = ns - base < 32 ? ns - base : 32;
                 for (uint32_t j = 0; j < cnt && ok; ++j) {
-                    const int64_t K = __shfl_sync(0xffffffffu, cur, j);
-                    for (int kc = 0; kc < CHUNKS && ok; ++kc, ++it) {
+                    const int64_t K = __shfl_sync(0xffffffffu, ck, j);
+                    const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
+                    const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
+                    for (int kc = 0; kc < CHUNKS && ok; ++kc) {
                         if (lane == 0) {
-                            const int s = (int)(it % ST);
-                            const uint32_t ph = (uint32_t)((it / ST) & 1);
-                            if (wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status)) {
+                            if (fill == 0) {
+                                s = (int)(stage_it % ST);
+                                const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
+                                ok = wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status);
+                            }
+                            if (ok) {
                                 const uint32_t full = smem_u32(&bar_full[s]);
-                                mbar_expect_tx(full, T::kStage);
+                                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
+                                             "r"((uint32_t)T::kIter)
+                                             : "memory");
                                 const int64_t row = (K * CHUNKS + kc) * p.nlp;
-                                unsigned char* sbuf = stages + (size_t)s * T::kStage;
-                                const size_t piece = (size_t)LEAF * 16 * T::kEsize;
+                                unsigned char* slot = stages + (size_t)s * T::kStage +
+                                                      (size_t)fill * T::kIter;
 #pragma unroll
                                 for (int part = 0; part < T::kParts; ++part) {
-                                    bulk_g2s(smem_u32(sbuf + part * T::kSlice),
+                                    bulk_g2s(smem_u32(slot + part * T::kSlice),
                                              static_cast<const unsigned char*>(p.pa[part]) +
                                                  (size_t)(row + srow) * piece,
                                              T::kSlice, full);
-                                    bulk_g2s(smem_u32(sbuf + (T::kParts + 2 * part) * T::kSlice),
+                                    bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
                                              static_cast<const unsigned char*>(p.pb[part]) +
                                                  (size_t)(row + scol) * piece,
                                              2 * T::kSlice, full);
                                 }
-                                issued_s = it + 1;
-                            } else {
-                                ok = false;
+                                st_mask[s][fill][0] = m0;
+                                st_mask[s][fill][1] = m1;
+                                if (++fill == T::kSPS) {
+                                    st_count[s] = (uint32_t)fill;
+                                    mbar_arrive(full);
+                                    issued_s = ++stage_it;
+                                    fill = 0;
+                                }
                             }
                         }
                         ok = __shfl_sync(0xffffffffu, ok, 0);
                     }
                 }
-                cur = nxt;
+                ck = nk;
+                cm0 = nm0;
+                cm1 = nm1;
+            }
+            // a stage never spans two tiles
+            if (lane == 0 && fill > 0) {
+                st_count[s] = (uint32_t)fill;
+                mbar_arrive(smem_u32(&bar_full[s]));
+                issued_s = ++stage_it;
+                fill = 0;
             }
         }
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA
-        // Same batching of the step masks; lane 0 issues.  Iteration i of a
+        // Lane 0 alone: per stage one wait and one commit.  Iteration i of a
         // tile (step i / CHUNKS, K-chunk i % CHUNKS) opens a new TMEM chunk
         // when i % kChunkIters == 0 and closes it at the chunk's last
         // iteration; a tile without steps gets one empty (zeroed) chunk.
-        unsigned long long it = 0;
-        uint32_t ccount = 0;  // chunks opened so far (selects the TMEM buffer)
-        bool ok = true;
-        const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
-        const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
-        uint32_t dacc = tmem;
-        for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-            const int u = tile_at(k, p.tr, p.tc);
-            const uint32_t ns = p.steps[u];
-            const uint64_t sb = (uint64_t)p.off[u] * p.S;
-            const uint32_t iters = ns * CHUNKS;
-            if (iters == 0) {
-                if (lane == 0) {
+        if (lane == 0) {
+            unsigned long long stage_it = 0;
+            uint32_t ccount = 0;  // chunks opened so far (selects the TMEM buffer)
+            bool ok = true;
+            const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
+            const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
+            uint32_t dacc = tmem;
+            uint32_t ns_next = blockIdx.x < p.tiles ? p.steps[tile_at(blockIdx.x, p.tr, p.tc)] : 0u;
+            for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
+                const uint32_t ns = ns_next;
+                if (k + (int)gridDim.x < p.tiles)
+                    ns_next = p.steps[tile_at(k + gridDim.x, p.tr, p.tc)];
+                const uint32_t iters = ns * CHUNKS;
+                if (iters == 0) {
                     const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
                     if (wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
                         tc_fence_after();
@@ -351,135 +389,121 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                         ok = false;
                     }
                     ++ccount;
+                    continue;
                 }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                continue;
-            }
-            uint32_t i = 0;
-            unsigned long long cur0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
-            unsigned long long cur1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
-            for (uint32_t base = 0; base < ns && ok; base += 32) {
-                const bool more = base + 32 + lane < ns;
-                const unsigned long long nxt0 = more ? pm[2 * (sb + base + 32 + lane)] : 0ull;
-                const unsigned long long nxt1 = more ? pm[2 * (sb + base + 32 + lane) + 1] : 0ull;
-                const uint32_t cnt = ns - base < 32 ? ns - base : 32;
-                for (uint32_t j = 0; j < cnt && ok; ++j) {
-                    const unsigned long long mask0 = __shfl_sync(0xffffffffu, cur0, j);
-                    const unsigned long long mask1 = __shfl_sync(0xffffffffu, cur1, j);
-                    for (int kc = 0; kc < CHUNKS && ok; ++kc, ++i, ++it) {
-                        if (lane == 0) {
-                            if (i % kChunkIters == 0) {
-                                const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
-                                if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag,
-                                              status))
-                                    ok = false;
-                                tc_fence_after();
-                                dacc = tmem + ab * 256;
-                                // clear the chunk accumulator: 0 * 0, input accumulator off
-                                if (ok)
-                                    mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256),
-                                              dis0, 0u);
-                            }
-                            const int s = (int)(it % ST);
-                            const uint32_t ph = (uint32_t)((it / ST) & 1);
-                            if (ok && !wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status))
+                uint32_t i = 0;
+                while (i < iters && ok) {
+                    const int s = (int)(stage_it % ST);
+                    const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
+                    if (!wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t cnt = st_count[s];
+                    consumed_s = stage_it + 1;
+                    for (uint32_t jj = 0; jj < cnt && ok; ++jj, ++i) {
+                        if (i % kChunkIters == 0) {
+                            const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
+                            if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
                                 ok = false;
-                            if (ok) {
-                                consumed_s = it + 1;
-                                tc_fence_after();
-                                const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
-                                const uint32_t a_hi = sbuf, a_lo = sbuf + T::kSlice;
-                                const uint32_t b_hi = sbuf + T::kParts * T::kSlice;
-                                const uint32_t b_lo = b_hi + 2 * T::kSlice;
-                                // Runs of column leaves with the same kept row leaves:
-                                // a column y starts a run when its row mask is non-zero
-                                // and differs from column y-1's.  Uniform halves (the
-                                // common case on dense blocks) give one run directly.
-                                constexpr unsigned long long kRep =
-                                    TL == 8 ? 0x0101010101010101ull : 0x0000000001010101ull;
-                                const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
-                                const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
-                                const bool u0 = mask0 == (unsigned long long)x0 * kRep;
-                                const bool u1 = mask1 == (unsigned long long)x1 * kRep;
-                                uint32_t starts, nz;
-                                if (u0 && u1) {
-                                    starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
-                                    nz = (x0 ? (1u << TL) - 1u : 0u) |
-                                         (x1 ? ((1u << TL) - 1u) << TL : 0u);
-                                } else {
-                                    starts = 0u;
-                                    nz = 0u;
-                                    uint32_t prev = 0u;
+                                break;
+                            }
+                            tc_fence_after();
+                            dacc = tmem + ab * 256;
+                            // clear the chunk accumulator: 0 * 0, input accumulator off
+                            mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256), dis0, 0u);
+                        }
+                        const unsigned long long mask0 = st_mask[s][jj][0];
+                        const unsigned long long mask1 = st_mask[s][jj][1];
+                        const uint32_t sbuf =
+                            smem_u32(stages + (size_t)s * T::kStage + (size_t)jj * T::kIter);
+                        const uint32_t a_hi = sbuf, a_lo = sbuf + T::kSlice;
+                        const uint32_t b_hi = sbuf + T::kParts * T::kSlice;
+                        const uint32_t b_lo = b_hi + 2 * T::kSlice;
+                        // Runs of column leaves with the same kept row leaves:
+                        // a column y starts a run when its row mask is non-zero
+                        // and differs from column y-1's.  Uniform halves (the
+                        // common case on dense blocks) give one run directly.
+                        constexpr unsigned long long kRep =
+                            TL == 8 ? 0x0101010101010101ull : 0x0000000001010101ull;
+                        const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
+                        const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
+                        const bool u0 = mask0 == (unsigned long long)x0 * kRep;
+                        const bool u1 = mask1 == (unsigned long long)x1 * kRep;
+                        uint32_t starts, nz;
+                        if (u0 && u1) {
+                            starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
+                            nz = (x0 ? (1u << TL) - 1u : 0u) |
+                                 (x1 ? ((1u << TL) - 1u) << TL : 0u);
+                        } else {
+                            starts = 0u;
+                            nz = 0u;
+                            uint32_t prev = 0u;
 #pragma unroll
-                                    for (int yy = 0; yy < TLC; ++yy) {
-                                        const uint32_t xm =
-                                            yy < TL ? (uint32_t)(mask0 >> (8 * yy)) & 0xFFu
-                                                    : (uint32_t)(mask1 >> (8 * (yy - TL))) & 0xFFu;
-                                        if (xm) nz |= 1u << yy;
-                                        if (xm && xm != prev) starts |= 1u << yy;
-                                        prev = xm;
-                                    }
-                                }
-                                uint64_t ah[2], al[2];
-#pragma unroll
-                                for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                    ah[kk] = make_desc(a_hi + (uint32_t)kk * 256u, 128, T::kSBO);
-                                    al[kk] = make_desc(a_lo + (uint32_t)kk * 256u, 128, T::kSBO);
-                                }
-                                while (starts) {
-                                    const int y = __ffs(starts) - 1;
-                                    starts &= starts - 1;
-                                    const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
-                                    const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
-                                    const int len = yend - y;
-                                    const uint32_t xm = y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
-                                                               : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
-                                    uint32_t dis[4];
-#pragma unroll
-                                    for (int w = 0; w < 4; ++w) {
-                                        uint32_t v = 0;
-#pragma unroll
-                                        for (int q = 0; q < 32 / LEAF; ++q) {
-                                            const int x = w * (32 / LEAF) + q;
-                                            if (!((xm >> x) & 1u))
-                                                v |= (LEAF == 32 ? 0xFFFFFFFFu
-                                                                 : (0xFFFFu << (16 * q)));
-                                        }
-                                        dis[w] = v;
-                                    }
-                                    const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
-                                    const uint32_t d = dacc + (uint32_t)(y * LEAF);
-                                    const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
-#pragma unroll
-                                    for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                        const uint32_t koff = (uint32_t)kk * 256u;
-                                        const uint64_t bh =
-                                            make_desc(b_hi + boff + koff, 128, T::kSBO);
-                                        if (PREC != SPAMM_PREC_TF32) {
-                                            const uint64_t bl =
-                                                make_desc(b_lo + boff + koff, 128, T::kSBO);
-                                            mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
-                                            mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
-                                        }
-                                        mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
-                                    }
-                                }
-                                tc_commit(smem_u32(&bar_empty[s]));
-                                if (i % kChunkIters == kChunkIters - 1 || i == iters - 1) {
-                                    tc_commit(smem_u32(&bar_accf[ccount & 1]));
-                                    ++ccount;
-                                }
+                            for (int yy = 0; yy < TLC; ++yy) {
+                                const uint32_t xm =
+                                    yy < TL ? (uint32_t)(mask0 >> (8 * yy)) & 0xFFu
+                                            : (uint32_t)(mask1 >> (8 * (yy - TL))) & 0xFFu;
+                                if (xm) nz |= 1u << yy;
+                                if (xm && xm != prev) starts |= 1u << yy;
+                                prev = xm;
                             }
                         }
-                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        uint64_t ah[2], al[2];
+#pragma unroll
+                        for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                            ah[kk] = make_desc(a_hi + (uint32_t)kk * 256u, 128, T::kSBO);
+                            al[kk] = make_desc(a_lo + (uint32_t)kk * 256u, 128, T::kSBO);
+                        }
+                        while (starts) {
+                            const int y = __ffs(starts) - 1;
+                            starts &= starts - 1;
+                            const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
+                            const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
+                            const int len = yend - y;
+                            const uint32_t xm = y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
+                                                       : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
+                            uint32_t dis[4];
+#pragma unroll
+                            for (int w = 0; w < 4; ++w) {
+                                uint32_t v = 0;
+#pragma unroll
+                                for (int q = 0; q < 32 / LEAF; ++q) {
+                                    const int x = w * (32 / LEAF) + q;
+                                    if (!((xm >> x) & 1u))
+                                        v |= (LEAF == 32 ? 0xFFFFFFFFu
+                                                         : (0xFFFFu << (16 * q)));
+                                }
+                                dis[w] = v;
+                            }
+                            const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
+                            const uint32_t d = dacc + (uint32_t)(y * LEAF);
+                            const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
+#pragma unroll
+                            for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                const uint32_t koff = (uint32_t)kk * 256u;
+                                const uint64_t bh =
+                                    make_desc(b_hi + boff + koff, 128, T::kSBO);
+                                if (PREC != SPAMM_PREC_TF32) {
+                                    const uint64_t bl =
+                                        make_desc(b_lo + boff + koff, 128, T::kSBO);
+                                    mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
+                                    mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
+                                }
+                                mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
+                            }
+                        }
+                        if (i % kChunkIters == kChunkIters - 1 || i == iters - 1) {
+                            tc_commit(smem_u32(&bar_accf[ccount & 1]));
+                            ++ccount;
+                        }
                     }
+                    // the stage's MMAs have read its shared memory once they complete
+                    tc_commit(smem_u32(&bar_empty[s]));
+                    ++stage_it;
                 }
-                cur0 = nxt0;
-                cur1 = nxt1;
             }
-        }
-        // drain: every MMA issued so far has completed before TMEM is freed
-        if (lane == 0) {
+            // drain: every MMA issued so far has completed before TMEM is freed
             tc_commit(smem_u32(&bar_drain));
             wait_bar(smem_u32(&bar_drain), 0, &abort_flag, status);
         }
@@ -558,7 +582,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     // ------------------------------------------------------------ teardown
     __syncthreads();
     if (abort_flag && threadIdx.x == 0) {
-        // copies issued but never consumed must land before the block exits
+        // stages whose copies were issued but never consumed must land
+        // before the block exits
         for (unsigned long long it = consumed_s; it < issued_s; ++it) {
             const int s = (int)(it % ST);
             const uint32_t ph = (uint32_t)((it / ST) & 1);
