@@ -189,6 +189,26 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ GPU arm
 
+def sampled_parity(A_h, C, b, tau, count=48, seed=1):
+    """max|dC| / max|C| of the GPU result against the FP64 oracle at the same
+    tau, on sampled C blocks (plus diagonal ones)."""
+    from oracle import oracle as O
+    n = A_h.shape[0]
+    nl = -(-n // b)
+    rng = np.random.default_rng(seed)
+    ij = [tuple(map(int, x)) for x in rng.integers(0, nl, size=(count, 2))]
+    ij += [(q, q) for q in rng.integers(0, nl, size=8).tolist()]
+    pa = O.pyramid(A_h, b)
+    ref, _ = O.blocks(A_h, A_h, b, tau, ij, pa, pa)
+    Ch = C.cpu().numpy()
+    got = np.zeros_like(ref)
+    for q, (I, J) in enumerate(ij):
+        blk = Ch[I * b:min(n, (I + 1) * b), J * b:min(n, (J + 1) * b)]
+        got[q, :blk.shape[0], :blk.shape[1]] = blk
+    return {"rel_max_err_vs_oracle": float(np.abs(got - ref).max() / np.abs(ref).max()),
+            "blocks": len(ij), "tau": tau}
+
+
 def run_quick(args, P, A, n, b, stream):
     """Time the SpAMM step alone at a fixed tau (no reference products)."""
     import torch
@@ -295,6 +315,7 @@ def main():
     ctx.multiply(tree, tree, tau, C=C)
     err_tau = float((C.double() - C_exact).abs().max())
     del C_exact
+    parity = sampled_parity(A_h, C, b, tau)
     torch.cuda.empty_cache()
 
     # --- timed steps on resident inputs ----------------------------------
@@ -407,6 +428,7 @@ def main():
         "kept_leaf_triples": st["leaf_triples"], "kept_fraction":
             st["leaf_triples"] / float(-(-n // b)) ** 3,
         "ms_symbolic": st0["ms_symbolic"], "ms_numeric": leaf_ms,
+        "parity_sampled": parity,
         "tau_sweep": sweep, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": kernels_per_step(st["depth"], b) * args.steps, "clocks": clk,
     }

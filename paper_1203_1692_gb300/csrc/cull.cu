@@ -261,7 +261,6 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
                                                    const uint32_t* __restrict__ off,
                                                    uint32_t* __restrict__ steps, int tc) {
     constexpr int S = 1 << DS;               // K leaves per tier-tt K'
-    constexpr int PAIRS = S * S;             // leaf pairs (x, y) of one slice and half
     constexpr int WIN = 2048;                // steps per window (32 KB of masks)
     constexpr int KPW = WIN / S;             // K' per window
     extern __shared__ uint32_t dyn[];        // K' bitmaps of both halves, then the K' list
@@ -314,56 +313,80 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
     unsigned long long cand[4] = {0, 0, 0, 0}, kept[4] = {0, 0, 0, 0}, tie = 0;
     for (int kw = 0; kw < nk; kw += KPW) {
         const int kn = min(KPW, nk - kw);
-        // phase 1: one warp per (K', kk) slice, both halves
-        for (int item = warp; item < kn * S; item += 16) {
-            const int g = item / S, kk = item % S;
+        // phase 1: one warp per (K', half) sub-cube; each tier below the
+        // tile node is evaluated once, 8^l triples spread over the lanes,
+        // and shared through ballots (bit index (k * side + y) * side + x).
+        for (int item = warp; item < 2 * kn; item += 16) {
+            const int g = item >> 1, half = item & 1;
             const uint32_t Kp = klist[kw + g];
-            const bool has0 = ((bm0[Kp >> 5] >> (Kp & 31)) & 1u) != 0;
-            const bool has1 = ((bm1[Kp >> 5] >> (Kp & 31)) & 1u) != 0;
-            unsigned long long bits0 = 0ull, bits1 = 0ull;
+            const bool has = half ? ((bm1[Kp >> 5] >> (Kp & 31)) & 1u) != 0
+                                  : ((bm0[Kp >> 5] >> (Kp & 31)) & 1u) != 0;
+            const uint32_t J0 = Jp * 2 + half;
+            unsigned long long prev = has ? 1ull : 0ull;  // tier-tt node kept
+            unsigned long long lv2[2] = {0ull, 0ull};    // level-2 bits (64)
 #pragma unroll
-            for (int hh = 0; hh < (2 * PAIRS + 31) / 32; ++hh) {
-                const int pidx = lane + 32 * hh;
-                const int half = pidx / PAIRS;
-                if (pidx < 2 * PAIRS && (half ? has1 : has0)) {
-                    const int q = pidx % PAIRS;
-                    const int x = q % S, y = q / S;
-                    const uint32_t J0 = Jp * 2 + half;
-                    bool alive = true;
+            for (int l = 1; l <= DS; ++l) {
+                const int side = 1 << l;
+                const int per = side * side * side;
+                const int t = tt + l;
+                const int64_t w = (int64_t)1 << t;
+                const int64_t off_t = (((int64_t)1 << (2 * t)) - 1) / 3;
 #pragma unroll
-                    for (int l = 1; l <= DS; ++l) {
-                        const int sh = DS - l;
-                        const int t = tt + l;
-                        const int64_t w = (int64_t)1 << t;
-                        const int64_t off_t = (((int64_t)1 << (2 * t)) - 1) / 3;
-                        const int64_t i = ((int64_t)I0 << l) + (x >> sh);
-                        const int64_t k = ((int64_t)Kp << l) + (kk >> sh);
-                        const int64_t j = ((int64_t)J0 << l) + (y >> sh);
+                for (int r = 0; r < (per + 31) / 32; ++r) {
+                    const int idx = lane + 32 * r;
+                    const int xi = idx & (side - 1), yi = (idx >> l) & (side - 1),
+                              ki = idx >> (2 * l);
+                    // parent bit at level l - 1
+                    const int ps = side >> 1;
+                    const int pidx = ((ki >> 1) * ps + (yi >> 1)) * ps + (xi >> 1);
+                    bool par;
+                    if (l == 1) par = prev != 0ull;
+                    else if (l == 2) par = (prev >> pidx) & 1ull;
+                    else par = (lv2[pidx >> 5 >> 1] >> (pidx & 63)) & 1ull;
+                    bool ok = false;
+                    if (idx < per && par) {
+                        const int64_t i = ((int64_t)I0 << l) + xi;
+                        const int64_t k = ((int64_t)Kp << l) + ki;
+                        const int64_t j = ((int64_t)J0 << l) + yi;
                         bool tb;
-                        const bool ok = spamm_keep(pyrA[off_t + i * w + k],
-                                                   pyrB[off_t + k * w + j], th, &tb);
-                        // count each tier-t triple once: at its first leaf
-                        const int rep = (1 << sh) - 1;
-                        if (alive && ((x | y | kk) & rep) == 0) {
-                            cand[l - 1] += 1;
-                            kept[l - 1] += ok ? 1 : 0;
-                            tie += tb ? 1 : 0;
-                        }
-                        alive = alive && ok;
+                        ok = spamm_keep(pyrA[off_t + i * w + k], pyrB[off_t + k * w + j], th, &tb);
+                        cand[l - 1] += 1;
+                        kept[l - 1] += ok ? 1 : 0;
+                        tie += tb ? 1 : 0;
                     }
-                    if (alive) {
-                        if (half) bits1 |= 1ull << (y * 8 + x);
-                        else bits0 |= 1ull << (y * 8 + x);
+                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    if (l == DS) {
+                        // leaf level: the mask of leaf column K' * S + ki
+                        if (DS == 3) {
+                            const int kk = r >> 1;           // uniform across the warp
+                            if (lane == 0) {
+                                if ((r & 1) == 0) masks[g * S + kk][half] = bal;
+                                else masks[g * S + kk][half] |= (unsigned long long)bal << 32;
+                            }
+                        } else {
+                            // remap bit (ki, yi, xi) -> mask of ki, bit yi * 8 + xi
+                            const unsigned long long bit = ok ? 1ull << (yi * 8 + xi) : 0ull;
+#pragma unroll
+                            for (int kq = 0; kq < S; ++kq) {
+                                const unsigned long long mine = (idx < per && ki == kq) ? bit : 0ull;
+                                const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)mine);
+                                const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(mine >> 32));
+                                if (r == 0 && lane == 0) masks[g * S + kq][half] = 0ull;
+                                if (lane == 0) masks[g * S + kq][half] |= ((unsigned long long)hi << 32) | lo;
+                            }
+                        }
+                    } else if (l == 1) {
+                        prev = bal & 0xFFu;
+                    } else if (l == 2) {
+                        if (r == 0) lv2[0] = bal;
+                        else lv2[0] |= (unsigned long long)bal << 32;
                     }
                 }
+                if (l == 2) prev = lv2[0];
+                if (l == 2) lv2[1] = 0ull;
             }
-            const uint32_t lo0 = __reduce_or_sync(0xffffffffu, (uint32_t)bits0);
-            const uint32_t hi0 = __reduce_or_sync(0xffffffffu, (uint32_t)(bits0 >> 32));
-            const uint32_t lo1 = __reduce_or_sync(0xffffffffu, (uint32_t)bits1);
-            const uint32_t hi1 = __reduce_or_sync(0xffffffffu, (uint32_t)(bits1 >> 32));
-            if (lane == 0) {
-                masks[item][0] = ((unsigned long long)hi0 << 32) | lo0;
-                masks[item][1] = ((unsigned long long)hi1 << 32) | lo1;
+            if (DS == 0) {
+                if (lane == 0) masks[g][half] = has ? 1ull : 0ull;
             }
         }
         __syncthreads();

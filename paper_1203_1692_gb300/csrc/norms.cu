@@ -85,13 +85,15 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
 }
 
 // Leaf norms plus tensor-core packs.  A block owns one leaf row-strip (b
-// rows) x 128 columns (TL leaves): it stages the strip in shared memory,
-// forms the leaf squared norms (FP64), splits every element into hi/lo
-// parts, writes them into shared-memory copies of the A-role and B-role
-// pieces, and then streams the pieces out with 16-byte stores: the A-role
+// rows) x 128 columns (TL leaves).  It stages the strip in shared memory
+// (16-byte loads) while forming the leaf squared norms (FP64), then produces
+// the pieces in output order: thread t writes the t-th, (t+128)-th, ...
+// 16-byte unit of each piece, reading the elements that unit holds from the
+// staged strip (a row quad for the A role, a column quad for the B role),
+// splitting them into hi/lo parts and storing both parts.  The A-role
 // pieces of one leaf and the B-role pieces of one K-chunk are contiguous in
-// HBM, so every global write is coalesced.  PK: 1 tf32 hi, 2 tf32 hi+lo,
-// 3 bf16 hi+lo.
+// HBM, so consecutive threads write consecutive 16-byte units: every global
+// store is coalesced.  PK: 1 tf32 hi, 2 tf32 hi+lo, 3 bf16 hi+lo.
 template <int PK, int LEAF>
 __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, int64_t n,
                                                    int64_t lda, int64_t nb, int64_t nl, int64_t nlp,
@@ -101,10 +103,12 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     constexpr int TL = 128 / LEAF;
     constexpr int CH = LEAF / 16;
     constexpr int ES = PK == 3 ? 2 : 4;                  // element bytes
+    constexpr int EPU = 16 / ES;                         // elements per 16-byte unit
     constexpr int PIECE = LEAF * 16 * ES;                // bytes of one piece
-    constexpr int BUF = TL * CH * PIECE;                 // = 128 * LEAF * ES
-    constexpr int NBUF = PK == 1 ? 2 : 4;                // A hi, (A lo), B hi, (B lo)
-    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int UPP = PIECE / 16;                      // units per piece
+    constexpr int CPC = 16 / EPU;                        // core matrices per 16-wide K chunk
+    constexpr int LDS = 128 + 4;                         // padded staging row
+    __shared__ __align__(16) float raw[LEAF][LDS];
     __shared__ double part[4][TL];
     const int64_t I = blockIdx.y;                        // leaf row
     const int64_t Q0 = (int64_t)blockIdx.x * TL;         // first leaf column
@@ -112,13 +116,8 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
-    unsigned char* bufA0 = sm;
-    unsigned char* bufA1 = sm + BUF;
-    unsigned char* bufB0 = sm + (NBUF / 2) * BUF;
-    unsigned char* bufB1 = bufB0 + BUF;
-    // thread t owns columns 4*(t%32)..+3 of rows t/32, t/32+4, ...
     const int cq = 4 * lane;
-    const int x = cq / LEAF, kk = cq % LEAF;            // leaf, column inside it
+    const int x = cq / LEAF;
     double s = 0.0;
 #pragma unroll 4
     for (int r = warp; r < LEAF; r += 4) {
@@ -140,81 +139,95 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
         s += dy * dy;
         s += dz * dz;
         s += dw * dw;
-        const float f[4] = {v.x, v.y, v.z, v.w};
-        const int kc = kk >> 4, kq = kk & 15;            // A role: row r, k = kk
-        const int bkc = r >> 4, bkq = r & 15;            // B role: n = kk + q, k = r
-        if (PK != 3) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                h[q] = to_tf32(f[q]);
-                l[q] = to_tf32(f[q] - __uint_as_float(h[q]));
-            }
-            const int offA = (x * CH + kc) * PIECE + ((r & 7) * 4 + (r >> 3) * 128 + (kq >> 2) * 32) * 4;
-            *reinterpret_cast<uint4*>(bufA0 + offA) = make_uint4(h[0], h[1], h[2], h[3]);
-            if (PK == 2) *reinterpret_cast<uint4*>(bufA1 + offA) = make_uint4(l[0], l[1], l[2], l[3]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int nn = kk + q;
-                const int offB = (bkc * TL + x) * PIECE +
-                                 ((nn & 7) * 4 + (nn >> 3) * 128 + (bkq & 3) + (bkq >> 2) * 32) * 4;
-                *reinterpret_cast<uint32_t*>(bufB0 + offB) = h[q];
-                if (PK == 2) *reinterpret_cast<uint32_t*>(bufB1 + offB) = l[q];
-            }
-        } else {
-            __nv_bfloat16 h[4], l[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                h[q] = __float2bfloat16_rn(f[q]);
-                l[q] = __float2bfloat16_rn(f[q] - __bfloat162float(h[q]));
-            }
-            const int offA = (x * CH + kc) * PIECE + ((r & 7) * 8 + (r >> 3) * 128 + (kq & 7) + (kq >> 3) * 64) * 2;
-            uint2 hv, lv;
-            hv.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
-            hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
-            lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
-            lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
-            *reinterpret_cast<uint2*>(bufA0 + offA) = hv;
-            *reinterpret_cast<uint2*>(bufA1 + offA) = lv;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int nn = kk + q;
-                const int offB = (bkc * TL + x) * PIECE +
-                                 ((nn & 7) * 8 + (nn >> 3) * 128 + (bkq & 7) + (bkq >> 3) * 64) * 2;
-                *reinterpret_cast<__nv_bfloat16*>(bufB0 + offB) = h[q];
-                *reinterpret_cast<__nv_bfloat16*>(bufB1 + offB) = l[q];
-            }
-        }
+        *reinterpret_cast<float4*>(&raw[r][cq]) = v;
     }
     // leaf squared norms: lanes of one leaf, then the four warps, fixed order
     constexpr int LPL = LEAF / 4;                        // lanes per leaf
-    if (LPL <= 32) {
-        for (int o = (LPL < 32 ? LPL : 32) >> 1; o > 0; o >>= 1)
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    if (LEAF <= 128 && (lane % LPL) == 0) part[warp][x] = s;
+    for (int o = LPL >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((lane % LPL) == 0) part[warp][x] = s;
     __syncthreads();
     if (t < TL) {
         const double v = ((part[0][t] + part[1][t]) + part[2][t]) + part[3][t];
         if (Q0 + t < nl) leaf[I * nb + Q0 + t] = v;
     }
-    // stream the pieces out with 16-byte stores
-    const size_t piece = PIECE;
-    for (int w = 0; w < NBUF / 2; ++w) {
-        const unsigned char* srcA = w ? bufA1 : bufA0;
-        const unsigned char* srcB = w ? bufB1 : bufB0;
-        unsigned char* dA = static_cast<unsigned char*>(w ? pa1 : pa0);
-        unsigned char* dB = static_cast<unsigned char*>(w ? pb1 : pb0);
-        for (int e = t; e < BUF / 16; e += 128) {
-            const int pc = (e * 16) / PIECE, inner = (e * 16) % PIECE;
-            // A role: piece (leaf x, chunk kc) -> ((Q * CH + kc) * nlp + I)
+    // pieces, in output order
+    constexpr int UNITS = TL * CH * UPP;                 // per role and part
+    for (int u = t; u < UNITS; u += 128) {
+        const int pc = u / UPP, w = u % UPP;
+        // unit w of a piece: row group w / (8 CPC), core (w / 8) % CPC, row w % 8
+        const int rg = w / (8 * CPC), core = (w / 8) % CPC, rr = w % 8;
+        const int prow = rg * 8 + rr;                    // row of the piece (b of them)
+        // ---- A role: piece (leaf xa, chunk kca): rows = i, k contiguous
+        {
             const int xa = pc / CH, kca = pc % CH;
-            const size_t ga = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * piece + inner;
-            *reinterpret_cast<uint4*>(dA + ga) = *reinterpret_cast<const uint4*>(srcA + e * 16);
-            // B role: piece (chunk kc, leaf x) -> ((I * CH + kc) * nlp + Q)
+            const float* src = &raw[prow][xa * LEAF + kca * 16 + core * EPU];
+            const size_t g = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * PIECE + (size_t)w * 16;
+            if (PK != 3) {
+                const float4 v = *reinterpret_cast<const float4*>(src);
+                uint4 h, l;
+                h.x = to_tf32(v.x); l.x = to_tf32(v.x - __uint_as_float(h.x));
+                h.y = to_tf32(v.y); l.y = to_tf32(v.y - __uint_as_float(h.y));
+                h.z = to_tf32(v.z); l.z = to_tf32(v.z - __uint_as_float(h.z));
+                h.w = to_tf32(v.w); l.w = to_tf32(v.w - __uint_as_float(h.w));
+                *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pa0) + g) = h;
+                if (PK == 2) *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pa1) + g) = l;
+            } else {
+                const float4 v0 = *reinterpret_cast<const float4*>(src);
+                const float4 v1 = *reinterpret_cast<const float4*>(src + 4);
+                const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * q]);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * q] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * q + 1] - __bfloat162float(h1));
+                    hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pa0) + g) =
+                    make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pa1) + g) =
+                    make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+        }
+        // ---- B role: piece (chunk kcb, leaf xb): rows = column j of the leaf,
+        //      k = row of the leaf contiguous
+        {
             const int kcb = pc / TL, xb = pc % TL;
-            const size_t gb = ((size_t)(I * CH + kcb) * nlp + (Q0 + xb)) * piece + inner;
-            *reinterpret_cast<uint4*>(dB + gb) = *reinterpret_cast<const uint4*>(srcB + e * 16);
+            const int colj = xb * LEAF + prow;           // staged column
+            const int k0 = kcb * 16 + core * EPU;        // staged first row
+            const size_t g = ((size_t)(I * CH + kcb) * nlp + (Q0 + xb)) * PIECE + (size_t)w * 16;
+            if (PK != 3) {
+                float f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) f[q] = raw[k0 + q][colj];
+                uint4 h, l;
+                h.x = to_tf32(f[0]); l.x = to_tf32(f[0] - __uint_as_float(h.x));
+                h.y = to_tf32(f[1]); l.y = to_tf32(f[1] - __uint_as_float(h.y));
+                h.z = to_tf32(f[2]); l.z = to_tf32(f[2] - __uint_as_float(h.z));
+                h.w = to_tf32(f[3]); l.w = to_tf32(f[3] - __uint_as_float(h.w));
+                *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pb0) + g) = h;
+                if (PK == 2) *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pb1) + g) = l;
+            } else {
+                float f[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) f[q] = raw[k0 + q][colj];
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * q]);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * q] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * q + 1] - __bfloat162float(h1));
+                    hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pb0) + g) =
+                    make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pb1) + g) =
+                    make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
         }
     }
 }
@@ -280,16 +293,9 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
     } else {
         const int tl = 128 / t->b;
         dim3 grid((unsigned)(t->nlp / tl), (unsigned)t->nl);
-        const int es = pk == 3 ? 2 : 4;
-        const int nbuf = pk == 1 ? 2 : 4;
-        const size_t dsm = (size_t)nbuf * 128 * t->b * es;
-#define SPAMM_LP(PKV, LV)                                                                     \
-    do {                                                                                      \
-        cudaFuncSetAttribute(k_leaf_pack<PKV, LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)dsm);                                                       \
-        k_leaf_pack<PKV, LV><<<grid, 128, dsm, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp,   \
-                                                    leaf, pa0, pa1, pb0, pb1);                \
-    } while (0)
+#define SPAMM_LP(PKV, LV)                                                                   \
+    k_leaf_pack<PKV, LV><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp, leaf, \
+                                              pa0, pa1, pb0, pb1)
         if (t->b == 16) {
             if (pk == 1) SPAMM_LP(1, 16);
             else if (pk == 2) SPAMM_LP(2, 16);
