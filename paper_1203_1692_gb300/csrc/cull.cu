@@ -261,10 +261,12 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
                                                    const uint32_t* __restrict__ off,
                                                    uint32_t* __restrict__ steps, int tc) {
     constexpr int S = 1 << DS;               // K leaves per tier-tt K'
-    constexpr int WIN = 2048;                // steps per window (32 KB of masks)
+    constexpr int WIN = 1024;                // steps per window (16 KB of masks)
     constexpr int KPW = WIN / S;             // K' per window
     extern __shared__ uint32_t dyn[];        // K' bitmaps of both halves, then the K' list
     __shared__ unsigned long long masks[WIN][2];
+    // per-warp staged norms of one sub-cube: levels 1..DS, A side [x][k], B side [k][y]
+    __shared__ double nA[16][2 + 8 + 32 + 64], nB[16][2 + 8 + 32 + 64];
     __shared__ uint32_t warp_sums[16], total_s;
     __shared__ unsigned long long st_cand[4], st_kept[4], st_tie;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
@@ -328,9 +330,23 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
             for (int l = 1; l <= DS; ++l) {
                 const int side = 1 << l;
                 const int per = side * side * side;
-                const int t = tt + l;
-                const int64_t w = (int64_t)1 << t;
-                const int64_t off_t = (((int64_t)1 << (2 * t)) - 1) / 3;
+                const int so = l == 1 ? 0 : l == 2 ? 4 : 20;
+                // stage this level's norms ([x][k] for A, [k][y] for B) only if
+                // the level above kept something
+                const bool any = l == 1 ? prev != 0ull : l == 2 ? prev != 0ull : lv2[0] != 0ull;
+                if (any) {
+                    const int t = tt + l;
+                    const int64_t w = (int64_t)1 << t;
+                    const int64_t off_t = (((int64_t)1 << (2 * t)) - 1) / 3;
+                    for (int e = lane; e < side * side; e += 32) {
+                        const int rr = e / side, cc = e % side;
+                        nA[warp][so + e] =
+                            pyrA[off_t + (((int64_t)I0 << l) + rr) * w + ((int64_t)Kp << l) + cc];
+                        nB[warp][so + e] =
+                            pyrB[off_t + (((int64_t)Kp << l) + rr) * w + ((int64_t)J0 << l) + cc];
+                    }
+                }
+                __syncwarp();
 #pragma unroll
                 for (int r = 0; r < (per + 31) / 32; ++r) {
                     const int idx = lane + 32 * r;
@@ -345,11 +361,9 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
                     else par = (lv2[pidx >> 5 >> 1] >> (pidx & 63)) & 1ull;
                     bool ok = false;
                     if (idx < per && par) {
-                        const int64_t i = ((int64_t)I0 << l) + xi;
-                        const int64_t k = ((int64_t)Kp << l) + ki;
-                        const int64_t j = ((int64_t)J0 << l) + yi;
                         bool tb;
-                        ok = spamm_keep(pyrA[off_t + i * w + k], pyrB[off_t + k * w + j], th, &tb);
+                        ok = spamm_keep(nA[warp][so + xi * side + ki], nB[warp][so + ki * side + yi],
+                                        th, &tb);
                         cand[l - 1] += 1;
                         kept[l - 1] += ok ? 1 : 0;
                         tie += tb ? 1 : 0;
@@ -388,6 +402,7 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
             if (DS == 0) {
                 if (lane == 0) masks[g][half] = has ? 1ull : 0ull;
             }
+            __syncwarp();  // staged norms are reused by the next sub-cube
         }
         __syncthreads();
         // phase 2: ordered compaction of the window's masks (ascending K)
@@ -453,9 +468,8 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
     const size_t dsm = sizeof(uint32_t) * (2 * words + ((size_t)1 << tt));
 #define SPAMM_TC(DSV)                                                                          \
     do {                                                                                       \
-        if (dsm > 48 * 1024)                                                                   \
-            cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)dsm);                                                    \
+        cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                             (int)dsm);                                                        \
         k_tile_cull<DSV><<<tiles, 512, dsm, s>>>(tt, A->pyr, B->pyr, th, ctx->ctl,             \
                                                  ctx->pool, ctx->tile_off, ctx->tile_steps,    \
                                                  tc);                                          \

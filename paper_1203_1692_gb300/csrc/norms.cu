@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     constexpr int LDS = 128 + 4;                         // padded staging row
     __shared__ __align__(16) float raw[LEAF][LDS];
     __shared__ double part[4][TL];
-    const int64_t I = blockIdx.y;                        // leaf row
-    const int64_t Q0 = (int64_t)blockIdx.x * TL;         // first leaf column
+    // leaf rows vary fastest across blocks, so the blocks running at once
+    // write neighbouring A-role pieces
+    const int64_t I = blockIdx.x;                        // leaf row
+    const int64_t Q0 = (int64_t)blockIdx.y * TL;         // first leaf column
     const int64_t r0 = I * LEAF, c0 = Q0 * LEAF;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
@@ -292,7 +294,7 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
             k_leaf_norms<false><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->b, t->nb, t->nl, leaf);
     } else {
         const int tl = 128 / t->b;
-        dim3 grid((unsigned)(t->nlp / tl), (unsigned)t->nl);
+        dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));
 #define SPAMM_LP(PKV, LV)                                                                   \
     k_leaf_pack<PKV, LV><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp, leaf, \
                                               pa0, pa1, pb0, pb1)
