@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_group_scatter(int tt, DevCtl* ctl,
     }
 }
 
-// Block-wide exclusive scan of one value per thread (blockDim = 512).
+// Block-wide exclusive scan of one value per thread (blockDim <= 512).
 __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t x = v;
@@ -244,7 +244,9 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 }
 
 // Finish the cull of one tile's sub-cubes (DS = d - tt tiers below the tile
-// nodes) and emit its (K, masks) steps in ascending K.  blockDim = 512.
+// nodes) and emit its (K, masks) steps in ascending K.  kCullWarps warps per
+// block, several blocks per SM so that one tile's barriers overlap another
+// tile's work.
 //
 // One warp evaluates one (K', kk) slice: the S x S leaf pairs (x, y) of
 // leaf column K = K' * S + kk in each half whose node has the entry
@@ -254,8 +256,10 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 // into the two 64-bit masks of that K.  Slices are independent, so no
 // block-wide synchronisation is needed between tiers; the masks of a window
 // of K values are then compacted in ascending K.
+constexpr int kCullWarps = 8;
+
 template <int DS>
-__global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restrict__ pyrA,
+__global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(int tt, const double* __restrict__ pyrA,
                                                    const double* __restrict__ pyrB, Thresh th,
                                                    DevCtl* ctl, uint64_t* __restrict__ pool,
                                                    const uint32_t* __restrict__ off,
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
     extern __shared__ uint32_t dyn[];        // K' bitmaps of both halves, then the K' list
     __shared__ unsigned long long masks[WIN][2];
     // per-warp staged norms of one sub-cube: levels 1..DS, A side [x][k], B side [k][y]
-    __shared__ double nA[16][2 + 8 + 32 + 64], nB[16][2 + 8 + 32 + 64];
+    __shared__ double nA[kCullWarps][84], nB[kCullWarps][84];
     __shared__ uint32_t warp_sums[16], total_s;
     __shared__ unsigned long long st_cand[4], st_kept[4], st_tie;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(512) k_tile_cull(int tt, const double* __restr
         // phase 1: one warp per (K', half) sub-cube; each tier below the
         // tile node is evaluated once, 8^l triples spread over the lanes,
         // and shared through ballots (bit index (k * side + y) * side + x).
-        for (int item = warp; item < 2 * kn; item += 16) {
+        for (int item = warp; item < 2 * kn; item += kCullWarps) {
             const int g = item >> 1, half = item & 1;
             const uint32_t Kp = klist[kw + g];
             const bool has = half ? ((bm1[Kp >> 5] >> (Kp & 31)) & 1u) != 0
@@ -470,7 +474,9 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
     do {                                                                                       \
         cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                              (int)dsm);                                                        \
-        k_tile_cull<DSV><<<tiles, 512, dsm, s>>>(tt, A->pyr, B->pyr, th, ctx->ctl,             \
+        cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
+                             100);                                                             \
+        k_tile_cull<DSV><<<tiles, kCullWarps * 32, dsm, s>>>(tt, A->pyr, B->pyr, th, ctx->ctl,             \
                                                  ctx->pool, ctx->tile_off, ctx->tile_steps,    \
                                                  tc);                                          \
     } while (0)
