@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--sites", type=int, default=300,
                    help="water-like workload: number of sites (n = 25 x sites)")
+    p.add_argument("--alt", default="bf16x3",
+                   help="also time this leaf precision on the same workload ('' = off)")
     p.add_argument("--quick", action="store_true",
                    help="time the SpAMM step only at a fixed --tau (for profiling)")
     return p.parse_args()
@@ -209,6 +211,36 @@ def sampled_parity(A_h, C, b, tau, count=48, seed=1):
             "blocks": len(ij), "tau": tau}
 
 
+def measure_alt(P, precision, A, A_h, b, tau, C_exact, stream, steps, t_sgemm):
+    """The same step in another leaf precision: time, max error against the
+    FP64 product and sampled parity against the oracle."""
+    import torch
+    ctx = P.Context(leaf=b, precision=precision, checked=True)
+    tree = ctx.build_norms(A)
+    C = torch.empty_like(A)
+    ctx.multiply(tree, tree, tau, C=C)
+    err = float((C.double() - C_exact).abs().max())
+    parity = sampled_parity(A_h, C, b, tau)
+    ctx.set_checked(False)
+    for _ in range(3):
+        tree.rebuild(A)
+        ctx.multiply(tree, tree, tau, C=C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        tree.rebuild(A)
+        ctx.multiply(tree, tree, tau, C=C)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.close()
+    return {"precision": precision, "value": st["kept_flops"] / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "ms_per_step": ms, "speedup_vs_sgemm": t_sgemm / ms,
+            "max_err": err, "parity_sampled": parity}
+
+
 def run_quick(args, P, A, n, b, stream):
     """Time the SpAMM step alone at a fixed tau (no reference products)."""
     import torch
@@ -275,9 +307,7 @@ def main():
     torch.backends.cuda.matmul.allow_tf32 = False
     A64h = A_h.astype(np.float64)
     C_exact = torch.from_numpy(A64h @ A64h).to(dev)       # host FP64 DGEMM (numpy)
-    A64 = A.double()
-    dgemm_dev = float((A64 @ A64 - C_exact).abs().max())   # diagnostic: GPU FP64 matmul
-    del A64, A64h
+    del A64h
     C_sgemm = A @ A
     torch.cuda.synchronize()
     err_sgemm = float((C_sgemm.double() - C_exact).abs().max())
@@ -314,8 +344,11 @@ def main():
         tau = float(args.tau)
     ctx.multiply(tree, tree, tau, C=C)
     err_tau = float((C.double() - C_exact).abs().max())
-    del C_exact
     parity = sampled_parity(A_h, C, b, tau)
+    alt = None
+    if args.alt and args.alt != args.precision:
+        alt = measure_alt(P, args.alt, A, A_h, b, tau, C_exact, stream, args.steps, t_sgemm)
+    del C_exact
     torch.cuda.empty_cache()
 
     # --- timed steps on resident inputs ----------------------------------
@@ -423,12 +456,11 @@ def main():
         "speedup_vs_sgemm": t_sgemm / ms_step,
         "sgemm_ms": t_sgemm, "effective_tflops": 2.0 * n ** 3 / (ms_step * 1e-3) / 1e12,
         "max_err": err_tau, "sgemm_max_err": err_sgemm, "max_abs_C": scale,
-        "gpu_dgemm_max_dev": dgemm_dev,
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
         "kept_leaf_triples": st["leaf_triples"], "kept_fraction":
             st["leaf_triples"] / float(-(-n // b)) ** 3,
         "ms_symbolic": st0["ms_symbolic"], "ms_numeric": leaf_ms,
-        "parity_sampled": parity,
+        "parity_sampled": parity, "alt_precision": alt,
         "tau_sweep": sweep, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": kernels_per_step(st["depth"], b) * args.steps, "clocks": clk,
     }
