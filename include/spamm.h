@@ -171,6 +171,27 @@ spamm_status spamm_tree_norms(spamm_ctx *ctx, const spamm_tree *tree, double *ho
 spamm_status spamm_multiply(spamm_ctx *ctx, const spamm_tree *A, const spamm_tree *B,
                             double tau, float alpha, float beta, float *C, int64_t ldc);
 
+/* Batched form of spamm_multiply (same Eqs. and algorithm) for `count`
+ * independent products of possibly different n:
+ *   C[p] = alpha[p] * SpAMM(A[p], B[p]; tau[p]) + beta[p] * C[p],  p < count.
+ * All trees must be built under ctx's configuration (leaf size, precision);
+ * A[p] and B[p] have the same n.  Stages 2-3 run per product in a
+ * sub-context of ctx (own pool, created on first use and kept); stage 4 of
+ * all products is one persistent launch over the concatenated list of C
+ * tiles (up to 64 products per launch) on the tensor-core precisions, one
+ * launch per product for SPAMM_PREC_FP32.  Every product's C is the same,
+ * bit for bit, as a single spamm_multiply of it.  Arrays are host arrays of
+ * length count; matrices are device memory.  In checked mode the call waits,
+ * grows the pool of any product that overflowed and re-runs the batch; with
+ * checked == 0 it is asynchronous and can be captured in a CUDA graph once
+ * the sub-contexts exist (after a first call).  spamm_stats then reports
+ * counts and flops summed over the batch.  INVALID_ARG, NONFINITE, CAPACITY,
+ * TIMEOUT, OOM, CUDA. */
+spamm_status spamm_multiply_batched(spamm_ctx *ctx, int32_t count, const spamm_tree *const *A,
+                                    const spamm_tree *const *B, const double *tau,
+                                    const float *alpha, const float *beta, float *const *C,
+                                    const int64_t *ldc);
+
 /* End-to-end form with HOST matrices (row-major, ld = n): copies A and B
  * (and C when beta != 0) to device buffers owned by ctx, builds both trees,
  * multiplies and copies C back.  B may be NULL or equal to A for a square.

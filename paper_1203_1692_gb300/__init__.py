@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _abi
 from ._abi import (PRECISIONS, SpammError, spamm_build_norms, spamm_config_default,  # noqa: F401
-                   spamm_create, spamm_destroy, spamm_multiply, spamm_multiply_host,
+                   spamm_create, spamm_destroy, spamm_multiply, spamm_multiply_batched,
+                   spamm_multiply_host,
                    spamm_reserve, spamm_set_checked, spamm_set_stream, spamm_stats,
                    spamm_tree_destroy, spamm_tree_norms, spamm_tree_rebuild, spamm_tree_shape,
                    spamm_triples)
@@ -108,6 +109,31 @@ class Context:
             raise ValueError("C has the wrong size")
         spamm_multiply(self.handle, A.handle, B.handle, tau, alpha, beta, C.data_ptr(), ldc)
         return C
+
+    def multiply_batched(self, As, Bs, taus, alphas=None, betas=None, Cs=None):
+        """Independent products C[p] = alpha[p] SpAMM(A[p], B[p]; tau[p]) +
+        beta[p] C[p] in one call (one persistent leaf launch on the
+        tensor-core precisions).  ``As``/``Bs`` are Trees; scalars broadcast."""
+        torch = _torch()
+        count = len(As)
+        def bcast(x, default):
+            if x is None:
+                x = default
+            return list(x) if isinstance(x, (list, tuple)) else [x] * count
+        taus = bcast(taus, 0.0)
+        alphas = bcast(alphas, 1.0)
+        betas = bcast(betas, 0.0)
+        if Cs is None:
+            Cs = [torch.empty((a.n, a.n), dtype=torch.float32, device=a.A.device) for a in As]
+        ldcs = []
+        for a, C in zip(As, Cs):
+            n, ldc = _check_matrix(C)
+            if n != a.n:
+                raise ValueError("C has the wrong size")
+            ldcs.append(ldc)
+        spamm_multiply_batched(self.handle, [a.handle for a in As], [b.handle for b in Bs],
+                               taus, alphas, betas, [C.data_ptr() for C in Cs], ldcs)
+        return Cs
 
     def multiply_host(self, A: np.ndarray, B, tau: float, alpha: float = 1.0,
                       beta: float = 0.0, C=None) -> np.ndarray:

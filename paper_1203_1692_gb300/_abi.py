@@ -73,6 +73,10 @@ SIGNATURES = {
     "spamm_tree_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "spamm_tree_norms": (_i32, [_vp, _vp, _vp, _i64]),
     "spamm_multiply": (_i32, [_vp, _vp, _vp, _dbl, _flt, _flt, _vp, _i64]),
+    "spamm_multiply_batched": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                      ctypes.POINTER(_dbl), ctypes.POINTER(_flt),
+                                      ctypes.POINTER(_flt), ctypes.POINTER(_vp),
+                                      ctypes.POINTER(_i64)]),
     "spamm_multiply_host": (_i32, [_vp, _vp, _vp, _i64, _dbl, _flt, _flt, _vp]),
     "spamm_stats": (_i32, [_vp, ctypes.POINTER(spamm_stats_t)]),
     "spamm_triples": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
@@ -172,6 +176,22 @@ def spamm_multiply(ctx, A_tree, B_tree, tau: float, alpha: float, beta: float, C
                               _vp(C_ptr), ldc)
     check(st, ctx)
     return st
+
+
+def spamm_multiply_batched(ctx, A_trees, B_trees, taus, alphas, betas, C_ptrs, ldcs) -> None:
+    """C[p] = alpha[p] SpAMM(A[p], B[p]; tau[p]) + beta[p] C[p] for every p."""
+    count = len(A_trees)
+    if not (len(B_trees) == len(taus) == len(alphas) == len(betas) == len(C_ptrs) == len(ldcs)
+            == count):
+        raise ValueError("batched arguments differ in length")
+    a = (_vp * max(count, 1))(*A_trees)
+    b = (_vp * max(count, 1))(*B_trees)
+    t = (_dbl * max(count, 1))(*[float(x) for x in taus])
+    al = (_flt * max(count, 1))(*[float(x) for x in alphas])
+    be = (_flt * max(count, 1))(*[float(x) for x in betas])
+    c = (_vp * max(count, 1))(*[_vp(x) for x in C_ptrs])
+    ld = (_i64 * max(count, 1))(*[int(x) for x in ldcs])
+    check(lib().spamm_multiply_batched(ctx, count, a, b, t, al, be, c, ld), ctx)
 
 
 def spamm_multiply_host(ctx, A_ptr: int, B_ptr, n: int, tau: float, alpha: float,

@@ -205,7 +205,8 @@ struct PrecTraits {
     static constexpr uint32_t kAB = PREC == SPAMM_PREC_BF16X3 ? 1u : 2u;
 };
 
-struct TcArgs {
+// One product of a (possibly one-element) batch, as the host prepares it.
+struct TcProd {
     const void* pa[2];
     const void* pb[2];
     int64_t nlp;
@@ -216,11 +217,24 @@ struct TcArgs {
     const uint64_t* pool;
     const uint32_t* off;
     const uint32_t* steps;
-    int tr, tc, tiles, S;
+    int tr, tc, S;
+    int base;  // first work item (tile) of this product in the batch
+};
+
+constexpr int kMaxBatch = 64;
+
+// Passed by value as the kernel parameter (~8 KB), so a launch carries its
+// own table: back-to-back launches cannot overwrite each other's, and a graph
+// capture records it with the launch.
+struct TcBatch {
+    TcProd prods[kMaxBatch];
+    int count;             // products
+    int total;             // work items (tiles) of all products
+    unsigned int* status;  // timeout status word
 };
 
 template <int LEAF, int PREC>
-__global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
+__global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     using T = PrecTraits<PREC>;
     constexpr int TL = 128 / LEAF;      // row leaves = column leaves per half
     constexpr int TLC = 2 * TL;         // column leaves of the tile
@@ -234,14 +248,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     __shared__ uint32_t st_count[ST];                        // filled slots of each stage
     __shared__ volatile int abort_flag;
     __shared__ unsigned long long issued_s, consumed_s;
+    // per product: step-list offsets in its pool, skip flag, end of its work
+    // items.  Everything else is read from the parameter space: pointers that
+    // come from there are known to be global, which keeps the MMA issue loop
+    // as tight as with a single product.
+    __shared__ unsigned long long sp_pk[kMaxBatch], sp_pm[kMaxBatch];
+    __shared__ int sp_skip[kMaxBatch], sp_end[kMaxBatch];
 
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* zero = base;
     unsigned char* stages = base + kZeroBytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned int* status = &p.ctl->status;
-    if (p.ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
+    unsigned int* status = bt.status;
+    for (int i = threadIdx.x; i < bt.count; i += kThreads) {
+        const TcProd& g = bt.prods[i];
+        sp_pk[i] = g.ctl->pk_off;
+        sp_pm[i] = g.ctl->pm_off;
+        // a product whose cull failed is left untouched (its status says why)
+        sp_skip[i] = (g.ctl->status & (ST_OVERFLOW | ST_NONFINITE)) ? 1 : 0;
+        sp_end[i] = g.base + g.tr * g.tc;
+    }
 
     for (int i = threadIdx.x; i < (int)(kZeroBytes / 16); i += kThreads)
         reinterpret_cast<uint4*>(zero)[i] = make_uint4(0, 0, 0, 0);
@@ -271,9 +298,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t* pk = reinterpret_cast<const uint32_t*>(p.pool + p.ctl->pk_off);
-    const unsigned long long* pm =
-        reinterpret_cast<const unsigned long long*>(p.pool + p.ctl->pm_off);
+    // work item k -> product index, advancing monotonically (k only grows)
+    auto product_of = [&](int k, int& pi) {
+        while (pi + 1 < bt.count && k >= sp_end[pi]) ++pi;
+    };
 
     if (warp == 0) {
         // ---------------------------------------------------------- producer
@@ -289,12 +317,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
         int s = 0;
         bool ok = true;
         const size_t piece = (size_t)LEAF * 16 * T::kEsize;
-        for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-            const int u = tile_at(k, p.tr, p.tc);
-            const int64_t srow = (int64_t)(u / p.tc) * TL;
-            const int64_t scol = (int64_t)(u % p.tc) * TLC;
-            const uint32_t ns = p.steps[u];
-            const uint64_t sb = (uint64_t)p.off[u] * p.S;
+        int pi = 0;
+        for (int k = blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+            product_of(k, pi);
+            if (sp_skip[pi]) continue;
+            const TcProd& q = bt.prods[pi];
+            const uint32_t* pk = reinterpret_cast<const uint32_t*>(q.pool + sp_pk[pi]);
+            const unsigned long long* pm =
+                reinterpret_cast<const unsigned long long*>(q.pool + sp_pm[pi]);
+            const int u = tile_at(k - q.base, q.tr, q.tc);
+            const int64_t srow = (int64_t)(u / q.tc) * TL;
+            const int64_t scol = (int64_t)(u % q.tc) * TLC;
+            const uint32_t ns = q.steps[u];
+            const uint64_t sb = (uint64_t)q.off[u] * q.S;
             uint32_t ck = lane < (int)ns ? pk[sb + lane] : 0u;
             unsigned long long cm0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
             unsigned long long cm1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
@@ -320,17 +355,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                                 asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
                                              "r"((uint32_t)T::kIter)
                                              : "memory");
-                                const int64_t row = (K * CHUNKS + kc) * p.nlp;
+                                const int64_t row = (K * CHUNKS + kc) * q.nlp;
                                 unsigned char* slot = stages + (size_t)s * T::kStage +
                                                       (size_t)fill * T::kIter;
 #pragma unroll
                                 for (int part = 0; part < T::kParts; ++part) {
                                     bulk_g2s(smem_u32(slot + part * T::kSlice),
-                                             static_cast<const unsigned char*>(p.pa[part]) +
+                                             static_cast<const unsigned char*>(q.pa[part]) +
                                                  (size_t)(row + srow) * piece,
                                              T::kSlice, full);
                                     bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
-                                             static_cast<const unsigned char*>(p.pb[part]) +
+                                             static_cast<const unsigned char*>(q.pb[part]) +
                                                  (size_t)(row + scol) * piece,
                                              2 * T::kSlice, full);
                                 }
@@ -372,11 +407,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
             const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
             const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
             uint32_t dacc = tmem;
-            uint32_t ns_next = blockIdx.x < p.tiles ? p.steps[tile_at(blockIdx.x, p.tr, p.tc)] : 0u;
-            for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-                const uint32_t ns = ns_next;
-                if (k + (int)gridDim.x < p.tiles)
-                    ns_next = p.steps[tile_at(k + gridDim.x, p.tr, p.tc)];
+            int pi = 0;
+            for (int k = blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+                product_of(k, pi);
+                if (sp_skip[pi]) continue;
+                const TcProd& q = bt.prods[pi];
+                const uint32_t ns = q.steps[tile_at(k - q.base, q.tr, q.tc)];
                 const uint32_t iters = ns * CHUNKS;
                 if (iters == 0) {
                     const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
@@ -510,13 +546,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
         __syncwarp();
     } else {
         // ---------------------------------------------------------- epilogue
-        const int q = warp & 3;                  // TMEM lane quarter this warp may access
+        const int qq = warp & 3;                 // TMEM lane quarter this warp may access
         const int hcol = (warp - 2) >> 2;        // which 128 columns of the 256
         uint32_t ccount = 0;
         bool ok = true;
-        for (int k = blockIdx.x; k < p.tiles && ok; k += gridDim.x) {
-            const int u = tile_at(k, p.tr, p.tc);
-            const uint32_t nch = chunks_of(p.steps[u] * CHUNKS);
+        int pi = 0;
+        for (int k = blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+            product_of(k, pi);
+            if (sp_skip[pi]) continue;
+            const TcProd& q = bt.prods[pi];
+            const int u = tile_at(k - q.base, q.tr, q.tc);
+            const uint32_t nch = chunks_of(q.steps[u] * CHUNKS);
             float master[128];
 #pragma unroll
             for (int v = 0; v < 128; ++v) master[v] = 0.f;
@@ -529,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                 }
                 tc_fence_after();
                 const uint32_t taddr =
-                    tmem + ((uint32_t)(q * 32) << 16) + ab * 256 + (uint32_t)(hcol * 128);
+                    tmem + ((uint32_t)(qq * 32) << 16) + ab * 256 + (uint32_t)(hcol * 128);
 #pragma unroll
                 for (int cc = 0; cc < 128; cc += 32) {
                     uint32_t r[32];
@@ -542,35 +582,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
                 if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
             }
             if (!ok) break;
-            const int64_t row = (int64_t)(u / p.tc) * 128 + q * 32 + lane;
-            const int64_t col0 = (int64_t)(u % p.tc) * 256 + hcol * 128;
-            if (row < p.n && col0 < p.n) {
-                float* crow = p.C + row * p.ldc + col0;
-                const bool vec = ((p.ldc & 3) == 0) &&
-                                 ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0) &&
-                                 (col0 + 128 <= p.n);
+            float* const Cp = q.C;
+            const int64_t ldc = q.ldc, n = q.n;
+            const float alpha = q.alpha, beta = q.beta;
+            const int64_t row = (int64_t)(u / q.tc) * 128 + qq * 32 + lane;
+            const int64_t col0 = (int64_t)(u % q.tc) * 256 + hcol * 128;
+            if (row < n && col0 < n) {
+                float* crow = Cp + row * ldc + col0;
+                const bool vec = ((ldc & 3) == 0) &&
+                                 ((reinterpret_cast<uintptr_t>(Cp) & 15) == 0) &&
+                                 (col0 + 128 <= n);
                 if (vec) {
 #pragma unroll
                     for (int v = 0; v < 32; ++v) {
-                        float4 o = make_float4(p.alpha * master[4 * v], p.alpha * master[4 * v + 1],
-                                               p.alpha * master[4 * v + 2],
-                                               p.alpha * master[4 * v + 3]);
+                        float4 o = make_float4(alpha * master[4 * v], alpha * master[4 * v + 1],
+                                               alpha * master[4 * v + 2],
+                                               alpha * master[4 * v + 3]);
                         float4* dst = reinterpret_cast<float4*>(crow) + v;
-                        if (p.beta != 0.f) {
+                        if (beta != 0.f) {
                             const float4 old = *dst;
-                            o.x = fmaf(p.beta, old.x, o.x);
-                            o.y = fmaf(p.beta, old.y, o.y);
-                            o.z = fmaf(p.beta, old.z, o.z);
-                            o.w = fmaf(p.beta, old.w, o.w);
+                            o.x = fmaf(beta, old.x, o.x);
+                            o.y = fmaf(beta, old.y, o.y);
+                            o.z = fmaf(beta, old.z, o.z);
+                            o.w = fmaf(beta, old.w, o.w);
                         }
                         *dst = o;
                     }
                 } else {
 #pragma unroll
                     for (int v = 0; v < 128; ++v) {
-                        if (col0 + v < p.n) {
-                            float o = p.alpha * master[v];
-                            if (p.beta != 0.f) o = fmaf(p.beta, crow[v], o);
+                        if (col0 + v < n) {
+                            float o = alpha * master[v];
+                            if (beta != 0.f) o = fmaf(beta, crow[v], o);
                             crow[v] = o;
                         }
                     }
@@ -601,52 +644,76 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcArgs p) {
 }
 
 template <int LEAF, int PREC>
-cudaError_t launch_t(spamm_ctx* ctx, const TcArgs& a) {
+cudaError_t launch_t(spamm_ctx* ctx, const TcBatch& bt) {
     using T = PrecTraits<PREC>;
     const size_t smem = 1024 + kZeroBytes + (size_t)T::kStages * T::kStage;
     cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, PREC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = a.tiles < ctx->sm_count ? a.tiles : ctx->sm_count;
-    k_leaf_tc<LEAF, PREC><<<grid, kThreads, smem, ctx->stream>>>(a);
+    const int grid = bt.total < ctx->sm_count ? bt.total : ctx->sm_count;
+    if (grid <= 0) return cudaSuccess;
+    k_leaf_tc<LEAF, PREC><<<grid, kThreads, smem, ctx->stream>>>(bt);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+// All jobs share the context's leaf size and precision.  At most kMaxBatch
+// products go into one launch.
+cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) {
+    for (int j0 = 0; j0 < count; j0 += kMaxBatch) {
+        TcBatch bt;
+        memset(&bt, 0, sizeof(bt));
+        bt.count = count - j0 < kMaxBatch ? count - j0 : kMaxBatch;
+        bt.status = &ctx->ctl->status;
+        int base = 0;
+        for (int i = 0; i < bt.count; ++i) {
+            const LeafJob& jb = jobs[j0 + i];
+            TcProd& q = bt.prods[i];
+            for (int h = 0; h < 2; ++h) {
+                q.pa[h] = jb.A->packA[h] ? jb.A->packA[h] : jb.A->packA[0];
+                q.pb[h] = jb.B->packB[h] ? jb.B->packB[h] : jb.B->packB[0];
+            }
+            q.nlp = jb.A->nlp;
+            q.C = jb.C;
+            q.ldc = jb.ldc;
+            q.n = jb.A->n;
+            q.alpha = jb.alpha;
+            q.beta = jb.beta;
+            q.ctl = jb.sub->ctl;
+            q.pool = jb.sub->pool;
+            q.off = jb.sub->tile_off;
+            q.steps = jb.sub->tile_steps;
+            q.tr = tile_rows(jb.A);
+            q.tc = tile_cols(jb.A);
+            q.S = jb.sub->last_S;
+            q.base = base;
+            base += q.tr * q.tc;
+        }
+        bt.total = base;
+        const int p = ctx->cfg.precision;
+        const int b = ctx->cfg.leaf;
+        cudaError_t e;
+        if (b == 16) {
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt);
+            else e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt);
+        } else if (b == 32) {
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt);
+            else e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt);
+        } else {
+            e = cudaErrorNotSupported;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, float alpha,
                            float beta, float* C, int64_t ldc) {
-    TcArgs a;
-    for (int i = 0; i < 2; ++i) {
-        a.pa[i] = A->packA[i] ? A->packA[i] : A->packA[0];
-        a.pb[i] = B->packB[i] ? B->packB[i] : B->packB[0];
-    }
-    a.nlp = A->nlp;
-    a.C = C;
-    a.ldc = ldc;
-    a.n = A->n;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.ctl = ctx->ctl;
-    a.pool = ctx->pool;
-    a.off = ctx->tile_off;
-    a.steps = ctx->tile_steps;
-    a.tr = tile_rows(A);
-    a.tc = tile_cols(A);
-    a.tiles = a.tr * a.tc;
-    a.S = ctx->last_S;
-    const int p = A->precision;
-    if (A->b == 16) {
-        if (p == SPAMM_PREC_TF32X3) return launch_t<16, SPAMM_PREC_TF32X3>(ctx, a);
-        if (p == SPAMM_PREC_TF32) return launch_t<16, SPAMM_PREC_TF32>(ctx, a);
-        return launch_t<16, SPAMM_PREC_BF16X3>(ctx, a);
-    }
-    if (A->b == 32) {
-        if (p == SPAMM_PREC_TF32X3) return launch_t<32, SPAMM_PREC_TF32X3>(ctx, a);
-        if (p == SPAMM_PREC_TF32) return launch_t<32, SPAMM_PREC_TF32>(ctx, a);
-        return launch_t<32, SPAMM_PREC_BF16X3>(ctx, a);
-    }
-    return cudaErrorNotSupported;
+    LeafJob jb{A, B, ctx, alpha, beta, C, ldc};
+    return launch_leaf_tc_jobs(ctx, &jb, 1);
 }
 
 }  // namespace spamm

@@ -172,6 +172,8 @@ spamm_status spamm_destroy(spamm_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->hostTreeA) spamm_tree_destroy(ctx->hostTreeA);
     if (ctx->hostTreeB) spamm_tree_destroy(ctx->hostTreeB);
+    for (spamm_ctx* sub : ctx->subs) spamm_destroy(sub);
+    ctx->subs.clear();
     cudaFree(ctx->pool);
     cudaFree(ctx->ctl);
     if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
@@ -354,6 +356,7 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
     const int64_t tiles = (int64_t)tile_rows(A) * tile_cols(A);
     spamm_status st = ensure_tiles(ctx, tiles);
     if (st != SPAMM_OK) return st;
+    ctx->last_batch = 0;
     ctx->last_d = A->d;
     ctx->last_b = A->b;
     ctx->last_n = A->n;
@@ -383,10 +386,13 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
     }
 }
 
+static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out);
+
 spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "stats");
+    if (ctx->last_batch > 0) return batch_stats(ctx, out);
     memset(out, 0, sizeof(*out));
     const DevCtl& c = *ctx->ctl_host;
     const int d = ctx->last_d;
@@ -423,6 +429,8 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     if (!ctx || !count || cap < 0 || (cap > 0 && !host_out)) return SPAMM_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "triples");
+    if (ctx->last_batch > 0)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "the last multiply was batched");
     const DevCtl& c = *ctx->ctl_host;
     const int d = ctx->last_d;
     const int64_t m = (int64_t)c.tier_count[d];
@@ -467,6 +475,152 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
         }
     }
     return SPAMM_OK;
+}
+
+static spamm_status status_of(spamm_ctx* ctx, const DevCtl& c) { return status_from_ctl(ctx, c); }
+
+static void note_shape(spamm_ctx* c, const spamm_tree* A, double tau) {
+    c->last_batch = 0;
+    c->last_d = A->d;
+    c->last_b = A->b;
+    c->last_n = A->n;
+    c->last_prec = A->precision;
+    c->last_tau = tau;
+    c->last_tiles = (int64_t)tile_rows(A) * tile_cols(A);
+    c->last_tr = tile_rows(A);
+    c->last_tc = tile_cols(A);
+    c->last_tt = tile_tier(A);
+    c->last_S = 1 << (A->d - c->last_tt);
+    c->last_status = SPAMM_OK;
+}
+
+spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_tree* const* A,
+                                    const spamm_tree* const* B, const double* tau,
+                                    const float* alpha, const float* beta, float* const* C,
+                                    const int64_t* ldc) {
+    if (!ctx || count < 0 || (count > 0 && (!A || !B || !tau || !alpha || !beta || !C || !ldc)))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL argument");
+    if (count == 0) return SPAMM_OK;
+    for (int p = 0; p < count; ++p) {
+        if (!A[p] || !B[p] || !C[p]) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL argument");
+        if (!(tau[p] >= 0.0) || !std::isfinite(tau[p]))
+            return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tau must be finite and >= 0");
+        if (A[p]->n != B[p]->n || A[p]->b != B[p]->b || A[p]->precision != B[p]->precision ||
+            A[p]->precision != ctx->cfg.precision || A[p]->b != ctx->cfg.leaf)
+            return set_err(ctx, SPAMM_ERR_INVALID_ARG, "trees differ from the configuration");
+        if (ldc[p] < A[p]->n) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "ldc below n");
+    }
+    // sub-contexts
+    while ((int)ctx->subs.size() < count) {
+        spamm_config c = ctx->cfg;
+        c.checked = 0;
+        if (!c.pool_bytes) c.pool_bytes = (int64_t)64 << 20;
+        spamm_ctx* sub = nullptr;
+        const spamm_status st = spamm_create(&sub, ctx->stream, &c);
+        if (st != SPAMM_OK) return set_err(ctx, st, "sub-context creation");
+        ctx->subs.push_back(sub);
+    }
+    for (int p = 0; p < count; ++p) {
+        spamm_ctx* sub = ctx->subs[p];
+        sub->stream = ctx->stream;
+        const spamm_status st = ensure_tiles(sub, (int64_t)tile_rows(A[p]) * tile_cols(A[p]));
+        if (st != SPAMM_OK) return st;
+        note_shape(sub, A[p], tau[p]);
+    }
+    ctx->last_batch = count;
+    ctx->last_status = SPAMM_OK;
+    std::vector<LeafJob> jobs((size_t)count);
+    for (int attempt = 0;; ++attempt) {
+        cudaStream_t s = ctx->stream;
+        cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
+        for (int p = 0; p < count && e == cudaSuccess; ++p) {
+            spamm_ctx* sub = ctx->subs[p];
+            e = cudaMemsetAsync(sub->ctl, 0, sizeof(DevCtl), s);
+            if (e == cudaSuccess) e = launch_cull(sub, A[p], B[p], tau[p], sub->last_tt);
+            if (e == cudaSuccess) e = launch_group(sub, A[p], B[p], tau[p], sub->last_tt);
+            jobs[p] = LeafJob{A[p], B[p], sub, alpha[p], beta[p], C[p], ldc[p]};
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
+        if (e == cudaSuccess) {
+            if (ctx->cfg.precision == SPAMM_PREC_FP32) {
+                for (int p = 0; p < count && e == cudaSuccess; ++p)
+                    e = launch_leaf_simt(ctx->subs[p], A[p], B[p], alpha[p], beta[p], C[p], ldc[p]);
+            } else {
+                e = launch_leaf_tc_jobs(ctx, jobs.data(), count);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2], s);
+        for (int p = 0; p < count && e == cudaSuccess; ++p)
+            e = cudaMemcpyAsync(ctx->subs[p]->ctl_host, ctx->subs[p]->ctl, sizeof(DevCtl),
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s);
+        ctx->timed = (e == cudaSuccess);
+        if (e != cudaSuccess)
+            return (spamm_status)(ctx->last_status = cuda_err(ctx, e, "batched multiply launch"));
+        if (!ctx->cfg.checked) return SPAMM_OK;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return (spamm_status)(ctx->last_status = cuda_err(ctx, e, "batched multiply"));
+        bool retry = false;
+        for (int p = 0; p < count; ++p) {
+            spamm_ctx* sub = ctx->subs[p];
+            const DevCtl& c = *sub->ctl_host;
+            if (c.status & (ST_NONFINITE | ST_TIMEOUT))
+                return (spamm_status)(ctx->last_status = status_of(ctx, c));
+            if (c.status & ST_OVERFLOW) {
+                const int64_t need = std::max<int64_t>(words_needed(c, sub->last_tt, sub->last_S),
+                                                       2 * sub->pool_words);
+                const spamm_status st = alloc_pool(sub, need * 8 + need * 2);
+                if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
+                retry = true;
+            }
+        }
+        const spamm_status st = status_of(ctx, *ctx->ctl_host);
+        if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
+        if (retry && attempt < 8) continue;
+        if (retry) return (spamm_status)(ctx->last_status = set_err(ctx, SPAMM_ERR_CAPACITY, "pool"));
+        return SPAMM_OK;
+    }
+}
+
+static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
+    memset(out, 0, sizeof(*out));
+    spamm_status worst = status_of(ctx, *ctx->ctl_host);
+    for (int p = 0; p < ctx->last_batch && p < (int)ctx->subs.size(); ++p) {
+        spamm_ctx* sub = ctx->subs[p];
+        const DevCtl& c = *sub->ctl_host;
+        const int d = sub->last_d;
+        for (int t = 0; t <= d && t < SPAMM_MAX_TIERS; ++t) {
+            out->tier_candidates[t] += (int64_t)c.tier_cand[t];
+            out->tier_kept[t] += (int64_t)c.tier_count[t];
+        }
+        out->depth = std::max<int32_t>(out->depth, d);
+        out->n = std::max<int64_t>(out->n, sub->last_n);
+        const int64_t m = (int64_t)c.tier_count[d];
+        out->leaf_triples += m;
+        out->tie_band += (int64_t)c.tie_band;
+        out->active_steps += (int64_t)c.active_steps;
+        out->tiles += sub->last_tiles;
+        const double b = sub->last_b;
+        out->kept_flops += 2.0 * b * b * b * (double)m;
+        out->dense_flops += 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
+        out->pool_bytes += sub->pool_words * 8;
+        out->pool_needed_bytes += words_needed(c, sub->last_tt, sub->last_S) * 8;
+        const spamm_status st = status_of(ctx, c);
+        if (worst == SPAMM_OK) worst = st;
+    }
+    out->leaf = ctx->cfg.leaf;
+    out->precision = ctx->cfg.precision;
+    if (ctx->timed) {
+        cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&out->ms_numeric, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&out->ms_total, ctx->ev[0], ctx->ev[2]);
+    }
+    if (ctx->last_status != SPAMM_OK && worst == SPAMM_OK) worst = (spamm_status)ctx->last_status;
+    out->status = worst;
+    return worst;
 }
 
 spamm_status spamm_multiply_host(spamm_ctx* ctx, const float* A, const float* B, int64_t n,

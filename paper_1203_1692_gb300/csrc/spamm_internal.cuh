@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/spamm.h"
 
@@ -152,6 +153,10 @@ struct spamm_ctx {
     int64_t stage_elems;
     spamm_tree* hostTreeA;
     spamm_tree* hostTreeB;
+    // batched multiplies: one sub-context (pool, control block, tile arrays)
+    // per product, created on demand and reused
+    std::vector<spamm_ctx*> subs;
+    int last_batch;  // products in the last multiply (0: a plain multiply)
     std::string err;
 };
 
@@ -183,5 +188,16 @@ cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tr
 // leaf_tc.cu
 cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                            float alpha, float beta, float* C, int64_t ldc);
+// One product of a batched leaf launch: its trees, the context that ran its
+// cull and grouping (pool, control block, tile arrays), and its C.
+struct LeafJob {
+    const spamm_tree* A;
+    const spamm_tree* B;
+    spamm_ctx* sub;
+    float alpha, beta;
+    float* C;
+    int64_t ldc;
+};
+cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count);
 
 }  // namespace spamm
