@@ -57,8 +57,8 @@ typedef enum {
 } spamm_precision;
 
 typedef struct {
-    int32_t leaf;          /* leaf block size b: 16, 32, 64 or 128 (tensor-core
-                              precisions: 16 or 32) */
+    int32_t leaf;          /* leaf block size b: 16, 32, 64 or 128 (every
+                              precision) */
     int32_t precision;     /* spamm_precision */
     double tie_rel;        /* relative half-width of the band around tau whose
                               triples are counted in spamm_stats (default 1e-6) */

@@ -461,7 +461,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         // and differs from column y-1's.  Uniform halves (the
                         // common case on dense blocks) give one run directly.
                         constexpr unsigned long long kRep =
-                            TL == 8 ? 0x0101010101010101ull : 0x0000000001010101ull;
+                            TL == 8   ? 0x0101010101010101ull
+                            : TL == 4 ? 0x0000000001010101ull
+                            : TL == 2 ? 0x0000000000000101ull
+                                      : 0x0000000000000001ull;
                         const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
                         const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
                         const bool u0 = mask0 == (unsigned long long)x0 * kRep;
@@ -499,16 +502,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                             const int len = yend - y;
                             const uint32_t xm = y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
                                                        : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
+                            // disable-output-lane bits: row r of the tile is
+                            // lane r, and a dropped row leaf x masks its b rows
                             uint32_t dis[4];
 #pragma unroll
                             for (int w = 0; w < 4; ++w) {
                                 uint32_t v = 0;
+                                if (LEAF <= 32) {
 #pragma unroll
-                                for (int q = 0; q < 32 / LEAF; ++q) {
-                                    const int x = w * (32 / LEAF) + q;
-                                    if (!((xm >> x) & 1u))
-                                        v |= (LEAF == 32 ? 0xFFFFFFFFu
-                                                         : (0xFFFFu << (16 * q)));
+                                    for (int q = 0; q < 32 / LEAF; ++q) {
+                                        const int x = w * (32 / LEAF) + q;
+                                        if (!((xm >> x) & 1u))
+                                            v |= (LEAF == 32 ? 0xFFFFFFFFu
+                                                             : (0xFFFFu << (16 * q)));
+                                    }
+                                } else {
+                                    const int x = (w * 32) / LEAF;
+                                    if (!((xm >> x) & 1u)) v = 0xFFFFFFFFu;
                                 }
                                 dis[w] = v;
                             }
@@ -702,6 +712,14 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
             if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt);
             else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt);
             else e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt);
+        } else if (b == 64) {
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt);
+            else e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt);
+        } else if (b == 128) {
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt);
+            else e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt);
         } else {
             e = cudaErrorNotSupported;
         }

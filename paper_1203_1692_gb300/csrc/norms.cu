@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     constexpr int UPP = PIECE / 16;                      // units per piece
     constexpr int CPC = 16 / EPU;                        // core matrices per 16-wide K chunk
     constexpr int LDS = 128 + 4;                         // padded staging row
-    __shared__ __align__(16) float raw[LEAF][LDS];
+    extern __shared__ __align__(16) float raw_dyn[];     // LEAF x LDS staged strip
+    float (*raw)[LDS] = reinterpret_cast<float (*)[LDS]>(raw_dyn);
     __shared__ double part[4][TL];
     // leaf rows vary fastest across blocks, so the blocks running at once
     // write neighbouring A-role pieces
@@ -295,18 +296,26 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
     } else {
         const int tl = 128 / t->b;
         dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));
-#define SPAMM_LP(PKV, LV)                                                                   \
-    k_leaf_pack<PKV, LV><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp, leaf, \
-                                              pa0, pa1, pb0, pb1)
-        if (t->b == 16) {
-            if (pk == 1) SPAMM_LP(1, 16);
-            else if (pk == 2) SPAMM_LP(2, 16);
-            else SPAMM_LP(3, 16);
-        } else {
-            if (pk == 1) SPAMM_LP(1, 32);
-            else if (pk == 2) SPAMM_LP(2, 32);
-            else SPAMM_LP(3, 32);
-        }
+        const size_t smem = (size_t)t->b * (128 + 4) * sizeof(float);
+#define SPAMM_LP(PKV, LV)                                                                      \
+    do {                                                                                       \
+        if (smem > 48 * 1024)                                                                  \
+            cudaFuncSetAttribute(k_leaf_pack<PKV, LV>,                                         \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+        k_leaf_pack<PKV, LV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp, \
+                                                     leaf, pa0, pa1, pb0, pb1);                \
+    } while (0)
+#define SPAMM_LP_B(LV)                \
+    do {                              \
+        if (pk == 1) SPAMM_LP(1, LV); \
+        else if (pk == 2) SPAMM_LP(2, LV); \
+        else SPAMM_LP(3, LV);         \
+    } while (0)
+        if (t->b == 16) SPAMM_LP_B(16);
+        else if (t->b == 32) SPAMM_LP_B(32);
+        else if (t->b == 64) SPAMM_LP_B(64);
+        else SPAMM_LP_B(128);
+#undef SPAMM_LP_B
 #undef SPAMM_LP
     }
     e = cudaGetLastError();

@@ -134,8 +134,6 @@ spamm_status spamm_create(spamm_ctx** out, void* stream, const spamm_config* cfg
     if (cfg) c = *cfg; else spamm_config_default(&c);
     if (!valid_leaf(c.leaf)) return SPAMM_ERR_INVALID_ARG;
     if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_BF16X3) return SPAMM_ERR_INVALID_ARG;
-    if (precision_uses_tc(c.precision) && !(c.leaf == 16 || c.leaf == 32))
-        return SPAMM_ERR_UNSUPPORTED;
     if (!(c.tie_rel >= 0.0 && c.tie_rel < 0.5) || c.pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
     for (int i = 0; i < 7; ++i)
         if (c.reserved[i]) return SPAMM_ERR_INVALID_ARG;

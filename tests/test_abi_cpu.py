@@ -65,9 +65,11 @@ def test_create_rejects_bad_config_before_touching_the_gpu(libpath):
     c.precision = 9
     assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_INVALID_ARG
     c = _abi.spamm_config_default()
-    c.precision = _abi.SPAMM_PREC_TF32X3
-    c.leaf = 128
-    assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_UNSUPPORTED
+    c.tie_rel = 0.7
+    assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_INVALID_ARG
+    c = _abi.spamm_config_default()
+    c.pool_bytes = -1
+    assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == _abi.SPAMM_ERR_INVALID_ARG
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):

@@ -69,6 +69,11 @@ CASES = [
     (333, 16, "dense", 0.0),
     (333, 32, "dense", 0.0),
     (600, 32, "exp", 1e-5),
+    (640, 64, "exp", 1e-5),
+    (530, 64, "alg", 1e-6),        # ragged: 530 = 8.3 leaves of 64
+    (300, 64, "dense", 0.0),
+    (768, 128, "exp", 1e-6),
+    (450, 128, "alg", 1e-5),       # ragged, one pair tile of 128-leaves
 ]
 
 
