@@ -40,6 +40,10 @@ WORKLOADS = {
                  "a_ij = g_ij exp(-0.5 r_ij), Hilbert order, b=16, A=B",
     "exp1024": "exponential decay a_ij = u_ij 0.9^|i-j| (n=1024), b=16, A=B",
     "alg16384": "algebraic decay a_ij = s_ij/(|i-j|^2+1) (n=16384), b=16, A=B",
+    "batched64": "64 independent products C_p = A_p A_p, n log-uniform in [512, 8192], "
+                 "a_ij = u_ij lambda^|i-j| with lambda uniform in [0.8, 0.95], tau=1e-7, "
+                 "one persistent leaf launch in a captured CUDA graph, leaf size and "
+                 "product order autotuned over b in {16, 32, 64, 128}",
 }
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense tensor-core ratio
 FP32_LANES_PER_SM = 128
@@ -270,6 +274,240 @@ def run_quick(args, P, A, n, b, stream):
                       "leaf_triples": st["leaf_triples"]}), flush=True)
 
 
+def run_batched(args, P, dev, rank, world, dist):
+    """The batch of 64 uneven products: autotuned leaf size and order, the
+    whole step (norm trees, culls, one leaf launch) replayed from a CUDA
+    graph; against 64 cuBLAS SGEMMs (also a graph) and against plain FP32
+    SpAMM run one product per call."""
+    import torch
+    from paper_1203_1692_gb300 import autotune
+    from spamm_inputs import device as D
+    torch.backends.cuda.matmul.allow_tf32 = False
+    tau = 1e-7 if args.tau == "auto" else float(args.tau)
+    specs = gen.batched_products(64, 512, 8192, 0.8, 0.95, seed=0)
+    mats = [D.exp_decay(n, lam, seed=s, device=dev) for n, lam, s in specs]
+    ns = [n for n, _, _ in specs]
+    count = len(mats)
+    taus = [tau] * count
+    torch.cuda.synchronize()
+
+    # --- autotune (leaf size x order), then the chosen configuration ------
+    leaves = autotune.LEAVES
+    choice = autotune.tune_batch([(A, A) for A in mats], taus, args.precision, leaves=leaves)
+    b = choice.leaf
+    perm = choice.permutation(ns)
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+    trees = [ctx.build_norms(mats[p]) for p in perm]
+    Cs = [torch.empty_like(mats[p]) for p in perm]
+    ctx.multiply_batched(trees, trees, taus, None, None, Cs)
+    st = ctx.stats()
+    kept_flops = st["kept_flops"]
+
+    # --- accuracy on sampled rows against FP64 (cuBLAS DGEMM rows) --------
+    rows = 32
+    err_sp, err_sg = 0.0, 0.0
+    gen_rows = torch.Generator(device="cpu").manual_seed(3)
+    for q, p in enumerate(perm):
+        A = mats[p]
+        r = torch.randint(0, ns[p], (rows,), generator=gen_rows).to(dev)
+        ref = A[r].double() @ A.double()
+        scale = float(ref.abs().max())
+        err_sp = max(err_sp, float((Cs[q][r].double() - ref).abs().max()) / scale)
+        err_sg = max(err_sg, float(((A[r] @ A).double() - ref).abs().max()) / scale)
+        del ref
+    # oracle parity on the four smallest products (sampled C blocks)
+    parity = []
+    for q in sorted(range(count), key=lambda q: ns[perm[q]])[:4]:
+        A_h = mats[perm[q]].cpu().numpy()
+        parity.append(sampled_parity(A_h, Cs[q], b, tau, count=24))
+    par_worst = max(x["rel_max_err_vs_oracle"] for x in parity)
+
+    # --- the step in a CUDA graph -----------------------------------------
+    ctx.set_checked(False)
+    s = torch.cuda.Stream(device=dev)
+    P._abi.spamm_set_stream(ctx.handle, s.cuda_stream)
+
+    def step():
+        for t, p in zip(trees, perm):
+            t.rebuild(mats[p])
+        ctx.multiply_batched(trees, trees, taus, None, None, Cs)
+
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    per = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for k in range(args.steps):
+            per[k][0].record(s)
+            g.replay()
+            per[k][1].record(s)
+        e1.record(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    lat = sorted(a.elapsed_time(c) for a, c in per)
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = kept_flops * world / (ms_step * 1e-3) / 1e12
+    # the leaf launch alone (its own events inside the library), not in a graph
+    with torch.cuda.stream(s):
+        leaf_ms = []
+        for _ in range(5):
+            ctx.multiply_batched(trees, trees, taus, None, None, Cs)
+            leaf_ms.append(ctx.stats()["ms_numeric"])
+    leaf_ms = statistics.median(leaf_ms)
+
+    # --- 64 cuBLAS SGEMMs in a graph --------------------------------------
+    outs = [torch.empty_like(A) for A in mats]
+    gs = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        for A, O in zip(mats, outs):
+            torch.mm(A, A, out=O)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(gs, stream=s):
+        for A, O in zip(mats, outs):
+            torch.mm(A, A, out=O)
+    for _ in range(3):
+        gs.replay()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        a0.record(s)
+        for _ in range(3):
+            gs.replay()
+        a1.record(s)
+    torch.cuda.synchronize()
+    t_sgemm = a0.elapsed_time(a1) / 3
+    del outs, gs
+
+    # --- plain FP32 SpAMM, one product per call (b = 16) ------------------
+    pctx = P.Context(leaf=16, precision="fp32", checked=True)
+    ptrees = [pctx.build_norms(A) for A in mats]
+    pouts = [torch.empty_like(A) for A in mats]
+    for t, O in zip(ptrees, pouts):
+        pctx.multiply(t, t, tau, C=O)            # checked: sizes the pool
+    pctx.set_checked(False)
+    P._abi.spamm_set_stream(pctx.handle, s.cuda_stream)
+    with torch.cuda.stream(s):
+        for t, A, O in zip(ptrees, mats, pouts):
+            t.rebuild(A)
+            pctx.multiply(t, t, tau, C=O)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(s)
+        for t, A, O in zip(ptrees, mats, pouts):
+            t.rebuild(A)
+            pctx.multiply(t, t, tau, C=O)
+        b1.record(s)
+    torch.cuda.synchronize()
+    t_plain = b0.elapsed_time(b1)
+    for t in ptrees:
+        t.close()
+    pctx.close()
+    del pouts
+    torch.cuda.empty_cache()
+
+    # --- end to end: pinned host inputs in, results out, every step --------
+    e2e = None
+    if not args.no_e2e:
+        hA = [mats[p].cpu().pin_memory() for p in perm]
+        hC = [torch.empty(A.shape, dtype=torch.float32).pin_memory() for A in hA]
+        dA = [mats[p] for p in perm]
+        times = []
+        for it in range(max(3, args.steps // 2) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(s):
+                for h, d in zip(hA, dA):
+                    d.copy_(h, non_blocking=True)
+                g.replay()
+                for h, c in zip(hC, Cs):
+                    h.copy_(c, non_blocking=True)
+            s.synchronize()
+            if it:
+                times.append(time.perf_counter() - t0)
+        byt = sum(4 * x.numel() for x in hA)
+        e2e = {"value": kept_flops * world / statistics.mean(times) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": byt, "d2h_bytes_per_step": byt,
+               "ms_per_step": 1e3 * statistics.mean(times)}
+        del hA, hC
+
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    if args.precision == "fp32":
+        mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "k_leaf_simt", "unit": "TFLOP/s",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz"}
+    else:
+        key = "bf16_tflops_sustained"
+        tf = args.precision.startswith("tf32")
+        peak = peaks[key] * (TF32_OVER_BF16 if tf else 1.0)
+        roof = {"bound": "tensor", "kernel": "k_leaf_tc", "unit": "TFLOP/s",
+                "peak_source": f"{key} of {peak_src} x "
+                               f"{'1.1/2.25 (tf32/bf16 nominal)' if tf else '1'}"}
+    achieved = kept_flops / (leaf_ms * 1e-3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision)),
+                 "note": f"of {peak_src}; algorithmic flops = 2 b^3 x kept leaf triples of "
+                         "the whole batch, one leaf launch"})
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        q = sorted(range(count), key=lambda q: ns[perm[q]])[count // 2]
+        v, threads, desc, _ = cpu_sample(mats[perm[q]].cpu().numpy(), b, tau, args.cpu_seconds)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"product of n={ns[perm[q]]} (median n of the batch): " + desc}
+    # per product: norm leaves, upper tiers, cull, grouping; one leaf launch
+    launches = sum(kernels_per_step(t.depth, b) - 1 for t in trees) + -(-count // 64)
+    line = {
+        "metric": "SpAMM leaf TFLOP/s (kept 2b^3 flops / step time), batch of 64 products",
+        "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched64"], "products": count,
+                   "n_min": min(ns), "n_max": max(ns), "sum_n3": float(sum(n ** 3 for n in ns)),
+                   "tau": tau, "precision": args.precision, "leaf": b,
+                   "order": choice.order, "autotune_ms": {f"b{k[0]}/{k[1]}": v
+                                                         for k, v in choice.trials.items()},
+                   "graph": "norm trees + culls + one leaf launch captured and replayed",
+                   "l2": "inputs larger than L2 (sum of 4n^2 over the batch)",
+                   "parallelism": f"replicas x{world}"},
+        "speedup_vs_sgemm": t_sgemm / ms_step, "sgemm_ms": t_sgemm,
+        "speedup_vs_plain_fp32_spamm": t_plain / ms_step, "plain_fp32_spamm_ms": t_plain,
+        "max_rel_err_sampled_rows": err_sp, "sgemm_max_rel_err_sampled_rows": err_sg,
+        "kept_leaf_triples": st["leaf_triples"],
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "ms_numeric": leaf_ms, "parity_sampled_worst": par_worst, "parity_sampled": parity,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def kernels_per_step(d, leaf):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
@@ -294,6 +532,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    if args.workload == "batched64":
+        run_batched(args, P, dev, rank, world, dist)
+        return
     A_h = make_matrix(args.workload, args.sites)
     n = A_h.shape[0]
     b = args.leaf

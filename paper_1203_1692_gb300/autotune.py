@@ -1,0 +1,105 @@
+"""Autotuner for the leaf size and the schedule of batched SpAMM products.
+
+The leaf size b sets how finely the cull of Sec. III works: small leaves
+drop more of the product, large leaves give the tensor-core kernel longer
+runs of work per step.  Which wins depends on n, on how fast the matrices
+decay and on tau, so it is measured rather than modelled.  Every candidate
+(leaf size, product order) runs the caller's own batch through
+spamm_multiply_batched, event-timed on the context's stream after a
+warm-up, and the fastest is kept.
+
+The schedule candidate is the order of the products in the launch.  The
+persistent leaf kernel deals the concatenated list of C tiles out to its
+blocks in turn, so the products at the end of the list make up the tail of
+the launch; "largest_first" puts the big products first and leaves the small
+ones to fill the tail.
+
+Choices are cached in-process per signature (precision, tau, the products'
+orders rounded to powers of two), so a serving loop pays for a tuning run
+once per kind of batch.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+LEAVES = (16, 32, 64, 128)
+ORDERS = ("given", "largest_first")
+
+_CACHE: dict = {}
+
+
+@dataclass
+class Choice:
+    leaf: int
+    order: str
+    ms: float
+    trials: dict = field(default_factory=dict)   # (leaf, order) -> ms
+
+    def permutation(self, ns):
+        return order_of(self.order, ns)
+
+
+def order_of(order: str, ns):
+    """Indices of the products in launch order."""
+    idx = list(range(len(ns)))
+    if order == "largest_first":
+        idx.sort(key=lambda p: (-ns[p], p))
+    return idx
+
+
+def signature(ns, taus, precision: str):
+    return (precision, tuple(sorted(round(math.log2(max(n, 1))) for n in ns)),
+            tuple(sorted(set(float(t) for t in taus))))
+
+
+def cached(ns, taus, precision: str):
+    return _CACHE.get(signature(ns, taus, precision))
+
+
+def tune_batch(pairs, taus, precision: str = "tf32x3", leaves=LEAVES, orders=ORDERS,
+               reps: int = 3, use_cache: bool = True) -> Choice:
+    """Pick (leaf, order) for the batch of products ``pairs`` = [(A, B), ...]
+    (square float32 CUDA tensors) at thresholds ``taus``."""
+    import torch
+    from . import Context
+    ns = [A.shape[0] for A, _ in pairs]
+    sig = signature(ns, taus, precision)
+    if use_cache and sig in _CACHE:
+        return _CACHE[sig]
+    stream = torch.cuda.current_stream()
+    trials = {}
+    for b in leaves:
+        ctx = Context(leaf=b, precision=precision, checked=True)
+        trees_a, trees_b = [], []
+        for A, B in pairs:
+            ta = ctx.build_norms(A)
+            trees_a.append(ta)
+            trees_b.append(ta if B is A else ctx.build_norms(B))
+        Cs = [torch.empty_like(A) for A, _ in pairs]
+        for order in orders:
+            perm = order_of(order, ns)
+            args = ([trees_a[p] for p in perm], [trees_b[p] for p in perm],
+                    [taus[p] for p in perm], None, None, [Cs[p] for p in perm])
+            ctx.set_checked(True)
+            ctx.multiply_batched(*args)          # sizes the pools
+            ctx.set_checked(False)
+            ctx.multiply_batched(*args)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.multiply_batched(*args)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.stats()                          # raises if a timed call failed
+            trials[(b, order)] = e0.elapsed_time(e1) / reps
+        for t in trees_a + trees_b:
+            t.close()
+        del Cs
+        ctx.close()
+        torch.cuda.empty_cache()
+    (b, order), ms = min(trials.items(), key=lambda kv: kv[1])
+    choice = Choice(leaf=b, order=order, ms=ms, trials=trials)
+    _CACHE[sig] = choice
+    return choice
