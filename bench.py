@@ -270,7 +270,8 @@ def run_quick(args, P, A, n, b, stream):
     print(json.dumps({"mode": "quick", "n": n, "leaf": b, "tau": tau,
                       "precision": args.precision, "ms_per_step": ms,
                       "kept_tflops": st["kept_flops"] / (ms * 1e-3) / 1e12,
-                      "ms_symbolic": st["ms_symbolic"], "ms_numeric": st["ms_numeric"],
+                      "ms_symbolic": st["ms_symbolic"], "ms_pack": st["ms_pack"],
+                      "ms_numeric": st["ms_numeric"],
                       "leaf_triples": st["leaf_triples"]}), flush=True)
 
 
@@ -327,9 +328,10 @@ def run_batched(args, P, dev, rank, world, dist):
     s = torch.cuda.Stream(device=dev)
     P._abi.spamm_set_stream(ctx.handle, s.cuda_stream)
 
+    pmats = [mats[p] for p in perm]
+
     def step():
-        for t, p in zip(trees, perm):
-            t.rebuild(mats[p])
+        ctx.rebuild_batched(trees, pmats)
         ctx.multiply_batched(trees, trees, taus, None, None, Cs)
 
     s.wait_stream(torch.cuda.current_stream())
@@ -481,7 +483,8 @@ def run_batched(args, P, dev, rank, world, dist):
         cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                "sample": f"product of n={ns[perm[q]]} (median n of the batch): " + desc}
     # per product: norm leaves, upper tiers, cull, grouping; one leaf launch
-    launches = sum(kernels_per_step(t.depth, b) - 1 for t in trees) + -(-count // 64)
+    launches = (sum(kernels_per_step(t.depth, b, args.precision) - 1 for t in trees)
+                + -(-count // 64))
     line = {
         "metric": "SpAMM leaf TFLOP/s (kept 2b^3 flops / step time), batch of 64 products",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -508,12 +511,13 @@ def run_batched(args, P, dev, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
-def kernels_per_step(d, leaf):
+def kernels_per_step(d, leaf, precision="tf32x3", same_tree=True):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
     # norm leaves + upper tiers | cull root, tiers < tt, finish | group x3,
-    # tile cull | leaf products
-    return (1 + math.ceil(d / 5)) + (tt + 2) + 4 + 1
+    # tile cull | norm maxima + packs (tensor cores) | leaf products
+    packs = 0 if precision == "fp32" else 1 + (1 if same_tree else 2)
+    return (1 + math.ceil(d / 5)) + (tt + 2) + 4 + packs + 1
 
 
 def main():
@@ -703,7 +707,7 @@ def main():
         "ms_symbolic": st0["ms_symbolic"], "ms_numeric": leaf_ms,
         "parity_sampled": parity, "alt_precision": alt,
         "tau_sweep": sweep, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": kernels_per_step(st["depth"], b) * args.steps, "clocks": clk,
+        "gpu_launches": kernels_per_step(st["depth"], b, args.precision) * args.steps, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     if dist:

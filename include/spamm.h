@@ -9,12 +9,13 @@
  *
  * The engine runs in four stages, each a CUDA kernel on one GPU:
  *   1. spamm_build_norms: leaf squared norms (FP64) and the upper tiers of the
- *      norm quadtree, plus, for tensor-core precisions, the matrix repacked
- *      into tensor-core leaf tiles;
+ *      norm quadtree;
  *   2. spamm_multiply: a level-by-level cull from the root that keeps a block
  *      triple (I,K,J) iff nA2 * nB2 >= tau^2 with both norms non-zero;
- *   3. grouping of the surviving leaf triples by 128 x 128 tile of C with
- *      the kept (row-leaf, column-leaf) pairs of every K as a bit mask;
+ *   3. grouping of the surviving leaf triples by 128 x 256 tile of C with
+ *      the kept (row-leaf, column-leaf) pairs of every K as bit masks, and,
+ *      for tensor-core precisions, the leaves that can take part in a kept
+ *      product repacked into tensor-core leaf tiles;
  *   4. the dense leaf products accumulated into C in ascending K.
  *
  * Conventions for every entry point:
@@ -93,7 +94,7 @@ typedef struct {
     int64_t tie_band;                  /* tested triples with | ||A|| ||B|| - tau |
                                           <= tie_rel * tau, over all tiers */
     int64_t active_steps;              /* (C tile, K) pairs with >= 1 kept product */
-    int64_t tiles;                     /* 128 x 128 C tiles (incl. empty ones) */
+    int64_t tiles;                     /* 128 x 256 C tiles (incl. empty ones) */
     double kept_flops;                 /* 2 b^3 per leaf triple */
     double dense_flops;                /* 2 n^3 (Appendix A, square case) */
     int64_t pool_bytes;                /* current pool size */
@@ -101,6 +102,7 @@ typedef struct {
     float ms_symbolic;                 /* cull + grouping, CUDA events */
     float ms_numeric;                  /* leaf products + C epilogue */
     float ms_total;
+    float ms_pack;                     /* tensor-core packs of the needed leaves */
 } spamm_stats_t;
 
 /* Create a context bound to the current CUDA device and to `stream` (a
@@ -131,7 +133,9 @@ const char *spamm_last_error(const spamm_ctx *ctx);
  * (the smallest d >= 0 with b 2^d >= n), the matrix zero-padded to
  * n_p = b 2^d, leaf squared norms summed in FP64 from exact FP64 squares,
  * and each upper node the sum of its four children.  For tensor-core
- * precisions it also writes the leaf tiles in tensor-core layout.  *out is
+ * precisions it allocates (but does not fill) the leaf tiles in tensor-core
+ * layout: spamm_multiply writes those of the leaves that can take part in a
+ * kept product, once tau and the other operand are known.  *out is
  * owned by the caller (spamm_tree_destroy).  The tree keeps the pointer A:
  * the caller keeps A alive and unchanged until the last multiply that reads
  * the tree has completed on the stream.  INVALID_ARG (n <= 0, lda < n, NULL
@@ -145,6 +149,14 @@ spamm_status spamm_build_norms(spamm_ctx *ctx, const float *A, int64_t n, int64_
  * spamm_build_norms. */
 spamm_status spamm_tree_rebuild(spamm_ctx *ctx, spamm_tree *tree, const float *A,
                                 int64_t lda);
+
+/* spamm_tree_rebuild for `count` trees at once (host arrays of length
+ * count; A[p] device matrices of the trees' n, lda[p] >= n), spread over the
+ * same side streams as spamm_multiply_batched and joined back into ctx's
+ * stream before the call returns control of it.  Capturable in a CUDA graph.
+ * INVALID_ARG, CUDA. */
+spamm_status spamm_tree_rebuild_batched(spamm_ctx *ctx, int32_t count, spamm_tree *const *trees,
+                                        const float *const *A, const int64_t *lda);
 
 /* Free a tree.  Synchronises its context's stream first. */
 spamm_status spamm_tree_destroy(spamm_tree *tree);
@@ -175,11 +187,13 @@ spamm_status spamm_multiply(spamm_ctx *ctx, const spamm_tree *A, const spamm_tre
  * independent products of possibly different n:
  *   C[p] = alpha[p] * SpAMM(A[p], B[p]; tau[p]) + beta[p] * C[p],  p < count.
  * All trees must be built under ctx's configuration (leaf size, precision);
- * A[p] and B[p] have the same n.  Stages 2-3 run per product in a
- * sub-context of ctx (own pool, created on first use and kept); stage 4 of
+ * A[p] and B[p] have the same n.  Stages 2-3 (and the packs) run per
+ * product in a sub-context of ctx (own pool, created on first use and kept),
+ * the products spread over eight side streams that fork from and join back
+ * into ctx's stream, so small products overlap on the device; stage 4 of
  * all products is one persistent launch over the concatenated list of C
  * tiles (up to 64 products per launch) on the tensor-core precisions, one
- * launch per product for SPAMM_PREC_FP32.  Every product's C is the same,
+ * launch per product (on the side streams) for SPAMM_PREC_FP32.  Every product's C is the same,
  * bit for bit, as a single spamm_multiply of it.  Arrays are host arrays of
  * length count; matrices are device memory.  In checked mode the call waits,
  * grows the pool of any product that overflowed and re-runs the batch; with

@@ -17,7 +17,8 @@ from ._abi import (PRECISIONS, SpammError, spamm_build_norms, spamm_config_defau
                    spamm_create, spamm_destroy, spamm_multiply, spamm_multiply_batched,
                    spamm_multiply_host,
                    spamm_reserve, spamm_set_checked, spamm_set_stream, spamm_stats,
-                   spamm_tree_destroy, spamm_tree_norms, spamm_tree_rebuild, spamm_tree_shape,
+                   spamm_tree_destroy, spamm_tree_norms, spamm_tree_rebuild,
+                   spamm_tree_rebuild_batched, spamm_tree_shape,
                    spamm_triples)
 
 __all__ = ["Context", "Tree", "SpammError", "PRECISIONS", "load"]
@@ -110,6 +111,20 @@ class Context:
         spamm_multiply(self.handle, A.handle, B.handle, tau, alpha, beta, C.data_ptr(), ldc)
         return C
 
+    def rebuild_batched(self, trees, mats):
+        """Tree.rebuild for many trees at once (the norm builds overlap on
+        the context's side streams)."""
+        ldas = []
+        for t, A in zip(trees, mats):
+            n, lda = _check_matrix(A)
+            if n != t.n:
+                raise ValueError("rebuild needs the same n")
+            ldas.append(lda)
+        spamm_tree_rebuild_batched(self.handle, [t.handle for t in trees],
+                                   [A.data_ptr() for A in mats], ldas)
+        for t, A in zip(trees, mats):
+            t.A = A
+
     def multiply_batched(self, As, Bs, taus, alphas=None, betas=None, Cs=None):
         """Independent products C[p] = alpha[p] SpAMM(A[p], B[p]; tau[p]) +
         beta[p] C[p] in one call (one persistent leaf launch on the
@@ -169,6 +184,7 @@ class Context:
             "kept_flops": s.kept_flops, "dense_flops": s.dense_flops,
             "pool_bytes": s.pool_bytes, "pool_needed_bytes": s.pool_needed_bytes,
             "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
+            "ms_pack": s.ms_pack,
         }
 
     def triples(self) -> np.ndarray:

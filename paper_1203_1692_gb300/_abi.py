@@ -49,7 +49,7 @@ class spamm_stats_t(ctypes.Structure):
                 ("kept_flops", ctypes.c_double), ("dense_flops", ctypes.c_double),
                 ("pool_bytes", ctypes.c_int64), ("pool_needed_bytes", ctypes.c_int64),
                 ("ms_symbolic", ctypes.c_float), ("ms_numeric", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_pack", ctypes.c_float)]
 
 
 _vp = ctypes.c_void_p
@@ -69,6 +69,8 @@ SIGNATURES = {
     "spamm_last_error": (ctypes.c_char_p, [_vp]),
     "spamm_build_norms": (_i32, [_vp, _vp, _i64, _i64, ctypes.POINTER(_vp)]),
     "spamm_tree_rebuild": (_i32, [_vp, _vp, _vp, _i64]),
+    "spamm_tree_rebuild_batched": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                          ctypes.POINTER(_i64)]),
     "spamm_tree_destroy": (_i32, [_vp]),
     "spamm_tree_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "spamm_tree_norms": (_i32, [_vp, _vp, _vp, _i64]),
@@ -153,6 +155,16 @@ def spamm_build_norms(ctx, A_ptr: int, n: int, lda: int):
 
 def spamm_tree_rebuild(ctx, tree, A_ptr: int, lda: int) -> None:
     check(lib().spamm_tree_rebuild(ctx, tree, _vp(A_ptr), lda), ctx)
+
+
+def spamm_tree_rebuild_batched(ctx, trees, A_ptrs, ldas) -> None:
+    count = len(trees)
+    if not (len(A_ptrs) == len(ldas) == count):
+        raise ValueError("batched arguments differ in length")
+    t = (_vp * max(count, 1))(*trees)
+    a = (_vp * max(count, 1))(*[_vp(x) for x in A_ptrs])
+    ld = (_i64 * max(count, 1))(*[int(x) for x in ldas])
+    check(lib().spamm_tree_rebuild_batched(ctx, count, t, a, ld), ctx)
 
 
 def spamm_tree_destroy(tree) -> None:

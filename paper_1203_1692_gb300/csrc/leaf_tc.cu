@@ -152,8 +152,10 @@ __device__ __forceinline__ int tile_at(int k, int tr, int tc) {
     return (g * kGroupRows + w % rows) * tc + w / rows;
 }
 
+// TMEM chunks of a tile with `iters` K-chunk iterations; a tile without
+// kept products has none (its epilogue writes beta * C straight away).
 __device__ __forceinline__ uint32_t chunks_of(uint32_t iters) {
-    return iters == 0 ? 1u : (iters + kChunkIters - 1) / kChunkIters;
+    return (iters + kChunkIters - 1) / kChunkIters;
 }
 
 template <int PREC>
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         // Lane 0 alone: per stage one wait and one commit.  Iteration i of a
         // tile (step i / CHUNKS, K-chunk i % CHUNKS) opens a new TMEM chunk
         // when i % kChunkIters == 0 and closes it at the chunk's last
-        // iteration; a tile without steps gets one empty (zeroed) chunk.
+        // iteration; a tile without steps is skipped (no chunk).
         if (lane == 0) {
             unsigned long long stage_it = 0;
             uint32_t ccount = 0;  // chunks opened so far (selects the TMEM buffer)
@@ -414,19 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 const TcProd& q = bt.prods[pi];
                 const uint32_t ns = q.steps[tile_at(k - q.base, q.tr, q.tc)];
                 const uint32_t iters = ns * CHUNKS;
-                if (iters == 0) {
-                    const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
-                    if (wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
-                        tc_fence_after();
-                        mma<PREC>(tmem + ab * 256, zdesc, zdesc, make_idesc(T::kAB, 128, 256),
-                                  dis0, 0u);
-                        tc_commit(smem_u32(&bar_accf[ab]));
-                    } else {
-                        ok = false;
-                    }
-                    ++ccount;
-                    continue;
-                }
+                if (iters == 0) continue;
                 uint32_t i = 0;
                 while (i < iters && ok) {
                     const int s = (int)(stage_it % ST);

@@ -1,12 +1,14 @@
-// Stage 1: the FP64 norm quadtree (Sec. II.A-B, Eq. (norm)) and, for the
-// tensor-core precisions, the leaf tiles in tcgen05 shared-memory layout.
+// Stage 1: the FP64 norm quadtree (Sec. II.A-B, Eq. (norm)); and, for the
+// tensor-core precisions, the leaf tiles in tcgen05 shared-memory layout,
+// written inside a multiply (after the thresholds are known) for the leaves
+// that can take part in a kept product only.
 //
 // Leaf squares: a thread owns four consecutive columns of one leaf row-strip
-// and sums (double)a * (double)a (exact) down the strip's b rows; the b/4
-// lanes that share a leaf combine their partial sums with a segmented
-// xor-shuffle reduction.  The kernel reads each element of A once, with
-// 16-byte loads when A and lda allow it, so it is bound by HBM bandwidth.
-// With tensor-core packs the same sums come from k_leaf_pack below.
+// and sums their squares down the strip's b rows (exact squares, FP32-pair
+// accumulation folded into FP64, see k_leaf_norms); the b/4 lanes that share
+// a leaf combine their partial sums with a segmented xor-shuffle reduction.
+// The kernel reads each element of A once, with 16-byte loads when A and lda
+// allow it, so it is bound by HBM bandwidth.
 // The upper tiers come from a second kernel that builds five tiers per pass
 // in shared memory, each node the sum of its four children in the order
 // A11 + A12 + A21 + A22.
@@ -26,6 +28,8 @@
 // leaf (I, K) with rows = i (K-major as stored); the B role holds leaf (K, J)
 // transposed, rows = j.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "spamm_internal.cuh"
 
@@ -48,46 +52,166 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// Leaf squared norms only (FP32 leaf products need no packs).
-template <bool VEC>
+// Leaf squared norms without the FP64 pipe, which is narrow on GB300.
+//
+// A block covers one leaf row-strip (LEAF rows) x 512 columns; a thread owns
+// four consecutive columns.  Its squares are summed in FP32 pairs: with x
+// scaled by a power of two to xs in [0, 2), xs^2 = p + e exactly (p = xs*xs,
+// e = fma(xs, xs, -p)), p enters the running pair (hi, lo) through an
+// error-free two-sum and e goes into lo.  The scale follows the largest
+// exponent seen so far (rescaling the pair exactly by a power of two; terms
+// 2^-100 below the largest square are far under FP64's resolution of the
+// sum).  Every eight rows the pair is folded into an FP64 sum, so a pair
+// holds at most 32 terms and the sum's relative error stays near 1e-13, far
+// inside the 1e-6 band the cull reports around tau.  The lanes of one leaf
+// then combine their FP64 sums with a segmented xor-shuffle reduction.
+// Inf or NaN anywhere makes the leaf's norm NaN.
+__device__ __forceinline__ float pow2f(int k) {          // 2^k, k in [-127, 127]
+    return k >= -126 ? __int_as_float((k + 127) << 23) : __int_as_float(1 << 22);
+}
+
+__device__ __forceinline__ double pow2d(int k) {         // 2^k, k in [-1022, 1023]
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+struct SqAcc {
+    float hi = 0.f, lo = 0.f, sc = 0x1p127f;
+    int E = 0;                  // biased exponent of the scale: x = xs * 2^(E - 127)
+    bool bad = false;
+    double sum = 0.0;
+
+    // explicit round-to-nearest operations: the error-free transformations
+    // must not be contracted into fused multiply-adds
+    __device__ __forceinline__ void add1(float x) {
+        const float xs = __fmul_rn(x, sc);
+        const float p = __fmul_rn(xs, xs);
+        const float e = fmaf(xs, xs, -p);
+        const float t = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void add4(float4 v) {
+        const int m = max(max((__float_as_int(v.x) >> 23) & 0xff, (__float_as_int(v.y) >> 23) & 0xff),
+                          max((__float_as_int(v.z) >> 23) & 0xff, (__float_as_int(v.w) >> 23) & 0xff));
+        if (m == 0xff) {
+            bad = true;
+            return;
+        }
+        if (m > E) {
+            const int k = 2 * (E - m);
+            const float f = k >= -126 ? pow2f(k) : 0.f;
+            hi = __fmul_rn(hi, f);
+            lo = __fmul_rn(lo, f);
+            E = m;
+            sc = pow2f(127 - E);
+        }
+        add1(v.x);
+        add1(v.y);
+        add1(v.z);
+        add1(v.w);
+    }
+    __device__ __forceinline__ void fold() {
+        sum = __dadd_rn(sum, __dmul_rn(__dadd_rn((double)hi, (double)lo), pow2d(2 * E - 254)));
+        hi = lo = 0.f;
+    }
+    __device__ __forceinline__ double result() {
+        fold();
+        return bad ? __longlong_as_double(0x7ff8000000000000ll) : sum;
+    }
+};
+
+template <int LEAF, bool VEC>
 __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A, int64_t n,
-                                                    int64_t lda, int b, int64_t nb, int64_t nl,
+                                                    int64_t lda, int64_t nb, int64_t nl,
                                                     double* __restrict__ leaf) {
     const int64_t I = blockIdx.y;                       // leaf row
     const int64_t col0 = (int64_t)blockIdx.x * 512 + 4 * threadIdx.x;
-    const int64_t K = col0 / b;                          // leaf column
-    const int lanes = b >> 2;                            // lanes per leaf
-    double s = 0.0;
-    const int64_t r0 = I * b;
-    for (int r = 0; r < b; ++r) {
-        const int64_t row = r0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row < n) {
-            const float* p = A + row * lda + col0;
-            if (VEC && col0 + 3 < n) {
-                v = __ldg(reinterpret_cast<const float4*>(p));
-            } else {
-                if (col0 + 0 < n) v.x = __ldg(p + 0);
-                if (col0 + 1 < n) v.y = __ldg(p + 1);
-                if (col0 + 2 < n) v.z = __ldg(p + 2);
-                if (col0 + 3 < n) v.w = __ldg(p + 3);
-            }
+    const int64_t K = col0 / LEAF;                       // leaf column
+    constexpr int lanes = LEAF / 4;                      // lanes per leaf
+    const int64_t r0 = I * LEAF;
+    const float* base = A + r0 * lda + col0;
+    SqAcc acc;
+    if (VEC && col0 + 3 < n && r0 + LEAF <= n) {
+        for (int r8 = 0; r8 < LEAF; r8 += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)(r8 + q) * lda));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc.add4(v[q]);
+            acc.fold();
         }
-        const double x = v.x, y = v.y, z = v.z, w = v.w;
-        s += x * x;
-        s += y * y;
-        s += z * z;
-        s += w * w;
+    } else {
+        for (int r = 0; r < LEAF; ++r) {
+            if (r0 + r >= n) break;
+            const float* p = base + (int64_t)r * lda;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col0 + 0 < n) v.x = __ldg(p + 0);
+            if (col0 + 1 < n) v.y = __ldg(p + 1);
+            if (col0 + 2 < n) v.z = __ldg(p + 2);
+            if (col0 + 3 < n) v.w = __ldg(p + 3);
+            acc.add4(v);
+            if ((r & 7) == 7) acc.fold();
+        }
     }
+    double s = acc.result();
     // segmented reduction over the lanes of one leaf
     for (int off = lanes >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if ((threadIdx.x & (lanes - 1)) == 0 && K < nl) leaf[I * nb + K] = s;
 }
 
-// Leaf norms plus tensor-core packs.  A block owns one leaf row-strip (b
-// rows) x 128 columns (TL leaves).  It stages the strip in shared memory
-// (16-byte loads) while forming the leaf squared norms (FP64), then produces
-// the pieces in output order: thread t writes the t-th, (t+128)-th, ...
+// Per-K maxima of the leaf squared norms, which bound every leaf product a
+// multiply can keep (the SpAMM condition is monotone in each norm):
+//   colmaxA[K] = max_I ||A_IK||^2,   rowmaxB[K] = max_J ||B_KJ||^2.
+// A piece of A (I, K) can be read only if ||A_IK||^2 * rowmaxB[K] passes the
+// condition, a piece of B (K, J) only if colmaxA[K] * ||B_KJ||^2 does.
+// blockIdx.y = 0: a block per 32 columns of A, lane = column, the eight
+// warps split the rows and combine their maxima in shared memory;
+// blockIdx.y = 1: a warp per row K of B.
+__global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ leafA,
+                                                  const double* __restrict__ leafB, int64_t nb,
+                                                  int64_t nl, double* __restrict__ colmaxA,
+                                                  double* __restrict__ rowmaxB) {
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.y == 0) {
+        for (int64_t K0 = (int64_t)blockIdx.x * 32; K0 < nl; K0 += (int64_t)gridDim.x * 32) {
+            const int64_t K = K0 + lane;
+            double m = 0.0;
+            if (K < nl) {
+#pragma unroll 4
+                for (int64_t I = warp; I < nl; I += 8) m = fmax(m, leafA[I * nb + K]);
+            }
+            part[warp][lane] = m;
+            __syncthreads();
+            if (warp == 0 && K < nl) {
+                double r = part[0][lane];
+#pragma unroll
+                for (int w = 1; w < 8; ++w) r = fmax(r, part[w][lane]);
+                colmaxA[K] = r;
+            }
+            __syncthreads();
+        }
+    } else {
+        const int64_t warps = (int64_t)gridDim.x * 8;
+        for (int64_t K = (int64_t)blockIdx.x * 8 + warp; K < nl; K += warps) {
+            double m = 0.0;
+#pragma unroll 4
+            for (int64_t J = lane; J < nl; J += 32) m = fmax(m, leafB[K * nb + J]);
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) rowmaxB[K] = m;
+        }
+    }
+}
+
+// Tensor-core packs of the leaves a multiply can read.  A block owns one
+// leaf row-strip (b rows) x 128 columns (TL leaves): it decides which of its
+// leaves are needed as A-role pieces (rowmaxB given) and as B-role pieces
+// (colmaxA given) with the SpAMM condition above, returns at once if none
+// is, else stages the strip in shared memory (16-byte loads) and produces
+// the needed pieces in output order: thread t writes the t-th, (t+128)-th, ...
 // 16-byte unit of each piece, reading the elements that unit holds from the
 // staged strip (a row quad for the A role, a column quad for the B role),
 // splitting them into hi/lo parts and storing both parts.  The A-role
@@ -97,7 +221,9 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
 template <int PK, int LEAF>
 __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, int64_t n,
                                                    int64_t lda, int64_t nb, int64_t nl, int64_t nlp,
-                                                   double* __restrict__ leaf,
+                                                   const double* __restrict__ leaf,
+                                                   const double* __restrict__ rowmaxB,
+                                                   const double* __restrict__ colmaxA, Thresh th,
                                                    void* __restrict__ pa0, void* __restrict__ pa1,
                                                    void* __restrict__ pb0, void* __restrict__ pb1) {
     constexpr int TL = 128 / LEAF;
@@ -110,7 +236,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     constexpr int LDS = 128 + 4;                         // padded staging row
     extern __shared__ __align__(16) float raw_dyn[];     // LEAF x LDS staged strip
     float (*raw)[LDS] = reinterpret_cast<float (*)[LDS]>(raw_dyn);
-    __shared__ double part[4][TL];
+    __shared__ int needA[TL], needB[TL], any;
     // leaf rows vary fastest across blocks, so the blocks running at once
     // write neighbouring A-role pieces
     const int64_t I = blockIdx.x;                        // leaf row
@@ -118,10 +244,20 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     const int64_t r0 = I * LEAF, c0 = Q0 * LEAF;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
+    if (t == 0) any = 0;
+    __syncthreads();
+    if (t < TL) {
+        const int64_t Q = Q0 + t;
+        bool tie;
+        const double nq = Q < nl ? leaf[I * nb + Q] : 0.0;
+        needA[t] = (rowmaxB && Q < nl && spamm_keep(nq, rowmaxB[Q], th, &tie)) ? 1 : 0;
+        needB[t] = (colmaxA && Q < nl && spamm_keep(colmaxA[I], nq, th, &tie)) ? 1 : 0;
+        if (needA[t] | needB[t]) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (!any) return;
     const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
     const int cq = 4 * lane;
-    const int x = cq / LEAF;
-    double s = 0.0;
 #pragma unroll 4
     for (int r = warp; r < LEAF; r += 4) {
         const int64_t row = r0 + r, col = c0 + cq;
@@ -137,22 +273,9 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                 if (col + 3 < n) v.w = __ldg(p + 3);
             }
         }
-        const double dx = v.x, dy = v.y, dz = v.z, dw = v.w;
-        s += dx * dx;
-        s += dy * dy;
-        s += dz * dz;
-        s += dw * dw;
         *reinterpret_cast<float4*>(&raw[r][cq]) = v;
     }
-    // leaf squared norms: lanes of one leaf, then the four warps, fixed order
-    constexpr int LPL = LEAF / 4;                        // lanes per leaf
-    for (int o = LPL >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((lane % LPL) == 0) part[warp][x] = s;
     __syncthreads();
-    if (t < TL) {
-        const double v = ((part[0][t] + part[1][t]) + part[2][t]) + part[3][t];
-        if (Q0 + t < nl) leaf[I * nb + Q0 + t] = v;
-    }
     // pieces, in output order
     constexpr int UNITS = TL * CH * UPP;                 // per role and part
     for (int u = t; u < UNITS; u += 128) {
@@ -161,7 +284,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
         const int rg = w / (8 * CPC), core = (w / 8) % CPC, rr = w % 8;
         const int prow = rg * 8 + rr;                    // row of the piece (b of them)
         // ---- A role: piece (leaf xa, chunk kca): rows = i, k contiguous
-        {
+        if (pa0 && needA[pc / CH]) {
             const int xa = pc / CH, kca = pc % CH;
             const float* src = &raw[prow][xa * LEAF + kca * 16 + core * EPU];
             const size_t g = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * PIECE + (size_t)w * 16;
@@ -196,7 +319,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
         }
         // ---- B role: piece (chunk kcb, leaf xb): rows = column j of the leaf,
         //      k = row of the leaf contiguous
-        {
+        if (pb0 && needB[pc % TL]) {
             const int kcb = pc / TL, xb = pc % TL;
             const int colj = xb * LEAF + prow;           // staged column
             const int k0 = kcb * 16 + core * EPU;        // staged first row
@@ -279,45 +402,19 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(leaf, 0, sizeof(double) * t->nb * t->nb, s);
     if (e != cudaSuccess) return e;
     const bool vec = ((reinterpret_cast<uintptr_t>(t->A) & 15) == 0) && (t->lda % 4 == 0);
-    void* pa0 = t->packA[0];
-    void* pa1 = t->packA[1];
-    void* pb0 = t->packB[0];
-    void* pb1 = t->packB[1];
-    const int pk = t->precision == SPAMM_PREC_FP32    ? 0
-                   : t->precision == SPAMM_PREC_TF32  ? 1
-                   : t->precision == SPAMM_PREC_TF32X3 ? 2
-                                                       : 3;
-    if (pk == 0) {
-        dim3 grid((unsigned)((t->nl * t->b + 511) / 512), (unsigned)t->nl);
-        if (vec)
-            k_leaf_norms<true><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->b, t->nb, t->nl, leaf);
-        else
-            k_leaf_norms<false><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->b, t->nb, t->nl, leaf);
-    } else {
-        const int tl = 128 / t->b;
-        dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));
-        const size_t smem = (size_t)t->b * (128 + 4) * sizeof(float);
-#define SPAMM_LP(PKV, LV)                                                                      \
-    do {                                                                                       \
-        if (smem > 48 * 1024)                                                                  \
-            cudaFuncSetAttribute(k_leaf_pack<PKV, LV>,                                         \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-        k_leaf_pack<PKV, LV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl, t->nlp, \
-                                                     leaf, pa0, pa1, pb0, pb1);                \
+    dim3 grid((unsigned)((t->nl * t->b + 511) / 512), (unsigned)t->nl);
+#define SPAMM_LN(LV)                                                                          \
+    do {                                                                                      \
+        if (vec)                                                                              \
+            k_leaf_norms<LV, true><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, leaf); \
+        else                                                                                  \
+            k_leaf_norms<LV, false><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, leaf); \
     } while (0)
-#define SPAMM_LP_B(LV)                \
-    do {                              \
-        if (pk == 1) SPAMM_LP(1, LV); \
-        else if (pk == 2) SPAMM_LP(2, LV); \
-        else SPAMM_LP(3, LV);         \
-    } while (0)
-        if (t->b == 16) SPAMM_LP_B(16);
-        else if (t->b == 32) SPAMM_LP_B(32);
-        else if (t->b == 64) SPAMM_LP_B(64);
-        else SPAMM_LP_B(128);
-#undef SPAMM_LP_B
-#undef SPAMM_LP
-    }
+    if (t->b == 16) SPAMM_LN(16);
+    else if (t->b == 32) SPAMM_LN(32);
+    else if (t->b == 64) SPAMM_LN(64);
+    else SPAMM_LN(128);
+#undef SPAMM_LN
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int L = t->d;
@@ -331,6 +428,62 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
         L -= levels;
     }
     return cudaSuccess;
+}
+
+// Packs for one multiply: the per-K maxima of the two leaf tiers, then the
+// needed A-role pieces of A and B-role pieces of B (one pass when A and B are
+// the same tree).  `scratch` holds 2 nb doubles.
+cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, double rel,
+                         double* scratch, int sm_count, cudaStream_t s) {
+    const int64_t off_leaf = (((int64_t)1 << (2 * A->d)) - 1) / 3;
+    const double* la = A->pyr + off_leaf;
+    const double* lb = B->pyr + off_leaf;
+    double* colmaxA = scratch;
+    double* rowmaxB = scratch + A->nb;
+    const int blocks = (int)std::min<int64_t>((A->nl + 31) / 32 * 4, 8 * (int64_t)sm_count);
+    k_leaf_max<<<dim3((unsigned)std::max(blocks, 1), 2), 256, 0, s>>>(la, lb, A->nb, A->nl,
+                                                                        colmaxA, rowmaxB);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const Thresh th = make_thresh(tau, rel);
+    const int pk = A->precision == SPAMM_PREC_TF32 ? 1 : A->precision == SPAMM_PREC_TF32X3 ? 2 : 3;
+    const int tl = 128 / A->b;
+    const size_t smem = (size_t)A->b * (128 + 4) * sizeof(float);
+    auto one = [&](const spamm_tree* t, const double* rmB, const double* cmA) -> cudaError_t {
+        const bool roleA = rmB != nullptr, roleB = cmA != nullptr;
+        void* pa0 = roleA ? t->packA[0] : nullptr;
+        void* pa1 = roleA ? t->packA[1] : nullptr;
+        void* pb0 = roleB ? t->packB[0] : nullptr;
+        void* pb1 = roleB ? t->packB[1] : nullptr;
+        const double* leaf = t->pyr + off_leaf;
+        dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));
+#define SPAMM_LP(PKV, LV)                                                                    \
+    do {                                                                                     \
+        if (smem > 48 * 1024)                                                                \
+            cudaFuncSetAttribute(k_leaf_pack<PKV, LV>,                                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+        k_leaf_pack<PKV, LV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,       \
+                                                     t->nlp, leaf, rmB, cmA, th, pa0, pa1,   \
+                                                     pb0, pb1);                              \
+    } while (0)
+#define SPAMM_LP_B(LV)                     \
+    do {                                   \
+        if (pk == 1) SPAMM_LP(1, LV);      \
+        else if (pk == 2) SPAMM_LP(2, LV); \
+        else SPAMM_LP(3, LV);              \
+    } while (0)
+        if (t->b == 16) SPAMM_LP_B(16);
+        else if (t->b == 32) SPAMM_LP_B(32);
+        else if (t->b == 64) SPAMM_LP_B(64);
+        else SPAMM_LP_B(128);
+#undef SPAMM_LP_B
+#undef SPAMM_LP
+        return cudaGetLastError();
+    };
+    if (A == B) return one(A, rowmaxB, colmaxA);
+    e = one(A, rowmaxB, nullptr);
+    if (e != cudaSuccess) return e;
+    return one(B, nullptr, colmaxA);
 }
 
 }  // namespace spamm

@@ -86,6 +86,19 @@ spamm_status ensure_tiles(spamm_ctx* ctx, int64_t tiles) {
     return SPAMM_OK;
 }
 
+spamm_status ensure_need(spamm_ctx* ctx, int64_t nb) {
+    if (2 * nb <= ctx->need_cap) return SPAMM_OK;
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->need);
+    ctx->need = nullptr;
+    ctx->need_cap = 0;
+    const int64_t cap = std::max<int64_t>(2 * nb, 1024);
+    cudaError_t e = cudaMalloc(&ctx->need, sizeof(double) * cap);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "norm maxima");
+    ctx->need_cap = cap;
+    return SPAMM_OK;
+}
+
 void free_tree_storage(spamm_tree* t) {
     cudaFree(t->pyr);
     for (int i = 0; i < 2; ++i) {
@@ -179,11 +192,20 @@ spamm_status spamm_destroy(spamm_ctx* ctx) {
     cudaFree(ctx->tile_fill);
     cudaFree(ctx->tile_off);
     cudaFree(ctx->tile_steps);
+    cudaFree(ctx->need);
     cudaFree(ctx->dA);
     cudaFree(ctx->dB);
     cudaFree(ctx->dC);
     for (int i = 0; i < 4; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->aux_ready) {
+        for (int i = 0; i < spamm_ctx::kAux; ++i) {
+            cudaStreamSynchronize(ctx->aux[i]);
+            cudaStreamDestroy(ctx->aux[i]);
+            cudaEventDestroy(ctx->aux_ev[i]);
+        }
+        cudaEventDestroy(ctx->fork_ev);
+    }
     cudaGetLastError();
     delete ctx;
     return SPAMM_OK;
@@ -314,6 +336,9 @@ static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
     if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau, tt);
     if (e == cudaSuccess) e = launch_group(ctx, A, B, tau, tt);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
+    if (e == cudaSuccess && precision_uses_tc(ctx->cfg.precision))
+        e = launch_packs(A, B, tau, ctx->cfg.tie_rel, ctx->need, ctx->sm_count, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
     if (e == cudaSuccess) {
         if (ctx->cfg.precision == SPAMM_PREC_FP32)
             e = launch_leaf_simt(ctx, A, B, alpha, beta, C, ldc);
@@ -353,6 +378,7 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
     if (ldc < A->n) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "ldc below n");
     const int64_t tiles = (int64_t)tile_rows(A) * tile_cols(A);
     spamm_status st = ensure_tiles(ctx, tiles);
+    if (st == SPAMM_OK) st = ensure_need(ctx, A->nb);
     if (st != SPAMM_OK) return st;
     ctx->last_batch = 0;
     ctx->last_d = A->d;
@@ -414,7 +440,8 @@ spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     out->pool_needed_bytes = words_needed(c, ctx->last_tt, ctx->last_S) * 8;
     if (ctx->timed) {
         cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
-        cudaEventElapsedTime(&out->ms_numeric, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&out->ms_pack, ctx->ev[1], ctx->ev[3]);
+        cudaEventElapsedTime(&out->ms_numeric, ctx->ev[3], ctx->ev[2]);
         cudaEventElapsedTime(&out->ms_total, ctx->ev[0], ctx->ev[2]);
     }
     spamm_status st = status_from_ctl(ctx, c);
@@ -477,6 +504,46 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
 
 static spamm_status status_of(spamm_ctx* ctx, const DevCtl& c) { return status_from_ctl(ctx, c); }
 
+static spamm_status ensure_aux(spamm_ctx* ctx) {
+    if (ctx->aux_ready) return SPAMM_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    int made = 0;
+    for (; made < spamm_ctx::kAux && e == cudaSuccess; ++made) {
+        e = cudaStreamCreateWithFlags(&ctx->aux[made], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&ctx->aux_ev[made], cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+        for (int i = 0; i < made; ++i) {
+            cudaStreamDestroy(ctx->aux[i]);
+            cudaEventDestroy(ctx->aux_ev[i]);
+        }
+        cudaEventDestroy(ctx->fork_ev);
+        return cuda_err(ctx, e, "side streams");
+    }
+    ctx->aux_ready = true;
+    return SPAMM_OK;
+}
+
+// Fork: every side stream waits for the work queued so far on ctx->stream.
+static cudaError_t fork_aux(spamm_ctx* ctx) {
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, ctx->stream);
+    for (int i = 0; i < spamm_ctx::kAux && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(ctx->aux[i], ctx->fork_ev, 0);
+    return e;
+}
+
+// Join: ctx->stream waits for everything queued on the side streams.
+static cudaError_t join_aux(spamm_ctx* ctx) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < spamm_ctx::kAux && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ctx->aux_ev[i], ctx->aux[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->aux_ev[i], 0);
+    }
+    return e;
+}
+
 static void note_shape(spamm_ctx* c, const spamm_tree* A, double tau) {
     c->last_batch = 0;
     c->last_d = A->d;
@@ -490,6 +557,32 @@ static void note_shape(spamm_ctx* c, const spamm_tree* A, double tau) {
     c->last_tt = tile_tier(A);
     c->last_S = 1 << (A->d - c->last_tt);
     c->last_status = SPAMM_OK;
+}
+
+spamm_status spamm_tree_rebuild_batched(spamm_ctx* ctx, int32_t count, spamm_tree* const* trees,
+                                        const float* const* A, const int64_t* lda) {
+    if (!ctx || count < 0 || (count > 0 && (!trees || !A || !lda)))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL argument");
+    if (count == 0) return SPAMM_OK;
+    for (int p = 0; p < count; ++p) {
+        spamm_tree* t = trees[p];
+        if (!t) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL tree");
+        const spamm_status st = check_matrix(ctx, A[p], t->n, lda[p]);
+        if (st != SPAMM_OK) return st;
+        if (t->precision != ctx->cfg.precision || t->b != ctx->cfg.leaf)
+            return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tree built under another configuration");
+    }
+    spamm_status st = ensure_aux(ctx);
+    if (st != SPAMM_OK) return st;
+    cudaError_t e = fork_aux(ctx);
+    for (int p = 0; p < count && e == cudaSuccess; ++p) {
+        spamm_tree* t = trees[p];
+        t->A = A[p];
+        t->lda = lda[p];
+        e = launch_build_norms(t, ctx->aux[p % spamm_ctx::kAux]);
+    }
+    if (e == cudaSuccess) e = join_aux(ctx);
+    return cuda_err(ctx, e, "batched norm build launch");
 }
 
 spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_tree* const* A,
@@ -518,10 +611,13 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
         if (st != SPAMM_OK) return set_err(ctx, st, "sub-context creation");
         ctx->subs.push_back(sub);
     }
+    spamm_status sta = ensure_aux(ctx);
+    if (sta != SPAMM_OK) return sta;
     for (int p = 0; p < count; ++p) {
         spamm_ctx* sub = ctx->subs[p];
-        sub->stream = ctx->stream;
-        const spamm_status st = ensure_tiles(sub, (int64_t)tile_rows(A[p]) * tile_cols(A[p]));
+        sub->stream = ctx->aux[p % spamm_ctx::kAux];
+        spamm_status st = ensure_tiles(sub, (int64_t)tile_rows(A[p]) * tile_cols(A[p]));
+        if (st == SPAMM_OK) st = ensure_need(sub, A[p]->nb);
         if (st != SPAMM_OK) return st;
         note_shape(sub, A[p], tau[p]);
     }
@@ -532,22 +628,27 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
         cudaStream_t s = ctx->stream;
         cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
+        // stages 2-3 and the packs of each product on a side stream
+        if (e == cudaSuccess) e = fork_aux(ctx);
         for (int p = 0; p < count && e == cudaSuccess; ++p) {
             spamm_ctx* sub = ctx->subs[p];
-            e = cudaMemsetAsync(sub->ctl, 0, sizeof(DevCtl), s);
+            e = cudaMemsetAsync(sub->ctl, 0, sizeof(DevCtl), sub->stream);
             if (e == cudaSuccess) e = launch_cull(sub, A[p], B[p], tau[p], sub->last_tt);
             if (e == cudaSuccess) e = launch_group(sub, A[p], B[p], tau[p], sub->last_tt);
+            if (e == cudaSuccess && precision_uses_tc(ctx->cfg.precision))
+                e = launch_packs(A[p], B[p], tau[p], ctx->cfg.tie_rel, sub->need, ctx->sm_count,
+                                 sub->stream);
+            // FP32 leaf products stay on the side stream, one launch per product
+            if (e == cudaSuccess && ctx->cfg.precision == SPAMM_PREC_FP32)
+                e = launch_leaf_simt(sub, A[p], B[p], alpha[p], beta[p], C[p], ldc[p]);
             jobs[p] = LeafJob{A[p], B[p], sub, alpha[p], beta[p], C[p], ldc[p]};
         }
+        if (e == cudaSuccess) e = join_aux(ctx);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
-        if (e == cudaSuccess) {
-            if (ctx->cfg.precision == SPAMM_PREC_FP32) {
-                for (int p = 0; p < count && e == cudaSuccess; ++p)
-                    e = launch_leaf_simt(ctx->subs[p], A[p], B[p], alpha[p], beta[p], C[p], ldc[p]);
-            } else {
-                e = launch_leaf_tc_jobs(ctx, jobs.data(), count);
-            }
-        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
+        // tensor-core leaf products of all products: one persistent launch
+        if (e == cudaSuccess && ctx->cfg.precision != SPAMM_PREC_FP32)
+            e = launch_leaf_tc_jobs(ctx, jobs.data(), count);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2], s);
         for (int p = 0; p < count && e == cudaSuccess; ++p)
             e = cudaMemcpyAsync(ctx->subs[p]->ctl_host, ctx->subs[p]->ctl, sizeof(DevCtl),
@@ -613,7 +714,8 @@ static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     out->precision = ctx->cfg.precision;
     if (ctx->timed) {
         cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
-        cudaEventElapsedTime(&out->ms_numeric, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&out->ms_pack, ctx->ev[1], ctx->ev[3]);
+        cudaEventElapsedTime(&out->ms_numeric, ctx->ev[3], ctx->ev[2]);
         cudaEventElapsedTime(&out->ms_total, ctx->ev[0], ctx->ev[2]);
     }
     if (ctx->last_status != SPAMM_OK && worst == SPAMM_OK) worst = (spamm_status)ctx->last_status;

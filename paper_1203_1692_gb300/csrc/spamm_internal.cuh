@@ -140,6 +140,9 @@ struct spamm_ctx {
     uint32_t* tile_steps; // (tile, K) steps per tile
     uint32_t* work_ctr;   // persistent-kernel work counter
     int64_t tiles_cap;
+    // per-K norm maxima for the packs of a multiply (2 x leaves per side)
+    double* need;
+    int64_t need_cap;
     // timing
     cudaEvent_t ev[4];
     bool timed;
@@ -157,6 +160,14 @@ struct spamm_ctx {
     // per product, created on demand and reused
     std::vector<spamm_ctx*> subs;
     int last_batch;  // products in the last multiply (0: a plain multiply)
+    // side streams for the per-product stages of batched calls (fork from
+    // and join back into `stream`; inside a graph capture they become
+    // parallel branches)
+    static constexpr int kAux = 8;
+    cudaStream_t aux[kAux];
+    cudaEvent_t aux_ev[kAux];
+    cudaEvent_t fork_ev;
+    bool aux_ready;
     std::string err;
 };
 
@@ -181,6 +192,11 @@ cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B
                         int tt);
 cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
                          int tt);
+
+// Tensor-core packs of the leaves that can take part in a kept product of
+// A x B at tau (norms.cu); scratch holds 2 x (leaves per side) doubles.
+cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, double rel,
+                         double* scratch, int sm_count, cudaStream_t s);
 
 // leaf_simt.cu
 cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,

@@ -157,3 +157,16 @@ def test_batched_rejects_bad_arguments():
     with pytest.raises(P.SpammError):
         ctx.multiply_batched([ta], [ta], [-1.0])
     ctx.multiply_batched([], [], [])    # empty batch: nothing to do
+
+
+def test_rebuild_batched_matches_single_builds():
+    """spamm_tree_rebuild_batched gives every tree the norms a fresh
+    spamm_build_norms gives (Sec. II.A), bit for bit."""
+    import paper_1203_1692_gb300 as P
+    ctx = P.Context(leaf=32, precision="bf16x3")
+    mats = [torch.from_numpy(gen.exp_decay(n, 0.88, seed=40 + n)).cuda()
+            for n in (100, 640, 1000, 1333, 64, 2048, 700, 900, 515)]
+    trees = [ctx.build_norms(torch.zeros_like(A)) for A in mats]
+    ctx.rebuild_batched(trees, mats)
+    for t, A in zip(trees, mats):
+        assert np.array_equal(t.norms(), ctx.build_norms(A).norms())

@@ -68,6 +68,26 @@ def test_norm_pyramid_matches_oracle(n, b, lda):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("b", [16, 32, 64, 128])
+def test_norms_of_wide_range_and_subnormal_entries(b):
+    """Leaf squares are exact and their sums stay within 1e-12 of FP64
+    whatever the magnitudes: entries spread over 1e-40 .. 1e30, a block of
+    subnormals, a block near FP32's largest values, exact zeros."""
+    n = 300
+    rng = np.random.default_rng(b)
+    A = gen.uniform_dense(n, seed=b, symmetric=False).astype(np.float64)
+    A *= 10.0 ** rng.uniform(-40, 30, size=(n, n))
+    A[:40, :40] = gen.uniform_dense(40, seed=1).astype(np.float64) * 1e-42
+    A[100:140, 200:240] = gen.uniform_dense(40, seed=2).astype(np.float64) * 1e18
+    A[250:, :50] = 0.0
+    A = A.astype(np.float32)
+    ctx = _spamm().Context(leaf=b)
+    got = ctx.build_norms(_dev(A)).norms()
+    ref = O.pyramid(A, b)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+    assert np.array_equal(got == 0, ref == 0)
+
+
 # ---------------------------------------------------- triples and C, FP32
 
 CASES = [  # n, b, generator, tau

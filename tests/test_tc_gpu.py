@@ -118,3 +118,31 @@ def test_tc_water_like_n7500_sampled(prec):
     ref, _ = O.blocks(A, A, b, tau, ij, pa, pa)
     got = blocks_from(C, ij, b, n)
     assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 32), ("tf32x3", 64)])
+def test_tc_stale_pieces_never_reach_C(prec, b):
+    """A multiply packs only the leaves that can take part in a kept product
+    (Sec. III culling is monotone in each norm).  Pieces it does not pack
+    keep whatever an earlier multiply left there; here that is a matrix of
+    1e15s packed in full at tau = 0, and none of it may leak into C."""
+    import paper_1203_1692_gb300 as P
+    n = 700
+    ctx = P.Context(leaf=b, precision=prec)
+    big = torch.full((n, n), 1e15, dtype=torch.float32, device="cuda")
+    tree = ctx.build_norms(big)
+    C = torch.empty_like(big)
+    ctx.multiply(tree, tree, 0.0, C=C)
+    A = _matrix("exp", n)
+    dA = torch.from_numpy(A).cuda()
+    tree.rebuild(dA)
+    for tau in (1e-2, 1e-5):
+        ctx.multiply(tree, tree, tau, C=C)
+        ref = O.multiply(A, A, b, tau)
+        assert rel_max_err(C.cpu().numpy(), ref.C) <= TOL[prec]
+    # another right operand through the same left tree
+    Bm = gen.exp_decay_nonsym(n, 0.85, seed=9)
+    tb = ctx.build_norms(torch.from_numpy(Bm).cuda())
+    ctx.multiply(tree, tb, 1e-4, C=C)
+    ref = O.multiply(A, Bm, b, 1e-4)
+    assert rel_max_err(C.cpu().numpy(), ref.C) <= TOL[prec]
