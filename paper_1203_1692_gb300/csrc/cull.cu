@@ -25,16 +25,71 @@
 // column leaf y of each half), compacted into a coalesced list in ascending
 // K.  This is the leaf-triple list in tile-compressed form; the leaf kernels
 // walk it, which fixes the accumulation order of every C block.
+//
+// Batches.  Every kernel takes a table of products (one for spamm_multiply,
+// up to 64 for spamm_multiply_batched) and a flattened grid: product p owns
+// the blocks [bbase[p], bbase[p+1]) and works through them as its own grid.
+// A batch therefore runs each tier, each grouping step and the tile cull of
+// all its products in one launch each, with the blocks of a product sized
+// to its share of the work.
 #include <algorithm>
+#include <vector>
 
 #include "spamm_internal.cuh"
 
 namespace spamm {
 
-__global__ void k_cull_root(const double* __restrict__ pa, const double* __restrict__ pb,
-                            Thresh th, DevCtl* ctl, uint64_t* __restrict__ pool) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double na = pa[0], nb = pb[0];
+// One product of a symbolic launch.
+struct CullProd {
+    const double* pyrA;
+    const double* pyrB;
+    Thresh th;
+    DevCtl* ctl;
+    uint64_t* pool;
+    unsigned long long cap;    // pool words
+    uint32_t* tile_cnt;
+    uint32_t* tile_fill;
+    uint32_t* tile_off;
+    uint32_t* tile_steps;
+    int tt, tc, tiles, S;
+};
+
+constexpr int kCullBatch = 64;
+
+// Passed by value (the table travels with the launch, also into a graph).
+template <int NB>
+struct CullBatch {
+    CullProd p[NB];
+    int bbase[NB + 1];  // first block of each product in the flattened grid
+    int count;
+};
+
+template <int NB>
+__device__ __forceinline__ int product_of_block(const CullBatch<NB>& cb, int b) {
+    int lo = 0, hi = cb.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cb.bbase[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// This block's product q, its block index vb and block count vg within it.
+#define CULL_RESOLVE(cb)                                       \
+    const int pi_ = product_of_block(cb, (int)blockIdx.x);     \
+    const CullProd& q = cb.p[pi_];                             \
+    const int vb = (int)blockIdx.x - cb.bbase[pi_];            \
+    const int vg = cb.bbase[pi_ + 1] - cb.bbase[pi_]
+
+template <int NB>
+__global__ void k_cull_root(CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    (void)vb;
+    (void)vg;
+    if (threadIdx.x != 0) return;
+    DevCtl* ctl = q.ctl;
+    const double na = q.pyrA[0], nb = q.pyrB[0];
     ctl->tier_off[0] = 0;
     ctl->tier_cand[0] = 1;
     if (!isfinite(na) || !isfinite(nb)) {
@@ -44,31 +99,36 @@ __global__ void k_cull_root(const double* __restrict__ pa, const double* __restr
         return;
     }
     bool tie;
-    const bool keep = spamm_keep(na, nb, th, &tie);
+    const bool keep = spamm_keep(na, nb, q.th, &tie);
     if (tie) ctl->tie_band += 1;
     ctl->tier_count[0] = keep ? 1 : 0;
-    if (keep) pool[0] = pack_triple(0, 0, 0);
+    if (keep) q.pool[0] = pack_triple(0, 0, 0);
 }
 
-// Expand tier t into tier t + 1.  na/nb are the tier-(t+1) norm grids.
-__global__ void __launch_bounds__(256) k_cull_tier(int t, const double* __restrict__ na,
-                                                   const double* __restrict__ nb, Thresh th,
-                                                   DevCtl* ctl,
-                                                   uint64_t* __restrict__ pool,
-                                                   unsigned long long cap) {
+// Expand tier t into tier t + 1 (the tier-(t+1) norm grids of both trees).
+template <int NB>
+__global__ void __launch_bounds__(256) k_cull_tier(int t, CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    DevCtl* ctl = q.ctl;
+    uint64_t* __restrict__ pool = q.pool;
+    const unsigned long long cap = q.cap;
+    const int64_t off_t = (((int64_t)1 << (2 * (t + 1))) - 1) / 3;
+    const double* __restrict__ na = q.pyrA + off_t;
+    const double* __restrict__ nb = q.pyrB + off_t;
+    const Thresh th = q.th;
     const unsigned long long in_off = ctl->tier_off[t];
     const unsigned long long in_cnt = stored_count(ctl, t, cap);
     const unsigned long long out_off = in_off + in_cnt;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (vb == 0 && threadIdx.x == 0) {
         ctl->tier_off[t + 1] = out_off;
         ctl->tier_cand[t + 1] = in_cnt * 8;
     }
     const int64_t w = (int64_t)1 << (t + 1);
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long total = in_cnt * 8;
-    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long warps = (unsigned long long)vg * (blockDim.x >> 5);
     unsigned long long tie = 0;
-    for (unsigned long long base = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) +
+    for (unsigned long long base = ((unsigned long long)vb * (blockDim.x >> 5) +
                                     (threadIdx.x >> 5)) * 32;
          base < total; base += warps * 32) {
         const unsigned long long g = base + lane;
@@ -76,10 +136,10 @@ __global__ void __launch_bounds__(256) k_cull_tier(int t, const double* __restri
         uint64_t child = 0;
         if (g < total) {
             const uint64_t par = pool[in_off + (g >> 3)];
-            const unsigned q = (unsigned)(g & 7);
-            const uint64_t i = 2ull * tri_I(par) + ((q >> 2) & 1);
-            const uint64_t k = 2ull * tri_K(par) + ((q >> 1) & 1);
-            const uint64_t j = 2ull * tri_J(par) + (q & 1);
+            const unsigned qd = (unsigned)(g & 7);
+            const uint64_t i = 2ull * tri_I(par) + ((qd >> 2) & 1);
+            const uint64_t k = 2ull * tri_K(par) + ((qd >> 1) & 1);
+            const uint64_t j = 2ull * tri_J(par) + (qd & 1);
             bool tb;
             keep = spamm_keep(na[i * w + k], nb[k * w + j], th, &tb);
             tie += tb ? 1 : 0;
@@ -96,41 +156,19 @@ __global__ void __launch_bounds__(256) k_cull_tier(int t, const double* __restri
             if (pos < cap) pool[pos] = child;
         }
     }
-    // tie-band count and overflow flag
-    for (int off = 16; off > 0; off >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, off);
+    // tie-band count
+    for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
     if (lane == 0 && tie) atomicAdd(&ctl->tie_band, tie);
 }
 
-__global__ void k_cull_finish(int tt, DevCtl* ctl, unsigned long long cap) {
-    if (threadIdx.x || blockIdx.x) return;
-    for (int t = 0; t <= tt; ++t)
-        if (ctl->tier_off[t] + ctl->tier_count[t] > cap) ctl->status |= ST_OVERFLOW;
-}
-
-cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
-                        int tt) {
-    cudaStream_t s = ctx->stream;
-    const Thresh th = make_thresh(tau, ctx->cfg.tie_rel);
-    const unsigned long long cap = (unsigned long long)ctx->pool_words;
-    k_cull_root<<<1, 32, 0, s>>>(A->pyr, B->pyr, th, ctx->ctl, ctx->pool);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int blocks = ctx->sm_count * 4;
-    for (int t = 0; t < tt; ++t) {
-        const int64_t off = (((int64_t)1 << (2 * (t + 1))) - 1) / 3;
-        // Tier t + 1 has at most 8^(t+1) candidates: size small tiers' grids to them.
-        int g = blocks;
-        if (t + 1 < 7) {
-            const int64_t cand = (int64_t)1 << (3 * (t + 1));
-            g = (int)std::min<int64_t>(blocks, (cand + 255) / 256);
-        }
-        k_cull_tier<<<g, 256, 0, s>>>(t, A->pyr + off, B->pyr + off, th, ctx->ctl, ctx->pool,
-                                      cap);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    k_cull_finish<<<1, 32, 0, s>>>(tt, ctx->ctl, cap);
-    return cudaGetLastError();
+template <int NB>
+__global__ void k_cull_finish(CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    (void)vb;
+    (void)vg;
+    if (threadIdx.x) return;
+    for (int t = 0; t <= q.tt; ++t)
+        if (q.ctl->tier_off[t] + q.ctl->tier_count[t] > q.cap) q.ctl->status |= ST_OVERFLOW;
 }
 
 // ------------------------------------------------------------- grouping
@@ -139,26 +177,43 @@ __device__ inline uint32_t tile_of(uint64_t tri, int tc) {
     return tri_I(tri) * (uint32_t)tc + (tri_J(tri) >> 1);
 }
 
-__global__ void __launch_bounds__(256) k_group_count(int tt, DevCtl* ctl,
-                                                     const uint64_t* __restrict__ pool, int tc,
-                                                     uint32_t* __restrict__ tile_cnt) {
-    if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
-    const unsigned long long off = ctl->tier_off[tt];
-    const unsigned long long m = ctl->tier_count[tt];
-    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < m;
-         g += (unsigned long long)gridDim.x * blockDim.x)
-        atomicAdd(&tile_cnt[tile_of(pool[off + g], tc)], 1u);
+template <int NB>
+__global__ void __launch_bounds__(256) k_group_zero(CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < q.tiles;
+         i += (int64_t)vg * blockDim.x) {
+        q.tile_cnt[i] = 0u;
+        q.tile_fill[i] = 0u;
+    }
 }
 
-// Exclusive scan of the tile counts (single block), and the pool layout of
-// the grouped arrays behind the tier-tt frontier: entries (u32, one per
-// tier-tt triple), then step K (u32) and step masks (2 x u64), S per entry.
-__global__ void __launch_bounds__(1024) k_group_scan(int tt, int S, DevCtl* ctl,
-                                                     unsigned long long cap,
-                                                     const uint32_t* __restrict__ cnt,
-                                                     uint32_t* __restrict__ off, int tiles) {
+template <int NB>
+__global__ void __launch_bounds__(256) k_group_count(CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    DevCtl* ctl = q.ctl;
+    if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
+    const unsigned long long off = ctl->tier_off[q.tt];
+    const unsigned long long m = ctl->tier_count[q.tt];
+    for (unsigned long long g = (unsigned long long)vb * blockDim.x + threadIdx.x; g < m;
+         g += (unsigned long long)vg * blockDim.x)
+        atomicAdd(&q.tile_cnt[tile_of(q.pool[off + g], q.tc)], 1u);
+}
+
+// Exclusive scan of the tile counts (one block per product), and the pool
+// layout of the grouped arrays behind the tier-tt frontier: entries (u32, one
+// per tier-tt triple), then step K (u32) and step masks (2 x u64), S per
+// entry.
+template <int NB>
+__global__ void __launch_bounds__(1024) k_group_scan(CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    (void)vb;
+    (void)vg;
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t carry;
+    DevCtl* ctl = q.ctl;
+    const uint32_t* __restrict__ cnt = q.tile_cnt;
+    uint32_t* __restrict__ off = q.tile_off;
+    const int tiles = q.tiles;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -189,31 +244,31 @@ __global__ void __launch_bounds__(1024) k_group_scan(int tt, int S, DevCtl* ctl,
     }
     if (threadIdx.x == 0) {
         off[tiles] = carry;
-        const unsigned long long m = ctl->tier_count[tt];
-        const unsigned long long end = ctl->tier_off[tt] + m;
-        const unsigned long long ms = m * (unsigned long long)S;
+        const unsigned long long m = ctl->tier_count[q.tt];
+        const unsigned long long end = ctl->tier_off[q.tt] + m;
+        const unsigned long long ms = m * (unsigned long long)q.S;
         ctl->ent_off = end;
         ctl->pk_off = end + (m + 1) / 2;
         ctl->pm_off = ctl->pk_off + (ms + 1) / 2;
         ctl->need_words = ctl->pm_off + 2 * ms;
-        if (ctl->need_words > cap || m >= 0xffffffffull / (unsigned long long)S)
+        if (ctl->need_words > q.cap || m >= 0xffffffffull / (unsigned long long)q.S)
             ctl->status |= ST_OVERFLOW;
     }
 }
 
-__global__ void __launch_bounds__(256) k_group_scatter(int tt, DevCtl* ctl,
-                                                       uint64_t* __restrict__ pool, int tc,
-                                                       const uint32_t* __restrict__ off,
-                                                       uint32_t* __restrict__ fill) {
+template <int NB>
+__global__ void __launch_bounds__(256) k_group_scatter(CullBatch<NB> cb) {
+    CULL_RESOLVE(cb);
+    DevCtl* ctl = q.ctl;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
-    const unsigned long long loff = ctl->tier_off[tt];
-    const unsigned long long m = ctl->tier_count[tt];
-    uint32_t* ent = reinterpret_cast<uint32_t*>(pool + ctl->ent_off);
-    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < m;
-         g += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint64_t tri = pool[loff + g];
-        const uint32_t u = tile_of(tri, tc);
-        ent[off[u] + atomicAdd(&fill[u], 1u)] = (tri_K(tri) << 1) | (tri_J(tri) & 1u);
+    const unsigned long long loff = ctl->tier_off[q.tt];
+    const unsigned long long m = ctl->tier_count[q.tt];
+    uint32_t* ent = reinterpret_cast<uint32_t*>(q.pool + ctl->ent_off);
+    for (unsigned long long g = (unsigned long long)vb * blockDim.x + threadIdx.x; g < m;
+         g += (unsigned long long)vg * blockDim.x) {
+        const uint64_t tri = q.pool[loff + g];
+        const uint32_t u = tile_of(tri, q.tc);
+        ent[q.tile_off[u] + atomicAdd(&q.tile_fill[u], 1u)] = (tri_K(tri) << 1) | (tri_J(tri) & 1u);
     }
 }
 
@@ -258,12 +313,8 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 // of K values are then compacted in ascending K.
 constexpr int kCullWarps = 8;
 
-template <int DS>
-__global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(int tt, const double* __restrict__ pyrA,
-                                                   const double* __restrict__ pyrB, Thresh th,
-                                                   DevCtl* ctl, uint64_t* __restrict__ pool,
-                                                   const uint32_t* __restrict__ off,
-                                                   uint32_t* __restrict__ steps, int tc) {
+template <int DS, int NB>
+__global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> cb) {
     constexpr int S = 1 << DS;               // K leaves per tier-tt K'
     constexpr int WIN = 1024;                // steps per window (16 KB of masks)
     constexpr int KPW = WIN / S;             // K' per window
@@ -273,8 +324,17 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(int tt, const 
     __shared__ double nA[kCullWarps][84], nB[kCullWarps][84];
     __shared__ uint32_t warp_sums[16], total_s;
     __shared__ unsigned long long st_cand[4], st_kept[4], st_tie;
+    CULL_RESOLVE(cb);
+    const int tt = q.tt, tc = q.tc;
+    const double* __restrict__ pyrA = q.pyrA;
+    const double* __restrict__ pyrB = q.pyrB;
+    const Thresh th = q.th;
+    DevCtl* ctl = q.ctl;
+    uint64_t* __restrict__ pool = q.pool;
+    const uint32_t* __restrict__ off = q.tile_off;
+    uint32_t* __restrict__ steps = q.tile_steps;
     if (ctl->status & (ST_OVERFLOW | ST_NONFINITE)) return;
-    const uint32_t u = blockIdx.x;
+    const uint32_t u = (uint32_t)vb;
     const uint32_t e0 = off[u], e1 = off[u + 1];
     if (e0 == e1) {
         if (threadIdx.x == 0) steps[u] = 0;
@@ -451,43 +511,223 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(int tt, const 
     }
 }
 
+// ------------------------------------------------------------- launches
+
+// Blocks of product p for a grid-stride kernel: its share (by leaf count) of
+// `total`, at least one and at most `cap_blocks`.
+static void share_blocks(const std::vector<double>& weight, int total, int64_t cap_blocks,
+                         std::vector<int>& out) {
+    double sum = 0.0;
+    for (double w : weight) sum += w;
+    out.resize(weight.size());
+    for (size_t p = 0; p < weight.size(); ++p) {
+        int64_t g = (int64_t)(total * (weight[p] / sum)) + 1;
+        g = std::min<int64_t>(g, cap_blocks);
+        out[p] = (int)std::max<int64_t>(g, 1);
+    }
+}
+
+template <int NB>
+static int set_bases(CullBatch<NB>& cb, const std::vector<int>& blocks) {
+    int b = 0;
+    for (int p = 0; p < cb.count; ++p) {
+        cb.bbase[p] = b;
+        b += blocks[p];
+    }
+    cb.bbase[cb.count] = b;
+    return b;
+}
+
+// Stage 2 for up to NB products: root, one launch per tier, overflow check.
+template <int NB>
+static cudaError_t cull_stage(const CullProd* prods, const std::vector<double>& weight, int count,
+                              int sm_count, cudaStream_t s) {
+    CullBatch<NB> cb;
+    memset(&cb, 0, sizeof(cb));
+    cb.count = count;
+    int maxtt = 0;
+    for (int p = 0; p < count; ++p) {
+        cb.p[p] = prods[p];
+        maxtt = std::max(maxtt, prods[p].tt);
+    }
+    std::vector<int> blocks(count, 1);
+    int nb = set_bases(cb, blocks);
+    k_cull_root<NB><<<nb, 32, 0, s>>>(cb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int full = sm_count * 4;
+    for (int t = 0; t < maxtt; ++t) {
+        // tier t + 1 has at most 8^(t+1) candidates: small tiers get small grids
+        const int64_t cand_blocks = t + 1 < 7 ? (((int64_t)1 << (3 * (t + 1))) + 255) / 256 : full;
+        share_blocks(weight, full, std::min<int64_t>(full, cand_blocks), blocks);
+        // a product whose tiles sit above this tier takes no blocks; keep
+        // the flattened grid free of them by moving them to the end
+        CullBatch<NB> ct;
+        memset(&ct, 0, sizeof(ct));
+        std::vector<int> bl;
+        for (int p = 0; p < count; ++p)
+            if (t < prods[p].tt) {
+                ct.p[ct.count++] = prods[p];
+                bl.push_back(blocks[p]);
+            }
+        if (ct.count == 0) continue;
+        nb = set_bases(ct, bl);
+        k_cull_tier<NB><<<nb, 256, 0, s>>>(t, ct);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    std::fill(blocks.begin(), blocks.end(), 1);
+    nb = set_bases(cb, blocks);
+    k_cull_finish<NB><<<nb, 32, 0, s>>>(cb);
+    return cudaGetLastError();
+}
+
+// Stage 3 for up to NB products: tile counts, scan, scatter, tile cull.
+template <int NB>
+static cudaError_t group_stage(const CullProd* prods, const std::vector<double>& weight, int count,
+                               int sm_count, cudaStream_t s) {
+    CullBatch<NB> cb;
+    memset(&cb, 0, sizeof(cb));
+    cb.count = count;
+    for (int p = 0; p < count; ++p) cb.p[p] = prods[p];
+    const int full = sm_count * 4;
+    std::vector<int> blocks;
+    for (int p = 0; p < count; ++p) blocks.push_back(std::max(1, std::min(64, (prods[p].tiles + 255) / 256)));
+    int nb = set_bases(cb, blocks);
+    k_group_zero<NB><<<nb, 256, 0, s>>>(cb);
+    share_blocks(weight, full, full, blocks);
+    nb = set_bases(cb, blocks);
+    k_group_count<NB><<<nb, 256, 0, s>>>(cb);
+    std::vector<int> ones(count, 1);
+    const int nb1 = set_bases(cb, ones);
+    k_group_scan<NB><<<nb1, 1024, 0, s>>>(cb);
+    nb = set_bases(cb, blocks);
+    k_group_scatter<NB><<<nb, 256, 0, s>>>(cb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // tile cull, one launch per depth below the tile nodes (DS = d - tt)
+    for (int ds = 0; ds <= 3; ++ds) {
+        CullBatch<NB> ct;
+        memset(&ct, 0, sizeof(ct));
+        std::vector<int> bl;
+        size_t dsm = 0;
+        for (int p = 0; p < count; ++p) {
+            const int pds = prods[p].S == 1 ? 0 : prods[p].S == 2 ? 1 : prods[p].S == 4 ? 2 : 3;
+            if (pds != ds) continue;
+            ct.p[ct.count++] = prods[p];
+            bl.push_back(prods[p].tiles);
+            const int words = ((1 << prods[p].tt) + 31) / 32;
+            dsm = std::max(dsm, sizeof(uint32_t) * (2 * words + ((size_t)1 << prods[p].tt)));
+        }
+        if (ct.count == 0) continue;
+        nb = set_bases(ct, bl);
+        if (nb == 0) continue;
+#define SPAMM_TC(DSV)                                                                         \
+    do {                                                                                      \
+        cudaFuncSetAttribute(k_tile_cull<DSV, NB>,                                            \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);          \
+        cudaFuncSetAttribute(k_tile_cull<DSV, NB>,                                            \
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);            \
+        k_tile_cull<DSV, NB><<<nb, kCullWarps * 32, dsm, s>>>(ct);                            \
+    } while (0)
+        switch (ds) {
+            case 0: SPAMM_TC(0); break;
+            case 1: SPAMM_TC(1); break;
+            case 2: SPAMM_TC(2); break;
+            default: SPAMM_TC(3); break;
+        }
+#undef SPAMM_TC
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static CullProd make_prod(spamm_ctx* c, const spamm_tree* A, const spamm_tree* B, double tau,
+                          double rel, int tt) {
+    CullProd q;
+    q.pyrA = A->pyr;
+    q.pyrB = B->pyr;
+    q.th = make_thresh(tau, rel);
+    q.ctl = c->ctl;
+    q.pool = c->pool;
+    q.cap = (unsigned long long)c->pool_words;
+    q.tile_cnt = c->tile_cnt;
+    q.tile_fill = c->tile_fill;
+    q.tile_off = c->tile_off;
+    q.tile_steps = c->tile_steps;
+    q.tt = tt;
+    q.tc = tile_cols(A);
+    q.tiles = tile_rows(A) * q.tc;
+    q.S = 1 << (A->d - tt);
+    return q;
+}
+
+cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
+                        int tt) {
+    const CullProd q = make_prod(ctx, A, B, tau, ctx->cfg.tie_rel, tt);
+    return cull_stage<1>(&q, std::vector<double>(1, 1.0), 1, ctx->sm_count, ctx->stream);
+}
+
 cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
                          int tt) {
-    cudaStream_t s = ctx->stream;
-    const int tc = tile_cols(A);
-    const int tiles = tile_rows(A) * tc;
-    const int ds = A->d - tt;
-    const int S = 1 << ds;
-    const unsigned long long cap = (unsigned long long)ctx->pool_words;
-    const Thresh th = make_thresh(tau, ctx->cfg.tie_rel);
-    cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(uint32_t) * tiles, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tile_fill, 0, sizeof(uint32_t) * tiles, s);
-    if (e != cudaSuccess) return e;
-    const int blocks = ctx->sm_count * 4;
-    k_group_count<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tc, ctx->tile_cnt);
-    k_group_scan<<<1, 1024, 0, s>>>(tt, S, ctx->ctl, cap, ctx->tile_cnt, ctx->tile_off, tiles);
-    k_group_scatter<<<blocks, 256, 0, s>>>(tt, ctx->ctl, ctx->pool, tc, ctx->tile_off,
-                                           ctx->tile_fill);
-    const int words = ((1 << tt) + 31) / 32;
-    const size_t dsm = sizeof(uint32_t) * (2 * words + ((size_t)1 << tt));
-#define SPAMM_TC(DSV)                                                                          \
-    do {                                                                                       \
-        cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                             (int)dsm);                                                        \
-        cudaFuncSetAttribute(k_tile_cull<DSV>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
-                             100);                                                             \
-        k_tile_cull<DSV><<<tiles, kCullWarps * 32, dsm, s>>>(tt, A->pyr, B->pyr, th, ctx->ctl,             \
-                                                 ctx->pool, ctx->tile_off, ctx->tile_steps,    \
-                                                 tc);                                          \
-    } while (0)
-    switch (ds) {
-        case 0: SPAMM_TC(0); break;
-        case 1: SPAMM_TC(1); break;
-        case 2: SPAMM_TC(2); break;
-        default: SPAMM_TC(3); break;
+    const CullProd q = make_prod(ctx, A, B, tau, ctx->cfg.tie_rel, tt);
+    return group_stage<1>(&q, std::vector<double>(1, 1.0), 1, ctx->sm_count, ctx->stream);
+}
+
+// Stages 2-3 of `count` products, product p in sub-context subs[p] (its
+// pool, control block and tile arrays, tile tier subs[p]->last_tt), on
+// `stream`, up to kCullBatch products per launch.
+cudaError_t launch_symbolic_batched(spamm_ctx* ctx, spamm_ctx* const* subs,
+                                    const spamm_tree* const* A, const spamm_tree* const* B,
+                                    const double* tau, int count, cudaStream_t stream) {
+    for (int c0 = 0; c0 < count; c0 += kCullBatch) {
+        const int cnt = std::min(kCullBatch, count - c0);
+        std::vector<CullProd> prods;
+        std::vector<double> weight;
+        for (int i = 0; i < cnt; ++i) {
+            const int p = c0 + i;
+            prods.push_back(make_prod(subs[p], A[p], B[p], tau[p], ctx->cfg.tie_rel, subs[p]->last_tt));
+            weight.push_back((double)A[p]->nl * (double)A[p]->nl);
+        }
+        cudaError_t e = cull_stage<kCullBatch>(prods.data(), weight, cnt, ctx->sm_count, stream);
+        if (e == cudaSuccess)
+            e = group_stage<kCullBatch>(prods.data(), weight, cnt, ctx->sm_count, stream);
+        if (e != cudaSuccess) return e;
     }
-#undef SPAMM_TC
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+
+// Control blocks of a batch: zero them (out == nullptr) or gather them into
+// one array (out[p] = *ctl[p]) so that a single copy brings them to the host.
+struct CtlTable {
+    DevCtl* ctl[kCullBatch];
+};
+
+__global__ void k_ctl_batch(CtlTable tb, int count, DevCtl* __restrict__ out) {
+    constexpr int W = sizeof(DevCtl) / sizeof(unsigned long long);
+    static_assert(sizeof(DevCtl) % sizeof(unsigned long long) == 0, "");
+    const int p = blockIdx.x;
+    if (p >= count) return;
+    unsigned long long* src = reinterpret_cast<unsigned long long*>(tb.ctl[p]);
+    unsigned long long* dst = out ? reinterpret_cast<unsigned long long*>(out + p) : nullptr;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        if (dst) dst[w] = src[w];
+        else src[w] = 0ull;
+    }
+}
+
+cudaError_t launch_ctl_batch(spamm_ctx* const* subs, int count, DevCtl* out, cudaStream_t s) {
+    for (int c0 = 0; c0 < count; c0 += kCullBatch) {
+        const int cnt = std::min(kCullBatch, count - c0);
+        CtlTable tb;
+        memset(&tb, 0, sizeof(tb));
+        for (int i = 0; i < cnt; ++i) tb.ctl[i] = subs[c0 + i]->ctl;
+        k_ctl_batch<<<cnt, 128, 0, s>>>(tb, cnt, out ? out + c0 : nullptr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace spamm

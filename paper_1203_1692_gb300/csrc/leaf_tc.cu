@@ -557,6 +557,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const TcProd& q = bt.prods[pi];
             const int u = tile_at(k - q.base, q.tr, q.tc);
             const uint32_t nch = chunks_of(q.steps[u] * CHUNKS);
+            if (nch == 0) {
+                // no kept product: C = alpha * 0 + beta * C, written row-wise by
+                // the 256 epilogue threads (a warp stores 512 contiguous bytes)
+                float* const Cp = q.C;
+                const int64_t ldc = q.ldc, n = q.n;
+                const float alpha = q.alpha, beta = q.beta;
+                const int64_t R0 = (int64_t)(u / q.tc) * 128, C0 = (int64_t)(u % q.tc) * 256;
+                const int e = (warp - 2) * 32 + lane;
+                const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(Cp) & 15) == 0);
+                const float z = alpha * 0.f;
+                for (int idx = e; idx < 128 * 64; idx += kEpiWarps * 32) {
+                    const int64_t row = R0 + idx / 64, col = C0 + 4 * (idx % 64);
+                    if (row >= n || col >= n) continue;
+                    float* dst = Cp + row * ldc + col;
+                    if (vec && col + 3 < n) {
+                        float4 o = make_float4(z, z, z, z);
+                        if (beta != 0.f) {
+                            const float4 old = *reinterpret_cast<const float4*>(dst);
+                            o.x = fmaf(beta, old.x, z);
+                            o.y = fmaf(beta, old.y, z);
+                            o.z = fmaf(beta, old.z, z);
+                            o.w = fmaf(beta, old.w, z);
+                        }
+                        *reinterpret_cast<float4*>(dst) = o;
+                    } else {
+                        for (int c = 0; c < 4 && col + c < n; ++c)
+                            dst[c] = beta != 0.f ? fmaf(beta, dst[c], z) : z;
+                    }
+                }
+                continue;
+            }
             float master[128];
 #pragma unroll
             for (int v = 0; v < 128; ++v) master[v] = 0.f;

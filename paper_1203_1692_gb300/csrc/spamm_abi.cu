@@ -198,6 +198,8 @@ spamm_status spamm_destroy(spamm_ctx* ctx) {
     cudaFree(ctx->dC);
     for (int i = 0; i < 4; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    cudaFree(ctx->bctl);
+    if (ctx->bctl_host) cudaFreeHost(ctx->bctl_host);
     if (ctx->aux_ready) {
         for (int i = 0; i < spamm_ctx::kAux; ++i) {
             cudaStreamSynchronize(ctx->aux[i]);
@@ -612,6 +614,18 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
         ctx->subs.push_back(sub);
     }
     spamm_status sta = ensure_aux(ctx);
+    if (sta == SPAMM_OK && ctx->bctl_cap < count) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->bctl);
+        if (ctx->bctl_host) cudaFreeHost(ctx->bctl_host);
+        ctx->bctl = nullptr;
+        ctx->bctl_host = nullptr;
+        ctx->bctl_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->bctl, sizeof(DevCtl) * (size_t)count);
+        if (e == cudaSuccess) e = cudaMallocHost(&ctx->bctl_host, sizeof(DevCtl) * (size_t)count);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "batch control blocks");
+        ctx->bctl_cap = count;
+    }
     if (sta != SPAMM_OK) return sta;
     for (int p = 0; p < count; ++p) {
         spamm_ctx* sub = ctx->subs[p];
@@ -624,34 +638,45 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
     ctx->last_batch = count;
     ctx->last_status = SPAMM_OK;
     std::vector<LeafJob> jobs((size_t)count);
+    for (int p = 0; p < count; ++p)
+        jobs[p] = LeafJob{A[p], B[p], ctx->subs[p], alpha[p], beta[p], C[p], ldc[p]};
+    const bool tc = precision_uses_tc(ctx->cfg.precision);
     for (int attempt = 0;; ++attempt) {
         cudaStream_t s = ctx->stream;
         cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
-        // stages 2-3 and the packs of each product on a side stream
-        if (e == cudaSuccess) e = fork_aux(ctx);
-        for (int p = 0; p < count && e == cudaSuccess; ++p) {
-            spamm_ctx* sub = ctx->subs[p];
-            e = cudaMemsetAsync(sub->ctl, 0, sizeof(DevCtl), sub->stream);
-            if (e == cudaSuccess) e = launch_cull(sub, A[p], B[p], tau[p], sub->last_tt);
-            if (e == cudaSuccess) e = launch_group(sub, A[p], B[p], tau[p], sub->last_tt);
-            if (e == cudaSuccess && precision_uses_tc(ctx->cfg.precision))
-                e = launch_packs(A[p], B[p], tau[p], ctx->cfg.tie_rel, sub->need, ctx->sm_count,
-                                 sub->stream);
-            // FP32 leaf products stay on the side stream, one launch per product
-            if (e == cudaSuccess && ctx->cfg.precision == SPAMM_PREC_FP32)
-                e = launch_leaf_simt(sub, A[p], B[p], alpha[p], beta[p], C[p], ldc[p]);
-            jobs[p] = LeafJob{A[p], B[p], sub, alpha[p], beta[p], C[p], ldc[p]};
+        if (e == cudaSuccess) e = launch_ctl_batch(ctx->subs.data(), count, nullptr, s);
+        // the packs depend on the norms alone: side streams, beside the culls
+        if (e == cudaSuccess && tc) {
+            e = fork_aux(ctx);
+            for (int p = 0; p < count && e == cudaSuccess; ++p)
+                e = launch_packs(A[p], B[p], tau[p], ctx->cfg.tie_rel, ctx->subs[p]->need,
+                                 ctx->sm_count, ctx->subs[p]->stream);
         }
-        if (e == cudaSuccess) e = join_aux(ctx);
+        // stages 2-3 of all products: one launch per tier and grouping step
+        if (e == cudaSuccess)
+            e = launch_symbolic_batched(ctx, ctx->subs.data(), A, B, tau, count, s);
+        if (e == cudaSuccess && tc) e = join_aux(ctx);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
-        // tensor-core leaf products of all products: one persistent launch
-        if (e == cudaSuccess && ctx->cfg.precision != SPAMM_PREC_FP32)
-            e = launch_leaf_tc_jobs(ctx, jobs.data(), count);
+        if (e == cudaSuccess) {
+            if (tc) {
+                // tensor-core leaf products of all products: one persistent launch
+                e = launch_leaf_tc_jobs(ctx, jobs.data(), count);
+            } else {
+                // FP32 leaf products: one launch per product, on the side streams
+                e = fork_aux(ctx);
+                for (int p = 0; p < count && e == cudaSuccess; ++p) {
+                    spamm_ctx* sub = ctx->subs[p];
+                    e = launch_leaf_simt(sub, A[p], B[p], alpha[p], beta[p], C[p], ldc[p]);
+                }
+                if (e == cudaSuccess) e = join_aux(ctx);
+            }
+        }
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2], s);
-        for (int p = 0; p < count && e == cudaSuccess; ++p)
-            e = cudaMemcpyAsync(ctx->subs[p]->ctl_host, ctx->subs[p]->ctl, sizeof(DevCtl),
+        if (e == cudaSuccess) e = launch_ctl_batch(ctx->subs.data(), count, ctx->bctl, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->bctl_host, ctx->bctl, sizeof(DevCtl) * (size_t)count,
                                 cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s);
@@ -665,7 +690,7 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
         bool retry = false;
         for (int p = 0; p < count; ++p) {
             spamm_ctx* sub = ctx->subs[p];
-            const DevCtl& c = *sub->ctl_host;
+            const DevCtl& c = ctx->bctl_host[p];
             if (c.status & (ST_NONFINITE | ST_TIMEOUT))
                 return (spamm_status)(ctx->last_status = status_of(ctx, c));
             if (c.status & ST_OVERFLOW) {
@@ -689,7 +714,7 @@ static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     spamm_status worst = status_of(ctx, *ctx->ctl_host);
     for (int p = 0; p < ctx->last_batch && p < (int)ctx->subs.size(); ++p) {
         spamm_ctx* sub = ctx->subs[p];
-        const DevCtl& c = *sub->ctl_host;
+        const DevCtl& c = ctx->bctl_host[p];
         const int d = sub->last_d;
         for (int t = 0; t <= d && t < SPAMM_MAX_TIERS; ++t) {
             out->tier_candidates[t] += (int64_t)c.tier_cand[t];

@@ -163,7 +163,11 @@ struct spamm_ctx {
     // side streams for the per-product stages of batched calls (fork from
     // and join back into `stream`; inside a graph capture they become
     // parallel branches)
-    static constexpr int kAux = 8;
+    static constexpr int kAux = 16;
+    // gathered control blocks of the last batched multiply (device, pinned host)
+    spamm::DevCtl* bctl;
+    spamm::DevCtl* bctl_host;
+    int bctl_cap;
     cudaStream_t aux[kAux];
     cudaEvent_t aux_ev[kAux];
     cudaEvent_t fork_ev;
@@ -192,6 +196,14 @@ cudaError_t launch_cull(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B
                         int tt);
 cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
                          int tt);
+// Stages 2-3 of `count` products in sub-contexts subs[p] (tile tier
+// subs[p]->last_tt), table-driven launches of up to 64 products each.
+cudaError_t launch_symbolic_batched(spamm_ctx* ctx, spamm_ctx* const* subs,
+                                    const spamm_tree* const* A, const spamm_tree* const* B,
+                                    const double* tau, int count, cudaStream_t stream);
+// Zero the control blocks of subs[0..count) (out == nullptr) or gather them
+// into out[0..count).
+cudaError_t launch_ctl_batch(spamm_ctx* const* subs, int count, DevCtl* out, cudaStream_t s);
 
 // Tensor-core packs of the leaves that can take part in a kept product of
 // A x B at tau (norms.cu); scratch holds 2 x (leaves per side) doubles.
