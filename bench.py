@@ -40,6 +40,10 @@ WORKLOADS = {
                  "a_ij = g_ij exp(-0.5 r_ij), Hilbert order, b=16, A=B",
     "exp1024": "exponential decay a_ij = u_ij 0.9^|i-j| (n=1024), b=16, A=B",
     "alg16384": "algebraic decay a_ij = s_ij/(|i-j|^2+1) (n=16384), b=16, A=B",
+    "serving": "Poisson stream of 96 requests at 200/s, n log-uniform in [1024, 32768], "
+               "tau in {1e-6, 1e-8}, each a chain of 8 squarings X <- X^2 of an exponential-"
+               "decay matrix (lambda=0.9) scaled by 1/max row-sum, continuous batching under "
+               "a 150 GB device-memory budget, leaf size autotuned",
     "batched64": "64 independent products C_p = A_p A_p, n log-uniform in [512, 8192], "
                  "a_ij = u_ij lambda^|i-j| with lambda uniform in [0.8, 0.95], tau=1e-7, "
                  "one persistent leaf launch in a captured CUDA graph, leaf size and "
@@ -511,6 +515,93 @@ def run_batched(args, P, dev, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, P, dev, rank, world, dist):
+    """Continuous batching of chains of squarings on a Poisson arrival trace;
+    the same trace served one request at a time (a queue alone) beside it."""
+    import torch
+    from paper_1203_1692_gb300 import autotune
+    from paper_1203_1692_gb300.serve import GpuChainExecutor, Request, Server
+    from spamm_inputs import device as D
+    count = 96
+    trace = gen.serving_requests(count, rate=200.0, n_lo=1024, n_hi=32768,
+                                 taus=(1e-6, 1e-8), seed=0)
+    budget = 150 * (1 << 30)
+
+    def make_x0(n, seed):
+        X = D.exp_decay(n, 0.9, seed=seed, device=dev)
+        rows = torch.empty(n, dtype=torch.float32, device=dev)
+        for r0 in range(0, n, 4096):
+            rows[r0:r0 + 4096] = X[r0:r0 + 4096].abs().sum(1)
+        X /= rows.max()
+        return X
+
+    x0 = {rid: make_x0(n, s) for rid, (t, n, tau, s) in enumerate(trace)}
+    torch.cuda.synchronize()
+    # leaf size: the batch autotuner on one squaring of the first 16 requests
+    sample = list(range(min(16, count)))
+    choice = autotune.tune_batch([(x0[i], x0[i]) for i in sample],
+                                 [trace[i][2] for i in sample], args.precision)
+    b = choice.leaf
+
+    def requests():
+        return [Request(rid=i, n=n, tau=tau, squarings=8, arrival=t, X0=x0[i])
+                for i, (t, n, tau, s) in enumerate(trace)]
+
+    def serve(max_active):
+        ex = GpuChainExecutor(leaf=b, precision=args.precision, keep_results=False)
+        srv = Server(ex, budget_bytes=budget, max_active=max_active)
+        # warm-up on the first three requests (sub-contexts, pools, caches)
+        warm = Server(ex, budget_bytes=budget, max_active=max_active)
+        warm.run([Request(rid=-1 - i, n=trace[i][1], tau=trace[i][2], squarings=2, arrival=0.0,
+                          X0=x0[i]) for i in range(3)])
+        torch.cuda.synchronize()
+        ex.t0 = time.perf_counter()
+        t0 = ex.now()
+        done = srv.run(requests())
+        makespan = max(r.finished for r in done) - t0
+        lat = sorted(1e3 * r.latency for r in done)
+        flops = sum(r.kept_flops for r in done)
+        dense = sum(8 * 2.0 * r.n ** 3 for r in done)
+        ex.close()
+        pick = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+        return {"p50_ms": pick(0.5), "p99_ms": pick(0.99), "max_ms": lat[-1],
+                "makespan_s": makespan, "requests_per_s": len(done) / makespan,
+                "kept_tflops": flops / makespan / 1e12,
+                "dense_equivalent_tflops": dense / makespan / 1e12,
+                "iterations": srv.iterations,
+                "mean_batch": statistics.mean(srv.batch_sizes),
+                "max_batch": max(srv.batch_sizes),
+                "peak_budget_gb": srv.peak_used / 2 ** 30}
+
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    cont = serve(64)
+    clk = clocks.stop()
+    fifo = serve(1)
+    if rank != 0:
+        return
+    ns = [n for _, n, _, _ in trace]
+    line = {
+        "metric": "SpAMM serving: p50/p99 request latency and kept TFLOP/s, chains of 8 "
+                  "squarings under continuous batching",
+        "value": cont["kept_tflops"] * world, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": count, "warmup": 3, "ms_per_step": 1e3 * cont["makespan_s"] / count,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS["serving"], "requests": count,
+                   "n_min": min(ns), "n_max": max(ns), "leaf": b, "precision": args.precision,
+                   "budget_gb": 150, "max_active": 64,
+                   "autotune_ms": {f"b{k[0]}/{k[1]}": v for k, v in choice.trials.items()},
+                   "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+        "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
+        "continuous_batching": cont, "queue_one_at_a_time": fifo,
+        "p99_speedup_vs_queue": fifo["p99_ms"] / cont["p99_ms"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def kernels_per_step(d, leaf, precision="tf32x3", same_tree=True):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
@@ -538,6 +629,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.workload == "batched64":
         run_batched(args, P, dev, rank, world, dist)
+        return
+    if args.workload == "serving":
+        run_serving(args, P, dev, rank, world, dist)
         return
     A_h = make_matrix(args.workload, args.sites)
     n = A_h.shape[0]

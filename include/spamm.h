@@ -161,6 +161,11 @@ spamm_status spamm_tree_rebuild_batched(spamm_ctx *ctx, int32_t count, spamm_tre
 /* Free a tree.  Synchronises its context's stream first. */
 spamm_status spamm_tree_destroy(spamm_tree *tree);
 
+/* Device bytes a tree of order n takes under ctx's configuration (norm
+ * pyramid plus, for tensor-core precisions, the pack arrays), for admission
+ * control before spamm_build_norms.  INVALID_ARG, UNSUPPORTED. */
+spamm_status spamm_tree_footprint(const spamm_ctx *ctx, int64_t n, int64_t *bytes);
+
 /* Depth and node count of a tree (no synchronisation). */
 spamm_status spamm_tree_shape(const spamm_tree *tree, int32_t *depth, int64_t *nodes);
 
@@ -205,6 +210,11 @@ spamm_status spamm_multiply_batched(spamm_ctx *ctx, int32_t count, const spamm_t
                                     const spamm_tree *const *B, const double *tau,
                                     const float *alpha, const float *beta, float *const *C,
                                     const int64_t *ldc);
+
+/* Statistics of product `index` of the last spamm_multiply_batched on ctx
+ * (same fields as spamm_stats, without the timings).  Synchronises.
+ * INVALID_ARG (no such product), or the product's own status. */
+spamm_status spamm_stats_item(spamm_ctx *ctx, int32_t index, spamm_stats_t *out);
 
 /* End-to-end form with HOST matrices (row-major, ld = n): copies A and B
  * (and C when beta != 0) to device buffers owned by ctx, builds both trees,

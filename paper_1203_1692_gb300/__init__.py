@@ -17,6 +17,7 @@ from ._abi import (PRECISIONS, SpammError, spamm_build_norms, spamm_config_defau
                    spamm_create, spamm_destroy, spamm_multiply, spamm_multiply_batched,
                    spamm_multiply_host,
                    spamm_reserve, spamm_set_checked, spamm_set_stream, spamm_stats,
+                   spamm_stats_item,
                    spamm_tree_destroy, spamm_tree_norms, spamm_tree_rebuild,
                    spamm_tree_rebuild_batched, spamm_tree_shape,
                    spamm_triples)
@@ -99,6 +100,10 @@ class Context:
 
     def build_norms(self, A) -> Tree:
         return Tree(self, A)
+
+    def tree_footprint(self, n: int) -> int:
+        """Device bytes of a tree of order n under this configuration."""
+        return _abi.spamm_tree_footprint(self.handle, n)
 
     def multiply(self, A: Tree, B: Tree, tau: float, alpha: float = 1.0, beta: float = 0.0,
                  C=None):
@@ -186,6 +191,10 @@ class Context:
             "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
             "ms_pack": s.ms_pack,
         }
+
+    def per_product_flops(self, count: int) -> list:
+        """Kept flops of each product of the last batched multiply."""
+        return [spamm_stats_item(self.handle, p).kept_flops for p in range(count)]
 
     def triples(self) -> np.ndarray:
         count = ctypes.c_int64()

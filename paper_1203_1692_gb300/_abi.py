@@ -73,6 +73,7 @@ SIGNATURES = {
                                           ctypes.POINTER(_i64)]),
     "spamm_tree_destroy": (_i32, [_vp]),
     "spamm_tree_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "spamm_tree_footprint": (_i32, [_vp, _i64, ctypes.POINTER(_i64)]),
     "spamm_tree_norms": (_i32, [_vp, _vp, _vp, _i64]),
     "spamm_multiply": (_i32, [_vp, _vp, _vp, _dbl, _flt, _flt, _vp, _i64]),
     "spamm_multiply_batched": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -81,6 +82,7 @@ SIGNATURES = {
                                       ctypes.POINTER(_i64)]),
     "spamm_multiply_host": (_i32, [_vp, _vp, _vp, _i64, _dbl, _flt, _flt, _vp]),
     "spamm_stats": (_i32, [_vp, ctypes.POINTER(spamm_stats_t)]),
+    "spamm_stats_item": (_i32, [_vp, _i32, ctypes.POINTER(spamm_stats_t)]),
     "spamm_triples": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "spamm_multiply_static": (_i32, [_vp, _i64, _vp, _i64, _i64, _dbl, _flt, _flt, _vp, _i64,
                                      _vp, _vp]),
@@ -178,6 +180,12 @@ def spamm_tree_shape(tree):
     return d.value, m.value
 
 
+def spamm_tree_footprint(ctx, n: int) -> int:
+    out = _i64()
+    check(lib().spamm_tree_footprint(ctx, n, ctypes.byref(out)), ctx)
+    return out.value
+
+
 def spamm_tree_norms(ctx, tree, out_ptr: int, count: int) -> None:
     check(lib().spamm_tree_norms(ctx, tree, _vp(out_ptr), count), ctx)
 
@@ -215,6 +223,14 @@ def spamm_multiply_host(ctx, A_ptr: int, B_ptr, n: int, tau: float, alpha: float
 def spamm_stats(ctx, raise_on_error: bool = True) -> spamm_stats_t:
     s = spamm_stats_t()
     st = lib().spamm_stats(ctx, ctypes.byref(s))
+    if raise_on_error:
+        check(st, ctx)
+    return s
+
+
+def spamm_stats_item(ctx, index: int, raise_on_error: bool = True) -> spamm_stats_t:
+    s = spamm_stats_t()
+    st = lib().spamm_stats_item(ctx, index, ctypes.byref(s))
     if raise_on_error:
         check(st, ctx)
     return s

@@ -312,6 +312,23 @@ spamm_status spamm_tree_destroy(spamm_tree* t) {
     return SPAMM_OK;
 }
 
+spamm_status spamm_tree_footprint(const spamm_ctx* ctx, int64_t n, int64_t* bytes) {
+    if (!ctx || !bytes || n <= 0) return SPAMM_ERR_INVALID_ARG;
+    const int b = ctx->cfg.leaf;
+    const int d = depth_for(n, b);
+    const int64_t nl = (n + b - 1) / b;
+    if (nl > kMaxLeavesPerSide || d >= SPAMM_MAX_TIERS - 1) return SPAMM_ERR_UNSUPPORTED;
+    const int tl = kTileRows / b;
+    const int64_t nlp = (nl + 2 * tl - 1) / (2 * tl) * (2 * tl);
+    const int64_t nodes = (((int64_t)1 << (2 * (d + 1))) - 1) / 3;
+    int64_t total = (int64_t)sizeof(double) * nodes;
+    if (precision_uses_tc(ctx->cfg.precision))
+        total += 2 * (int64_t)pack_arrays_for(ctx->cfg.precision) *
+                 (int64_t)pack_bytes_for(ctx->cfg.precision, nlp, b);
+    *bytes = total;
+    return SPAMM_OK;
+}
+
 spamm_status spamm_tree_shape(const spamm_tree* t, int32_t* depth, int64_t* nodes) {
     if (!t) return SPAMM_ERR_INVALID_ARG;
     if (depth) *depth = t->d;
@@ -707,6 +724,38 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
         if (retry) return (spamm_status)(ctx->last_status = set_err(ctx, SPAMM_ERR_CAPACITY, "pool"));
         return SPAMM_OK;
     }
+}
+
+spamm_status spamm_stats_item(spamm_ctx* ctx, int32_t index, spamm_stats_t* out) {
+    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "stats");
+    if (index < 0 || index >= ctx->last_batch)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "no such product in the last batch");
+    memset(out, 0, sizeof(*out));
+    spamm_ctx* sub = ctx->subs[index];
+    const DevCtl& c = ctx->bctl_host[index];
+    const int d = sub->last_d;
+    out->depth = d;
+    out->n = sub->last_n;
+    out->leaf = sub->last_b;
+    out->precision = sub->last_prec;
+    out->tau = sub->last_tau;
+    for (int t = 0; t <= d && t < SPAMM_MAX_TIERS; ++t) {
+        out->tier_candidates[t] = (int64_t)c.tier_cand[t];
+        out->tier_kept[t] = (int64_t)c.tier_count[t];
+    }
+    out->leaf_triples = (int64_t)c.tier_count[d];
+    out->tie_band = (int64_t)c.tie_band;
+    out->active_steps = (int64_t)c.active_steps;
+    out->tiles = sub->last_tiles;
+    const double b = sub->last_b;
+    out->kept_flops = 2.0 * b * b * b * (double)out->leaf_triples;
+    out->dense_flops = 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
+    out->pool_bytes = sub->pool_words * 8;
+    out->pool_needed_bytes = words_needed(c, sub->last_tt, sub->last_S) * 8;
+    out->status = status_of(ctx, c);
+    return (spamm_status)out->status;
 }
 
 static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
