@@ -37,7 +37,8 @@ import spamm_inputs as gen  # noqa: E402
 TAU_GRID = [1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10]
 WORKLOADS = {
     "water7500": "water-cluster-like density matrix, 300 sites x 25 functions (n=7500), "
-                 "a_ij = g_ij exp(-0.5 r_ij), Hilbert order, b=16, A=B",
+                 "a_ij = g_ij exp(-0.5 r_ij), Hilbert order, A=B, leaf size autotuned at "
+                 "equal max error",
     "exp1024": "exponential decay a_ij = u_ij 0.9^|i-j| (n=1024), b=16, A=B",
     "alg16384": "algebraic decay a_ij = s_ij/(|i-j|^2+1) (n=16384), b=16, A=B",
     "serving": "Poisson stream of 96 requests at 200/s, n log-uniform in [1024, 32768], "
@@ -65,7 +66,8 @@ def parse():
     p.add_argument("--impl", default="spamm", choices=["spamm", "reference"])
     p.add_argument("--workload", default="water7500", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "tf32", "bf16x3"])
-    p.add_argument("--leaf", type=int, default=16)
+    p.add_argument("--leaf", default="auto",
+                   help="leaf size b, or 'auto': the fastest of 16/32/64/128 at equal error")
     p.add_argument("--tau", default="auto")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -173,7 +175,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     A = make_matrix(args.workload)
-    b = args.leaf
+    b = 16 if args.leaf == "auto" else int(args.leaf)
     tau = 1e-6 if args.tau == "auto" else float(args.tau)
     budget = min(10.0, 150.0 / max(1, args.steps + args.warmup))
     vals = []
@@ -635,11 +637,10 @@ def main():
         return
     A_h = make_matrix(args.workload, args.sites)
     n = A_h.shape[0]
-    b = args.leaf
     A = torch.from_numpy(A_h).to(dev)
     stream = torch.cuda.current_stream()
     if args.quick:
-        run_quick(args, P, A, n, b, stream)
+        run_quick(args, P, A, n, 16 if args.leaf == "auto" else int(args.leaf), stream)
         return
 
     # --- equal-error tau against cuBLAS SGEMM (not timed) ----------------
@@ -663,24 +664,60 @@ def main():
     t_sgemm = ev[0].elapsed_time(ev[1]) / reps
     del C_sgemm
 
-    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
-    tree = ctx.build_norms(A)
-    C = torch.empty_like(A)
-    sweep = []
-    if args.tau == "auto":
-        tau = None
+    # --- leaf size: per candidate b the equal-error tau (the largest grid
+    # tau whose max error is at or below SGEMM's), then the fastest step ---
+    def sweep_tau(b, full):
+        c = P.Context(leaf=b, precision=args.precision, checked=True)
+        tr = c.build_norms(A)
+        out = torch.empty_like(A)
+        rec, found = [], None
         for t in TAU_GRID:
-            ctx.multiply(tree, tree, t, C=C)
-            err = float((C.double() - C_exact).abs().max())
-            st = ctx.stats()
-            sweep.append({"tau": t, "max_err": err, "kept": st["leaf_triples"],
-                          "ms": st["ms_total"]})
-            if err <= err_sgemm and tau is None:
-                tau = t
-        if tau is None:        # no tau on the grid reaches SGEMM's error
-            tau = TAU_GRID[-1]
+            c.multiply(tr, tr, t, C=out)
+            err = float((out.double() - C_exact).abs().max())
+            st = c.stats()
+            rec.append({"tau": t, "max_err": err, "kept": st["leaf_triples"],
+                        "ms": st["ms_total"]})
+            if err <= err_sgemm and found is None:
+                found = t
+                if not full:
+                    break
+        return c, tr, out, (found if found is not None else TAU_GRID[-1]), rec
+
+    def step_ms(c, tr, out, t, reps=5):
+        c.set_checked(False)
+        for _ in range(2):
+            tr.rebuild(A)
+            c.multiply(tr, tr, t, C=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            tr.rebuild(A)
+            c.multiply(tr, tr, t, C=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c.stats()
+        c.set_checked(True)
+        return e0.elapsed_time(e1) / reps
+
+    leaves = (16, 32, 64, 128) if args.leaf == "auto" else (int(args.leaf),)
+    leaf_trials = {}
+    for cand in leaves:
+        if args.tau == "auto":
+            c, tr, out, t, _ = sweep_tau(cand, full=False)
+        else:
+            c = P.Context(leaf=cand, precision=args.precision, checked=True)
+            tr, out, t = c.build_norms(A), torch.empty_like(A), float(args.tau)
+        leaf_trials[cand] = {"tau": t, "ms": step_ms(c, tr, out, t)}
+        tr.close()
+        c.close()
+    b = min(leaf_trials, key=lambda k: leaf_trials[k]["ms"])
+    if args.tau == "auto":
+        ctx, tree, C, tau, sweep = sweep_tau(b, full=True)
     else:
-        tau = float(args.tau)
+        ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+        tree = ctx.build_norms(A)
+        C = torch.empty_like(A)
+        tau, sweep = float(args.tau), []
     ctx.multiply(tree, tree, tau, C=C)
     err_tau = float((C.double() - C_exact).abs().max())
     parity = sampled_parity(A_h, C, b, tau)
@@ -789,6 +826,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32"
         else args.precision, "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "n": n, "leaf": b, "tau": tau,
+                   "leaf_trials": {str(k): v for k, v in leaf_trials.items()},
                    "precision": args.precision,
                    "l2": "inputs larger than L2 (A and C 4n^2 bytes each)",
                    "parallelism": f"replicas x{world}"},

@@ -183,6 +183,8 @@ spamm_status spamm_destroy(spamm_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->hostTreeA) spamm_tree_destroy(ctx->hostTreeA);
     if (ctx->hostTreeB) spamm_tree_destroy(ctx->hostTreeB);
+    for (spamm_tree* t : ctx->trees) t->ctx = nullptr;
+    ctx->trees.clear();
     for (spamm_ctx* sub : ctx->subs) spamm_destroy(sub);
     ctx->subs.clear();
     cudaFree(ctx->pool);
@@ -255,6 +257,7 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
     spamm_tree* t = new (std::nothrow) spamm_tree();
     if (!t) return SPAMM_ERR_OOM;
     t->ctx = ctx;
+    ctx->trees.push_back(t);
     t->A = A;
     t->n = n;
     t->lda = lda;
@@ -306,8 +309,12 @@ spamm_status spamm_tree_rebuild(spamm_ctx* ctx, spamm_tree* t, const float* A, i
 
 spamm_status spamm_tree_destroy(spamm_tree* t) {
     if (!t) return SPAMM_ERR_INVALID_ARG;
-    if (t->ctx) cudaStreamSynchronize(t->ctx->stream);
-    free_tree_storage(t);
+    if (t->ctx) {
+        cudaStreamSynchronize(t->ctx->stream);
+        std::vector<spamm_tree*>& v = t->ctx->trees;
+        v.erase(std::remove(v.begin(), v.end(), t), v.end());
+    }
+    free_tree_storage(t);   // cudaFree waits for work that still uses it
     delete t;
     return SPAMM_OK;
 }

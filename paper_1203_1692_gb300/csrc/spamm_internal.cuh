@@ -160,6 +160,9 @@ struct spamm_ctx {
     // per product, created on demand and reused
     std::vector<spamm_ctx*> subs;
     int last_batch;  // products in the last multiply (0: a plain multiply)
+    // trees built on this context: destroying the context detaches them, so
+    // a tree freed later never touches the freed context
+    std::vector<spamm_tree*> trees;
     // side streams for the per-product stages of batched calls (fork from
     // and join back into `stream`; inside a graph capture they become
     // parallel branches)

@@ -259,3 +259,16 @@ def test_water_like_n7500_sampled():
     assert err <= 1e-5
     st = ctx.stats()
     assert st["depth"] == 9 and st["leaf_triples"] > 0
+
+
+def test_tree_outliving_its_context_is_freed_safely():
+    """A tree freed after its context (as garbage collection may order it)
+    must not touch the freed context."""
+    P = _spamm()
+    for prec in ("fp32", "tf32x3"):
+        ctx = P.Context(leaf=16, precision=prec)
+        A = _dev(gen.exp_decay(300, 0.9, seed=1))
+        t = ctx.build_norms(A)
+        ctx.multiply(t, t, 1e-6)
+        ctx.close()
+        t.close()
