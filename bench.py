@@ -53,9 +53,9 @@ WORKLOADS = {
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense tensor-core ratio
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from an ncu capture, keyed by (kernel, workload, precision);
-# refreshed whenever that kernel changes.
-TRAFFIC = {}
+# kernel from an ncu capture (GB), keyed by (kernel, workload, precision,
+# leaf); refreshed whenever that kernel changes.
+TRAFFIC = {("k_leaf_tc", "water7500", "tf32x3", 64): 4.848742 + 0.229794}
 
 
 def parse():
@@ -479,7 +479,7 @@ def run_batched(args, P, dev, rank, world, dist):
                                f"{'1.1/2.25 (tf32/bf16 nominal)' if tf else '1'}"}
     achieved = kept_flops / (leaf_ms * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision)),
+                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision, b)),
                  "note": f"of {peak_src}; algorithmic flops = 2 b^3 x kept leaf triples of "
                          "the whole batch, one leaf launch"})
     cpu = None
@@ -813,7 +813,8 @@ def main():
                                f"{'1.1/2.25 (tf32/bf16 nominal)' if args.precision.startswith('tf32') else '1'}"}
     achieved = kept_flops / (leaf_ms * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision)),
+                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision, b)),
+                 "traffic_unit": "GB per launch",
                  "note": f"of {peak_src}; algorithmic flops = 2 b^3 x kept leaf triples"})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
