@@ -66,6 +66,9 @@ def lib():
         L.oracle_multiply.restype = _c_i64
         L.oracle_multiply.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _c_dbl, _c_dbl,
                                       _c_dbl, _p, _c_i64, _p, _c_i64, _p]
+        L.oracle_multiply_sliced.restype = _c_i64
+        L.oracle_multiply_sliced.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _c_i64,
+                                             _c_dbl, _c_dbl, _c_dbl, _p, _c_i64, _p]
         L.oracle_block.restype = _c_i64
         L.oracle_block.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _p, _p, _c_dbl,
                                    _c_i64, _c_i64, _p]
@@ -201,6 +204,26 @@ def multiply(A, B, b: int, tau: float, alpha: float = 1.0, beta: float = 0.0,
         if m < 0:
             raise RuntimeError(f"oracle_multiply failed ({m})")
         return Result(Cd, out[:m].copy(), stats[:d + 1].copy(), stats[d + 1:].copy())
+
+
+def multiply_sliced(A, B, b: int, g: int, tau: float, alpha: float = 1.0, beta: float = 0.0,
+                    C=None):
+    """C = alpha * SpAMM(A, B; b, tau) with the sub-leaf cull along k in
+    slices of g (reading R14) + beta * C, in FP64.  Returns (C, kept leaf
+    triples, kept slice products, tested slice products)."""
+    A = _f32(A)
+    B = _f32(B)
+    n = A.shape[0]
+    if B.shape != A.shape:
+        raise ValueError("shape mismatch")
+    Cd = np.zeros((n, n), dtype=np.float64) if C is None else \
+        np.ascontiguousarray(C, dtype=np.float64).copy()
+    stats = np.zeros(2, dtype=np.int64)
+    m = lib().oracle_multiply_sliced(_ptr(A), n, _ptr(B), n, n, b, g, tau, alpha, beta,
+                                     _ptr(Cd), n, _ptr(stats))
+    if m < 0:
+        raise RuntimeError(f"oracle_multiply_sliced failed ({m})")
+    return Cd, int(m), int(stats[0]), int(stats[1])
 
 
 def blocks(A, B, b: int, tau: float, ij, pyrA=None, pyrB=None):

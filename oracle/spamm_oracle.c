@@ -26,7 +26,10 @@
  *       tau = 0;
  *   R4  d = ceil(log2(n / b)) is taken as the smallest d >= 0 with
  *       b * 2^d >= n (so d = 0 when n <= b);
- *   R5  within a C block the kept products are accumulated in ascending k.
+ *   R5  within a C block the kept products are accumulated in ascending k;
+ *   R14 the sub-leaf cull (oracle_multiply_sliced) splits the k dimension of
+ *       a kept leaf product into slices of g and keeps a slice product iff
+ *       the norms of its two panels pass the same condition.
  */
 #include <math.h>
 #include <stdint.h>
@@ -362,6 +365,92 @@ int64_t oracle_multiply(const float *A, int64_t lda, const float *B, int64_t ldb
     }
     free(rowstart);
     return err ? OR_ENOMEM : cnt;
+}
+
+/* Sub-leaf cull along k (the paper's SpAMM(4x4) of Sec. III.B, cull finer
+ * than storage, read for tensor cores, reading R14): the leaf triples kept
+ * by the recursive product are multiplied slice by slice.  Slice s of leaf
+ * column K covers the g columns K*b + s*g .. K*b + s*g + g - 1 of A (the
+ * same rows of B); the b x g panel of A_IK and the g x b panel of B_KJ are
+ * multiplied only if their Frobenius norms pass the SpAMM condition (R1-R3,
+ * squared in FP64, panel norms summed row-major from exact squares).  Each C
+ * block accumulates its kept slice products in ascending (K, s).
+ * stats[0] = kept slice products, stats[1] = tested slice products.
+ * Returns the number of kept leaf triples or an error code. */
+static double panel_norm2(const float *M, int64_t ld, int64_t n, int64_t r0, int64_t nr,
+                          int64_t c0, int64_t nc)
+{
+    double s = 0.0;
+    for (int64_t r = r0; r < r0 + nr && r < n; r++)
+        for (int64_t c = c0; c < c0 + nc && c < n; c++) {
+            double v = (double)M[r * ld + c];
+            s += v * v;
+        }
+    return s;
+}
+
+int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int64_t ldb,
+                               int64_t n, int64_t b, int64_t g, double tau, double alpha,
+                               double beta, double *C, int64_t ldc, int64_t *stats)
+{
+    int d = oracle_depth(n, b);
+    if (d < 0 || lda < n || ldb < n || ldc < n || !(tau >= 0.0) || g <= 0 || b % g) return OR_EARG;
+    int64_t ps = oracle_pyramid_size(d);
+    double *pa = (double *)malloc(sizeof(double) * (size_t)ps);
+    double *pb = (double *)malloc(sizeof(double) * (size_t)ps);
+    int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(d + 1));
+    if (!pa || !pb || !cand) { free(pa); free(pb); free(cand); return OR_ENOMEM; }
+    oracle_build_pyramid(A, n, lda, b, pa);
+    oracle_build_pyramid(B, n, ldb, b, pb);
+    /* count, then collect the kept leaf triples */
+    int64_t cnt = oracle_cull_recursive(pa, pb, d, tau, NULL, 0, cand, cand + d + 1);
+    int32_t *tri = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(cnt > 0 ? cnt : 1));
+    if (!tri) { free(pa); free(pb); free(cand); return OR_ENOMEM; }
+    oracle_cull_recursive(pa, pb, d, tau, tri, cnt, cand, cand + d + 1);
+    free(pa);
+    free(pb);
+    free(cand);
+    qsort(tri, (size_t)cnt, 3 * sizeof(int32_t), cmp_ijk);
+    int64_t nbr = (n + b - 1) / b;
+    int64_t kept = 0, tested = 0;
+    double *acc = (double *)malloc(sizeof(double) * (size_t)(b * b * nbr));
+    if (!acc) { free(tri); return OR_ENOMEM; }
+    int64_t t = 0;
+    for (int64_t I = 0; I < nbr; I++) {
+        memset(acc, 0, sizeof(double) * (size_t)(b * b * nbr));
+        for (; t < cnt && tri[3 * t] == I; t++) {
+            int64_t K = tri[3 * t + 1], J = tri[3 * t + 2];
+            for (int64_t s0 = 0; s0 < b; s0 += g) {
+                int64_t k0 = K * b + s0;
+                double na = panel_norm2(A, lda, n, I * b, b, k0, g);
+                double nbv = panel_norm2(B, ldb, n, k0, g, J * b, b);
+                tested++;
+                if (!keep(na, nbv, tau * tau)) continue;
+                kept++;
+                double *blk = acc + J * b * b;
+                for (int64_t r = 0; r < b && I * b + r < n; r++)
+                    for (int64_t c = 0; c < b && J * b + c < n; c++) {
+                        double sum = 0.0;
+                        for (int64_t q = k0; q < k0 + g && q < n; q++)
+                            sum += (double)A[(I * b + r) * lda + q] * (double)B[q * ldb + J * b + c];
+                        blk[r * b + c] += sum;
+                    }
+            }
+        }
+        for (int64_t r = I * b; r < I * b + b && r < n; r++)
+            for (int64_t c = 0; c < n; c++) {
+                int64_t J = c / b;
+                double v = alpha * acc[J * b * b + (r - I * b) * b + (c - J * b)];
+                C[r * ldc + c] = beta == 0.0 ? v : v + beta * C[r * ldc + c];
+            }
+    }
+    free(acc);
+    free(tri);
+    if (stats) {
+        stats[0] = kept;
+        stats[1] = tested;
+    }
+    return cnt;
 }
 
 /* One C block without the epilogue, for spot checks at sizes where the full

@@ -320,3 +320,51 @@ def test_blocks_match_full_oracle():
             blk = r.C[I*b:min(n, (I+1)*b), J*b:min(n, (J+1)*b)]
             np.testing.assert_allclose(acc[q][:blk.shape[0], :blk.shape[1]], blk,
                                        rtol=1e-13, atol=1e-15)
+
+
+# ------------------------------------------- sub-leaf cull along k (R14)
+
+def test_sliced_with_one_slice_per_leaf_is_plain_spamm():
+    A = gen.exp_decay(100, 0.8, seed=1)
+    for b, tau in [(16, 1e-3), (8, 1e-5), (32, 1e-2)]:
+        C, m, kept, tested = O.multiply_sliced(A, A, b, b, tau)
+        ref = O.multiply(A, A, b, tau)
+        assert np.array_equal(C, ref.C)
+        assert m == kept == tested == len(ref.triples)
+
+
+def test_sliced_at_tau_zero_is_the_dense_product():
+    A = gen.uniform_dense(70, seed=3, symmetric=False)
+    B = gen.exp_decay_nonsym(70, 0.9, seed=4)
+    C, m, kept, tested = O.multiply_sliced(A, B, 16, 4, 0.0)
+    exact = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.abs(C - exact).max() <= 1e-12 * np.abs(exact).max()
+
+
+def test_sliced_zero_panels_are_null_and_cost_no_accuracy():
+    """Every leaf's k-columns 2, 3 (of 4) are zero in A: slice 1 of every
+    leaf product has a zero panel, is dropped even at tau = 0 (R3), and the
+    product is still exact."""
+    n, b, g = 48, 4, 2
+    A = gen.uniform_dense(n, seed=5, symmetric=False)
+    A[:, np.arange(n) % 4 >= 2] = 0.0
+    B = gen.uniform_dense(n, seed=6, symmetric=False)
+    C, m, kept, tested = O.multiply_sliced(A, B, b, g, 0.0)
+    assert tested == 2 * m and kept == m
+    exact = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.abs(C - exact).max() <= 1e-12 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("b,g,tau", [(16, 4, 1e-3), (16, 8, 3e-4), (32, 16, 1e-3)])
+def test_sliced_error_bound_and_monotone(b, g, tau):
+    """Each dropped slice product has norm below tau (Frobenius
+    submultiplicativity), so ||C_leaf - C_sliced||_F < dropped * tau; fewer
+    slices survive a larger tau."""
+    A = gen.exp_decay(120, 0.85, seed=7)
+    plain = O.multiply(A, A, b, tau).C
+    C, m, kept, tested = O.multiply_sliced(A, A, b, g, tau)
+    assert kept <= tested == m * (b // g)
+    err = np.linalg.norm(plain - C)
+    assert err <= (tested - kept) * tau * (1 + 1e-12)
+    _, _, kept2, _ = O.multiply_sliced(A, A, b, g, tau * 3)
+    assert kept2 <= kept
