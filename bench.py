@@ -76,6 +76,7 @@ def parse():
                    help="water-like workload: number of sites (n = 25 x sites)")
     p.add_argument("--alt", default="bf16x3",
                    help="also time this leaf precision on the same workload ('' = off)")
+    p.add_argument("--slice", type=int, default=0, help="sub-leaf cull along k (16) or off (0)")
     p.add_argument("--quick", action="store_true",
                    help="time the SpAMM step only at a fixed --tau (for profiling)")
     return p.parse_args()
@@ -255,7 +256,7 @@ def run_quick(args, P, A, n, b, stream):
     """Time the SpAMM step alone at a fixed tau (no reference products)."""
     import torch
     tau = 1e-4 if args.tau == "auto" else float(args.tau)
-    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True, slice=args.slice)
     tree = ctx.build_norms(A)
     C = torch.empty_like(A)
     ctx.multiply(tree, tree, tau, C=C)
@@ -273,7 +274,8 @@ def run_quick(args, P, A, n, b, stream):
     torch.cuda.synchronize()
     st = ctx.stats()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"mode": "quick", "n": n, "leaf": b, "tau": tau,
+    print(json.dumps({"mode": "quick", "n": n, "leaf": b, "tau": tau, "slice": args.slice,
+                      "slice_kept": st["slice_kept"], "slice_tested": st["slice_tested"],
                       "precision": args.precision, "ms_per_step": ms,
                       "kept_tflops": st["kept_flops"] / (ms * 1e-3) / 1e12,
                       "ms_symbolic": st["ms_symbolic"], "ms_pack": st["ms_pack"],
@@ -303,7 +305,7 @@ def run_batched(args, P, dev, rank, world, dist):
     choice = autotune.tune_batch([(A, A) for A in mats], taus, args.precision, leaves=leaves)
     b = choice.leaf
     perm = choice.permutation(ns)
-    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True, slice=choice.slice)
     trees = [ctx.build_norms(mats[p]) for p in perm]
     Cs = [torch.empty_like(mats[p]) for p in perm]
     ctx.multiply_batched(trees, trees, taus, None, None, Cs)
@@ -500,8 +502,9 @@ def run_batched(args, P, dev, rank, world, dist):
         "config": {"workload": WORKLOADS["batched64"], "products": count,
                    "n_min": min(ns), "n_max": max(ns), "sum_n3": float(sum(n ** 3 for n in ns)),
                    "tau": tau, "precision": args.precision, "leaf": b,
-                   "order": choice.order, "autotune_ms": {f"b{k[0]}/{k[1]}": v
-                                                         for k, v in choice.trials.items()},
+                   "order": choice.order, "slice": choice.slice,
+                   "autotune_ms": {f"b{k[0]}/{k[1]}/s{k[2]}": v
+                                   for k, v in choice.trials.items()},
                    "graph": "norm trees + culls + one leaf launch captured and replayed",
                    "l2": "inputs larger than L2 (sum of 4n^2 over the batch)",
                    "parallelism": f"replicas x{world}"},
@@ -542,7 +545,7 @@ def run_serving(args, P, dev, rank, world, dist):
     # leaf size: the batch autotuner on one squaring of the first 16 requests
     sample = list(range(min(16, count)))
     choice = autotune.tune_batch([(x0[i], x0[i]) for i in sample],
-                                 [trace[i][2] for i in sample], args.precision)
+                                 [trace[i][2] for i in sample], args.precision, slices=(0,))
     b = choice.leaf
 
     def requests():
@@ -594,7 +597,7 @@ def run_serving(args, P, dev, rank, world, dist):
         "config": {"workload": WORKLOADS["serving"], "requests": count,
                    "n_min": min(ns), "n_max": max(ns), "leaf": b, "precision": args.precision,
                    "budget_gb": 150, "max_active": 64,
-                   "autotune_ms": {f"b{k[0]}/{k[1]}": v for k, v in choice.trials.items()},
+                   "autotune_ms": {f"b{k[0]}/{k[1]}/s{k[2]}": v for k, v in choice.trials.items()},
                    "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
         "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
         "continuous_batching": cont, "queue_one_at_a_time": fifo,

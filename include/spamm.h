@@ -69,7 +69,14 @@ typedef struct {
                               pool and re-runs on overflow, and reports device
                               errors in its return code; 0: fully asynchronous,
                               check spamm_stats */
-    int32_t reserved[7];   /* must be zero */
+    int32_t slice;         /* sub-leaf cull along k (the paper's SpAMM(4x4),
+                              Sec. III.B, cull finer than storage): 0 = off;
+                              16 = inside each kept leaf product, the product
+                              of the b x 16 panel of A_IK and the 16 x b panel
+                              of B_KJ over each group of 16 k is kept only if
+                              their norms pass the SpAMM condition.
+                              Tensor-core precisions and leaf >= 32 only. */
+    int32_t reserved[6];   /* must be zero */
 } spamm_config;
 
 /* Fill *cfg with the defaults: leaf 16, SPAMM_PREC_FP32, tie_rel 1e-6,
@@ -95,7 +102,8 @@ typedef struct {
                                           <= tie_rel * tau, over all tiers */
     int64_t active_steps;              /* (C tile, K) pairs with >= 1 kept product */
     int64_t tiles;                     /* 128 x 256 C tiles (incl. empty ones) */
-    double kept_flops;                 /* 2 b^3 per leaf triple */
+    double kept_flops;                 /* 2 b^3 per leaf triple (2 b^2 slice per
+                                          kept slice product with slice != 0) */
     double dense_flops;                /* 2 n^3 (Appendix A, square case) */
     int64_t pool_bytes;                /* current pool size */
     int64_t pool_needed_bytes;         /* bytes the last multiply needed */
@@ -103,6 +111,10 @@ typedef struct {
     float ms_numeric;                  /* leaf products + C epilogue */
     float ms_total;
     float ms_pack;                     /* tensor-core packs of the needed leaves */
+    int32_t slice;                     /* the config's slice (0: off) */
+    int32_t pad;
+    int64_t slice_kept;                /* kept k-slice products (slice != 0) */
+    int64_t slice_tested;              /* tested k-slice products (slice != 0) */
 } spamm_stats_t;
 
 /* Create a context bound to the current CUDA device and to `stream` (a

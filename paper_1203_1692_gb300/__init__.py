@@ -85,10 +85,11 @@ class Context:
     """A SpAMM context on the current CUDA device and stream."""
 
     def __init__(self, leaf: int = 16, precision: str = "fp32", tie_rel: float = 1e-6,
-                 pool_bytes: int = 0, checked: bool = True, stream=None):
+                 pool_bytes: int = 0, checked: bool = True, stream=None, slice: int = 0):
         torch = _torch()
         cfg = spamm_config_default()
         cfg.leaf = leaf
+        cfg.slice = slice
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.tie_rel = tie_rel
         cfg.pool_bytes = pool_bytes
@@ -96,6 +97,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = spamm_create(self.stream.cuda_stream, cfg)
         self.leaf = leaf
+        self.slice = slice
         self.precision = precision
 
     def build_norms(self, A) -> Tree:
@@ -189,7 +191,8 @@ class Context:
             "kept_flops": s.kept_flops, "dense_flops": s.dense_flops,
             "pool_bytes": s.pool_bytes, "pool_needed_bytes": s.pool_needed_bytes,
             "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
-            "ms_pack": s.ms_pack,
+            "ms_pack": s.ms_pack, "slice": s.slice, "slice_kept": s.slice_kept,
+            "slice_tested": s.slice_tested,
         }
 
     def per_product_flops(self, count: int) -> list:

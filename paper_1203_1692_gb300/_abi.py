@@ -35,7 +35,8 @@ SPAMM_MAX_TIERS = 32
 class spamm_config(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tie_rel", ctypes.c_double), ("pool_bytes", ctypes.c_int64),
-                ("checked", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("checked", ctypes.c_int32), ("slice", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class spamm_stats_t(ctypes.Structure):
@@ -49,7 +50,9 @@ class spamm_stats_t(ctypes.Structure):
                 ("kept_flops", ctypes.c_double), ("dense_flops", ctypes.c_double),
                 ("pool_bytes", ctypes.c_int64), ("pool_needed_bytes", ctypes.c_int64),
                 ("ms_symbolic", ctypes.c_float), ("ms_numeric", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("ms_pack", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_pack", ctypes.c_float),
+                ("slice", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("slice_kept", ctypes.c_int64), ("slice_tested", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p

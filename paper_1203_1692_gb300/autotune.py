@@ -8,7 +8,8 @@ decay and on tau, so it is measured rather than modelled.  Every candidate
 spamm_multiply_batched, event-timed on the context's stream after a
 warm-up, and the fastest is kept.
 
-The schedule candidate is the order of the products in the launch.  The
+The schedule candidates are the order of the products in the launch and,
+when the caller allows it, the sub-leaf cull along k (16-wide slices).  The
 persistent leaf kernel deals the concatenated list of C tiles out to its
 blocks in turn, so the products at the end of the list make up the tail of
 the launch; "largest_first" puts the big products first and leaves the small
@@ -25,6 +26,7 @@ from dataclasses import dataclass, field
 
 LEAVES = (16, 32, 64, 128)
 ORDERS = ("given", "largest_first")
+SLICES = (0, 16)          # sub-leaf cull along k: off, 16-wide slices (b >= 32)
 
 _CACHE: dict = {}
 
@@ -34,7 +36,8 @@ class Choice:
     leaf: int
     order: str
     ms: float
-    trials: dict = field(default_factory=dict)   # (leaf, order) -> ms
+    trials: dict = field(default_factory=dict)   # (leaf, order, slice) -> ms
+    slice: int = 0
 
     def permutation(self, ns):
         return order_of(self.order, ns)
@@ -53,24 +56,29 @@ def signature(ns, taus, precision: str):
             tuple(sorted(set(float(t) for t in taus))))
 
 
-def cached(ns, taus, precision: str):
-    return _CACHE.get(signature(ns, taus, precision))
+def cached(ns, taus, precision: str, leaves=LEAVES, orders=ORDERS, slices=SLICES):
+    return _CACHE.get(signature(ns, taus, precision) + (tuple(leaves), tuple(orders),
+                                                        tuple(slices)))
 
 
 def tune_batch(pairs, taus, precision: str = "tf32x3", leaves=LEAVES, orders=ORDERS,
-               reps: int = 3, use_cache: bool = True) -> Choice:
-    """Pick (leaf, order) for the batch of products ``pairs`` = [(A, B), ...]
-    (square float32 CUDA tensors) at thresholds ``taus``."""
+               slices=SLICES, reps: int = 3, use_cache: bool = True) -> Choice:
+    """Pick (leaf, order, sub-leaf cull) for the batch of products ``pairs``
+    = [(A, B), ...] (square float32 CUDA tensors) at thresholds ``taus``.
+    The sub-leaf cull changes the approximation (it drops more), so it is a
+    candidate only where the caller accepts that (``slices``)."""
     import torch
     from . import Context
     ns = [A.shape[0] for A, _ in pairs]
-    sig = signature(ns, taus, precision)
+    sig = signature(ns, taus, precision) + (tuple(leaves), tuple(orders), tuple(slices))
     if use_cache and sig in _CACHE:
         return _CACHE[sig]
     stream = torch.cuda.current_stream()
     trials = {}
-    for b in leaves:
-        ctx = Context(leaf=b, precision=precision, checked=True)
+    combos = [(b, sl) for b in leaves for sl in slices
+              if sl == 0 or (precision != "fp32" and b >= 32)]
+    for b, sl in combos:
+        ctx = Context(leaf=b, precision=precision, checked=True, slice=sl)
         trees_a, trees_b = [], []
         for A, B in pairs:
             ta = ctx.build_norms(A)
@@ -93,13 +101,13 @@ def tune_batch(pairs, taus, precision: str = "tf32x3", leaves=LEAVES, orders=ORD
             e1.record(stream)
             torch.cuda.synchronize()
             ctx.stats()                          # raises if a timed call failed
-            trials[(b, order)] = e0.elapsed_time(e1) / reps
+            trials[(b, order, sl)] = e0.elapsed_time(e1) / reps
         for t in trees_a + trees_b:
             t.close()
         del Cs
         ctx.close()
         torch.cuda.empty_cache()
-    (b, order), ms = min(trials.items(), key=lambda kv: kv[1])
-    choice = Choice(leaf=b, order=order, ms=ms, trials=trials)
+    (b, order, sl), ms = min(trials.items(), key=lambda kv: kv[1])
+    choice = Choice(leaf=b, order=order, ms=ms, trials=trials, slice=sl)
     _CACHE[sig] = choice
     return choice

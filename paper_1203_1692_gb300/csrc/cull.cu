@@ -51,7 +51,13 @@ struct CullProd {
     uint32_t* tile_fill;
     uint32_t* tile_off;
     uint32_t* tile_steps;
+    uint32_t* tile_iters;      // K-chunk iterations per tile (may be null)
+    const double* panA;        // panel norms of the sub-leaf cull (SL > 1)
+    const double* panB;
     int tt, tc, tiles, S;
+    int SL;                    // mask pairs per step: 1, or the 16-wide slices of a leaf
+    int chunks;                // 16-wide K-chunks per leaf (b / 16)
+    int nl;                    // leaves per side holding data
 };
 
 constexpr int kCullBatch = 64;
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(1024) k_group_scan(CullBatch<NB> cb) {
         ctl->ent_off = end;
         ctl->pk_off = end + (m + 1) / 2;
         ctl->pm_off = ctl->pk_off + (ms + 1) / 2;
-        ctl->need_words = ctl->pm_off + 2 * ms;
+        ctl->need_words = ctl->pm_off + 2 * ms * (unsigned long long)q.SL;
         if (ctl->need_words > q.cap || m >= 0xffffffffull / (unsigned long long)q.S)
             ctl->status |= ST_OVERFLOW;
     }
@@ -313,13 +319,19 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint
 // of K values are then compacted in ascending K.
 constexpr int kCullWarps = 8;
 
-template <int DS, int NB>
+// SL > 1: the sub-leaf cull along k.  Every leaf triple the cull keeps is
+// tested slice by slice with the panel norms (same FP64 condition), and a
+// step carries one mask pair per slice; a step none of whose slices
+// survives is not written.
+template <int DS, int NB, int SL>
 __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> cb) {
     constexpr int S = 1 << DS;               // K leaves per tier-tt K'
-    constexpr int WIN = 1024;                // steps per window (16 KB of masks)
+    constexpr int WIN = 1024 / SL;           // steps per window (16 KB of masks)
     constexpr int KPW = WIN / S;             // K' per window
     extern __shared__ uint32_t dyn[];        // K' bitmaps of both halves, then the K' list
-    __shared__ unsigned long long masks[WIN][2];
+    __shared__ unsigned long long masks[WIN][SL][2];
+    __shared__ unsigned long long st_slk, st_slt;
+    __shared__ uint32_t st_iters;
     // per-warp staged norms of one sub-cube: levels 1..DS, A side [x][k], B side [k][y]
     __shared__ double nA[kCullWarps][84], nB[kCullWarps][84];
     __shared__ uint32_t warp_sums[16], total_s;
@@ -337,7 +349,10 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
     const uint32_t u = (uint32_t)vb;
     const uint32_t e0 = off[u], e1 = off[u + 1];
     if (e0 == e1) {
-        if (threadIdx.x == 0) steps[u] = 0;
+        if (threadIdx.x == 0) {
+            steps[u] = 0;
+            if (q.tile_iters) q.tile_iters[u] = 0;
+        }
         return;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -351,7 +366,12 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
     uint32_t* klist = dyn + 2 * words;
     for (int w = tid; w < 2 * words; w += blockDim.x) dyn[w] = 0u;
     if (tid < 4) st_cand[tid] = st_kept[tid] = 0ull;
-    if (tid == 0) st_tie = 0ull;
+    if (tid == 0) {
+        st_tie = 0ull;
+        st_slk = st_slt = 0ull;
+        st_iters = 0u;
+    }
+    unsigned long long slk = 0, slt = 0;     // kept / tested slice products
     __syncthreads();
     for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
         const uint32_t v = ent[e], k = v >> 1;
@@ -433,13 +453,41 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                         tie += tb ? 1 : 0;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                    if (l == DS) {
+                    if (l == DS && SL > 1) {
+                        // leaf level with the sub-leaf cull: per slice, the
+                        // kept leaf triples whose panels pass, remapped to the
+                        // mask of leaf column K' * S + ki, bit yi * 8 + xi
+                        const int64_t I = ((int64_t)I0 << DS) + xi;
+                        const int64_t K = ((int64_t)Kp << DS) + ki;
+                        const int64_t J = ((int64_t)J0 << DS) + yi;
+#pragma unroll
+                        for (int sl = 0; sl < SL; ++sl) {
+                            bool oks = false;
+                            if (ok) {
+                                bool tb;
+                                oks = spamm_keep(q.panA[(I * q.nl + K) * SL + sl],
+                                                 q.panB[(K * SL + sl) * q.nl + J], th, &tb);
+                                tie += tb ? 1 : 0;
+                                slt += 1;
+                                slk += oks ? 1 : 0;
+                            }
+                            const unsigned long long bit = oks ? 1ull << (yi * 8 + xi) : 0ull;
+#pragma unroll
+                            for (int kq = 0; kq < S; ++kq) {
+                                const unsigned long long mine = (idx < per && ki == kq) ? bit : 0ull;
+                                const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)mine);
+                                const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(mine >> 32));
+                                if (r == 0 && lane == 0) masks[g * S + kq][sl][half] = 0ull;
+                                if (lane == 0) masks[g * S + kq][sl][half] |= ((unsigned long long)hi << 32) | lo;
+                            }
+                        }
+                    } else if (l == DS) {
                         // leaf level: the mask of leaf column K' * S + ki
                         if (DS == 3) {
                             const int kk = r >> 1;           // uniform across the warp
                             if (lane == 0) {
-                                if ((r & 1) == 0) masks[g * S + kk][half] = bal;
-                                else masks[g * S + kk][half] |= (unsigned long long)bal << 32;
+                                if ((r & 1) == 0) masks[g * S + kk][0][half] = bal;
+                                else masks[g * S + kk][0][half] |= (unsigned long long)bal << 32;
                             }
                         } else {
                             // remap bit (ki, yi, xi) -> mask of ki, bit yi * 8 + xi
@@ -449,8 +497,8 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                                 const unsigned long long mine = (idx < per && ki == kq) ? bit : 0ull;
                                 const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)mine);
                                 const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(mine >> 32));
-                                if (r == 0 && lane == 0) masks[g * S + kq][half] = 0ull;
-                                if (lane == 0) masks[g * S + kq][half] |= ((unsigned long long)hi << 32) | lo;
+                                if (r == 0 && lane == 0) masks[g * S + kq][0][half] = 0ull;
+                                if (lane == 0) masks[g * S + kq][0][half] |= ((unsigned long long)hi << 32) | lo;
                             }
                         }
                     } else if (l == 1) {
@@ -464,27 +512,51 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                 if (l == 2) lv2[1] = 0ull;
             }
             if (DS == 0) {
-                if (lane == 0) masks[g][half] = has ? 1ull : 0ull;
+                if (SL > 1) {
+                    // the tile node is the leaf: lane sl tests slice sl
+                    bool oks = false;
+                    if (lane < SL && has) {
+                        bool tb;
+                        oks = spamm_keep(q.panA[((int64_t)I0 * q.nl + Kp) * SL + lane],
+                                         q.panB[((int64_t)Kp * SL + lane) * q.nl + J0], th, &tb);
+                        tie += tb ? 1 : 0;
+                        slt += 1;
+                        slk += oks ? 1 : 0;
+                    }
+                    const unsigned bs = __ballot_sync(0xffffffffu, oks);
+                    if (lane == 0)
+                        for (int sl = 0; sl < SL; ++sl) masks[g][sl][half] = (bs >> sl) & 1u;
+                } else if (lane == 0) {
+                    masks[g][0][half] = has ? 1ull : 0ull;
+                }
             }
             __syncwarp();  // staged norms are reused by the next sub-cube
         }
         __syncthreads();
         // phase 2: ordered compaction of the window's masks (ascending K)
+        uint32_t it_mine = 0;
         for (int c0 = 0; c0 < kn * S; c0 += blockDim.x) {
             const int i = c0 + tid;
-            const unsigned long long m0 = i < kn * S ? masks[i][0] : 0ull;
-            const unsigned long long m1 = i < kn * S ? masks[i][1] : 0ull;
-            const bool any = (m0 | m1) != 0ull;
+            uint32_t live = 0;                   // slices with a kept product
+#pragma unroll
+            for (int sl = 0; sl < SL; ++sl)
+                if (i < kn * S && (masks[i][sl][0] | masks[i][sl][1]) != 0ull) live |= 1u << sl;
+            const bool any = live != 0u;
             const uint32_t r = block_excl_scan(any ? 1u : 0u, warp_sums, &total_s);
             if (any) {
                 const int g = i / S, kk = i % S;
                 const uint32_t pos = obase + written + r;
                 pk[pos] = klist[kw + g] * S + kk;
-                pm[2 * (size_t)pos] = m0;
-                pm[2 * (size_t)pos + 1] = m1;
+#pragma unroll
+                for (int sl = 0; sl < SL; ++sl) {
+                    pm[2 * ((size_t)pos * SL + sl)] = masks[i][sl][0];
+                    pm[2 * ((size_t)pos * SL + sl) + 1] = masks[i][sl][1];
+                }
+                it_mine += SL > 1 ? (uint32_t)__popc(live) : (uint32_t)q.chunks;
             }
             written += total_s;
         }
+        if (it_mine) atomicAdd(&st_iters, it_mine);
         __syncthreads();
     }
     // statistics of the tiers below the tile nodes
@@ -497,11 +569,24 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
         if (lane == 0 && cand[l]) atomicAdd(&st_cand[l], cand[l]);
         if (lane == 0 && kept[l]) atomicAdd(&st_kept[l], kept[l]);
     }
-    for (int o = 16; o > 0; o >>= 1) tie += __shfl_xor_sync(0xffffffffu, tie, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        tie += __shfl_xor_sync(0xffffffffu, tie, o);
+        slk += __shfl_xor_sync(0xffffffffu, slk, o);
+        slt += __shfl_xor_sync(0xffffffffu, slt, o);
+    }
     if (lane == 0 && tie) atomicAdd(&st_tie, tie);
+    if (lane == 0 && slt) {
+        atomicAdd(&st_slk, slk);
+        atomicAdd(&st_slt, slt);
+    }
     __syncthreads();
     if (tid == 0) {
         steps[u] = written;
+        if (q.tile_iters) q.tile_iters[u] = st_iters;
+        if (st_slt) {
+            atomicAdd(&ctl->slice_kept, st_slk);
+            atomicAdd(&ctl->slice_tested, st_slt);
+        }
         atomicAdd(&ctl->active_steps, (unsigned long long)written);
         for (int l = 0; l < DS; ++l) {
             atomicAdd(&ctl->tier_cand[tt + 1 + l], st_cand[l]);
@@ -607,13 +692,14 @@ static cudaError_t group_stage(const CullProd* prods, const std::vector<double>&
     if (e != cudaSuccess) return e;
     // tile cull, one launch per depth below the tile nodes (DS = d - tt)
     for (int ds = 0; ds <= 3; ++ds) {
+      for (int sl : {1, 2, 4, 8}) {
         CullBatch<NB> ct;
         memset(&ct, 0, sizeof(ct));
         std::vector<int> bl;
         size_t dsm = 0;
         for (int p = 0; p < count; ++p) {
             const int pds = prods[p].S == 1 ? 0 : prods[p].S == 2 ? 1 : prods[p].S == 4 ? 2 : 3;
-            if (pds != ds) continue;
+            if (pds != ds || prods[p].SL != sl) continue;
             ct.p[ct.count++] = prods[p];
             bl.push_back(prods[p].tiles);
             const int words = ((1 << prods[p].tt) + 31) / 32;
@@ -622,23 +708,39 @@ static cudaError_t group_stage(const CullProd* prods, const std::vector<double>&
         if (ct.count == 0) continue;
         nb = set_bases(ct, bl);
         if (nb == 0) continue;
-#define SPAMM_TC(DSV)                                                                         \
+#define SPAMM_TC(DSV, SLV)                                                                    \
     do {                                                                                      \
-        cudaFuncSetAttribute(k_tile_cull<DSV, NB>,                                            \
+        cudaFuncSetAttribute(k_tile_cull<DSV, NB, SLV>,                                       \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);          \
-        cudaFuncSetAttribute(k_tile_cull<DSV, NB>,                                            \
+        cudaFuncSetAttribute(k_tile_cull<DSV, NB, SLV>,                                       \
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);            \
-        k_tile_cull<DSV, NB><<<nb, kCullWarps * 32, dsm, s>>>(ct);                            \
+        k_tile_cull<DSV, NB, SLV><<<nb, kCullWarps * 32, dsm, s>>>(ct);                       \
     } while (0)
-        switch (ds) {
-            case 0: SPAMM_TC(0); break;
-            case 1: SPAMM_TC(1); break;
-            case 2: SPAMM_TC(2); break;
-            default: SPAMM_TC(3); break;
+        // leaf sizes: b = 16 (SL 1), 32 (SL 2), 64 (SL 4), 128 (SL 8); DS is
+        // log2(128 / b) except for products smaller than one tile
+        if (sl == 1) {
+            switch (ds) {
+                case 0: SPAMM_TC(0, 1); break;
+                case 1: SPAMM_TC(1, 1); break;
+                case 2: SPAMM_TC(2, 1); break;
+                default: SPAMM_TC(3, 1); break;
+            }
+        } else if (sl == 2) {
+            switch (ds) {
+                case 0: SPAMM_TC(0, 2); break;
+                case 1: SPAMM_TC(1, 2); break;
+                default: SPAMM_TC(2, 2); break;
+            }
+        } else if (sl == 4) {
+            if (ds == 0) SPAMM_TC(0, 4);
+            else SPAMM_TC(1, 4);
+        } else {
+            SPAMM_TC(0, 8);
         }
 #undef SPAMM_TC
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+      }
     }
     return cudaSuccess;
 }
@@ -656,10 +758,16 @@ static CullProd make_prod(spamm_ctx* c, const spamm_tree* A, const spamm_tree* B
     q.tile_fill = c->tile_fill;
     q.tile_off = c->tile_off;
     q.tile_steps = c->tile_steps;
+    q.tile_iters = c->tile_iters;
+    q.panA = A->panA;
+    q.panB = B->panB;
     q.tt = tt;
     q.tc = tile_cols(A);
     q.tiles = tile_rows(A) * q.tc;
     q.S = 1 << (A->d - tt);
+    q.SL = (A->slices && B->slices) ? A->slices : 1;
+    q.chunks = A->b / 16;
+    q.nl = (int)A->nl;
     return q;
 }
 

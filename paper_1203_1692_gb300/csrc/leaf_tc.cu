@@ -219,7 +219,9 @@ struct TcProd {
     const uint64_t* pool;
     const uint32_t* off;
     const uint32_t* steps;
+    const uint32_t* iters;  // K-chunk iterations per tile
     int tr, tc, S;
+    int sl;    // mask pairs per step: 1, or one per K-chunk (sub-leaf cull)
     int base;  // first work item (tile) of this product in the batch
 };
 
@@ -332,61 +334,100 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const int64_t scol = (int64_t)(u % q.tc) * TLC;
             const uint32_t ns = q.steps[u];
             const uint64_t sb = (uint64_t)q.off[u] * q.S;
-            uint32_t ck = lane < (int)ns ? pk[sb + lane] : 0u;
-            unsigned long long cm0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
-            unsigned long long cm1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
-            for (uint32_t base = 0; base < ns && ok; base += 32) {
-                const bool more = base + 32 + lane < ns;
-                const uint32_t nk = more ? pk[sb + base + 32 + lane] : 0u;
-                const unsigned long long nm0 = more ? pm[2 * (sb + base + 32 + lane)] : 0ull;
-                const unsigned long long nm1 = more ? pm[2 * (sb + base + 32 + lane) + 1] : 0ull;
-                const uint32_t cnt = ns - base < 32 ? ns - base : 32;
-                for (uint32_t j = 0; j < cnt && ok; ++j) {
-                    const int64_t K = __shfl_sync(0xffffffffu, ck, j);
-                    const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
-                    const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
-                    for (int kc = 0; kc < CHUNKS && ok; ++kc) {
-                        if (lane == 0) {
-                            if (fill == 0) {
-                                s = (int)(stage_it % ST);
-                                const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
-                                ok = wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status);
-                            }
-                            if (ok) {
-                                const uint32_t full = smem_u32(&bar_full[s]);
-                                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                             "r"((uint32_t)T::kIter)
-                                             : "memory");
-                                const int64_t row = (K * CHUNKS + kc) * q.nlp;
-                                unsigned char* slot = stages + (size_t)s * T::kStage +
-                                                      (size_t)fill * T::kIter;
+            // lane 0: one K-chunk slot into the current stage
+            auto issue = [&](int64_t K, int kc, unsigned long long m0, unsigned long long m1) {
+                if (fill == 0) {
+                    s = (int)(stage_it % ST);
+                    const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
+                    ok = wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status);
+                }
+                if (!ok) return;
+                const uint32_t full = smem_u32(&bar_full[s]);
+                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
+                             "r"((uint32_t)T::kIter)
+                             : "memory");
+                const int64_t row = (K * CHUNKS + kc) * q.nlp;
+                unsigned char* slot = stages + (size_t)s * T::kStage + (size_t)fill * T::kIter;
 #pragma unroll
-                                for (int part = 0; part < T::kParts; ++part) {
-                                    bulk_g2s(smem_u32(slot + part * T::kSlice),
-                                             static_cast<const unsigned char*>(q.pa[part]) +
-                                                 (size_t)(row + srow) * piece,
-                                             T::kSlice, full);
-                                    bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
-                                             static_cast<const unsigned char*>(q.pb[part]) +
-                                                 (size_t)(row + scol) * piece,
-                                             2 * T::kSlice, full);
-                                }
-                                st_mask[s][fill][0] = m0;
-                                st_mask[s][fill][1] = m1;
-                                if (++fill == T::kSPS) {
-                                    st_count[s] = (uint32_t)fill;
-                                    mbar_arrive(full);
-                                    issued_s = ++stage_it;
-                                    fill = 0;
-                                }
-                            }
+                for (int part = 0; part < T::kParts; ++part) {
+                    bulk_g2s(smem_u32(slot + part * T::kSlice),
+                             static_cast<const unsigned char*>(q.pa[part]) +
+                                 (size_t)(row + srow) * piece,
+                             T::kSlice, full);
+                    bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
+                             static_cast<const unsigned char*>(q.pb[part]) +
+                                 (size_t)(row + scol) * piece,
+                             2 * T::kSlice, full);
+                }
+                st_mask[s][fill][0] = m0;
+                st_mask[s][fill][1] = m1;
+                if (++fill == T::kSPS) {
+                    st_count[s] = (uint32_t)fill;
+                    mbar_arrive(full);
+                    issued_s = ++stage_it;
+                    fill = 0;
+                }
+            };
+            if (q.sl == 1) {
+                // one mask pair per step, shared by its K-chunks
+                uint32_t ck = lane < (int)ns ? pk[sb + lane] : 0u;
+                unsigned long long cm0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
+                unsigned long long cm1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
+                for (uint32_t base = 0; base < ns && ok; base += 32) {
+                    const bool more = base + 32 + lane < ns;
+                    const uint32_t nk = more ? pk[sb + base + 32 + lane] : 0u;
+                    const unsigned long long nm0 = more ? pm[2 * (sb + base + 32 + lane)] : 0ull;
+                    const unsigned long long nm1 = more ? pm[2 * (sb + base + 32 + lane) + 1] : 0ull;
+                    const uint32_t cnt = ns - base < 32 ? ns - base : 32;
+                    for (uint32_t j = 0; j < cnt && ok; ++j) {
+                        const int64_t K = __shfl_sync(0xffffffffu, ck, j);
+                        const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
+                        const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
+                        for (int kc = 0; kc < CHUNKS && ok; ++kc) {
+                            if (lane == 0) issue(K, kc, m0, m1);
+                            ok = __shfl_sync(0xffffffffu, ok, 0);
                         }
+                    }
+                    ck = nk;
+                    cm0 = nm0;
+                    cm1 = nm1;
+                }
+            } else {
+                // sub-leaf cull: a mask pair per (step, K-chunk); chunks whose
+                // slice products were all culled are not loaded at all
+                const uint32_t nit = ns * CHUNKS;
+                auto ld = [&](uint32_t it, uint32_t& kk, unsigned long long& a,
+                              unsigned long long& b) {
+                    if (it < nit) {
+                        const uint64_t st = sb + it / CHUNKS;
+                        kk = pk[st];
+                        a = pm[2 * (st * CHUNKS + it % CHUNKS)];
+                        b = pm[2 * (st * CHUNKS + it % CHUNKS) + 1];
+                    } else {
+                        kk = 0u;
+                        a = b = 0ull;
+                    }
+                };
+                uint32_t ck;
+                unsigned long long cm0, cm1;
+                ld(lane, ck, cm0, cm1);
+                for (uint32_t base = 0; base < nit && ok; base += 32) {
+                    uint32_t nk;
+                    unsigned long long nm0, nm1;
+                    ld(base + 32 + lane, nk, nm0, nm1);
+                    const uint32_t cnt = nit - base < 32 ? nit - base : 32;
+                    for (uint32_t j = 0; j < cnt && ok; ++j) {
+                        const int64_t K = __shfl_sync(0xffffffffu, ck, j);
+                        const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
+                        const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
+                        if ((m0 | m1) == 0ull) continue;
+                        if (lane == 0) issue(K, (int)((base + j) % CHUNKS), m0, m1);
                         ok = __shfl_sync(0xffffffffu, ok, 0);
                     }
+                    ck = nk;
+                    cm0 = nm0;
+                    cm1 = nm1;
                 }
-                ck = nk;
-                cm0 = nm0;
-                cm1 = nm1;
             }
             // a stage never spans two tiles
             if (lane == 0 && fill > 0) {
@@ -399,9 +440,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA
         // Lane 0 alone: per stage one wait and one commit.  Iteration i of a
-        // tile (step i / CHUNKS, K-chunk i % CHUNKS) opens a new TMEM chunk
-        // when i % kChunkIters == 0 and closes it at the chunk's last
-        // iteration; a tile without steps is skipped (no chunk).
+        // tile (its i-th loaded K-chunk: every chunk of every step, or with
+        // the sub-leaf cull every chunk with a kept slice product) opens a
+        // new TMEM chunk when i % kChunkIters == 0 and closes it at the
+        // chunk's last iteration; a tile without steps is skipped.
         if (lane == 0) {
             unsigned long long stage_it = 0;
             uint32_t ccount = 0;  // chunks opened so far (selects the TMEM buffer)
@@ -414,8 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 product_of(k, pi);
                 if (sp_skip[pi]) continue;
                 const TcProd& q = bt.prods[pi];
-                const uint32_t ns = q.steps[tile_at(k - q.base, q.tr, q.tc)];
-                const uint32_t iters = ns * CHUNKS;
+                const uint32_t iters = q.iters[tile_at(k - q.base, q.tr, q.tc)];
                 if (iters == 0) continue;
                 uint32_t i = 0;
                 while (i < iters && ok) {
@@ -556,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             if (sp_skip[pi]) continue;
             const TcProd& q = bt.prods[pi];
             const int u = tile_at(k - q.base, q.tr, q.tc);
-            const uint32_t nch = chunks_of(q.steps[u] * CHUNKS);
+            const uint32_t nch = chunks_of(q.iters[u]);
             if (nch == 0) {
                 // no kept product: C = alpha * 0 + beta * C, written row-wise by
                 // the 256 epilogue threads (a warp stores 512 contiguous bytes)
@@ -715,6 +756,8 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
             q.pool = jb.sub->pool;
             q.off = jb.sub->tile_off;
             q.steps = jb.sub->tile_steps;
+            q.iters = jb.sub->tile_iters;
+            q.sl = (jb.A->slices && jb.B->slices) ? jb.A->slices : 1;
             q.tr = tile_rows(jb.A);
             q.tc = tile_cols(jb.A);
             q.S = jb.sub->last_S;

@@ -122,10 +122,18 @@ struct SqAcc {
     }
 };
 
-template <int LEAF, bool VEC>
+// PAN: also the panel norms of the sub-leaf cull along k (16-wide slices):
+// panA[(I nl + K) SL + s] over the b rows of leaf I and the 16 columns of
+// slice s of leaf K (the four lanes of a 16-column group), and
+// panB[(I SL + s) nl + K] over the 16 rows of slice s of leaf I and the b
+// columns of leaf K (a partial per 16 rows, then all the lanes of the leaf).
+template <int LEAF, bool VEC, bool PAN>
 __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A, int64_t n,
                                                     int64_t lda, int64_t nb, int64_t nl,
-                                                    double* __restrict__ leaf) {
+                                                    double* __restrict__ leaf,
+                                                    double* __restrict__ panA,
+                                                    double* __restrict__ panB) {
+    constexpr int SL = PAN ? LEAF / 16 : 1;              // 16-row groups tracked
     const int64_t I = blockIdx.y;                       // leaf row
     const int64_t col0 = (int64_t)blockIdx.x * 512 + 4 * threadIdx.x;
     const int64_t K = col0 / LEAF;                       // leaf column
@@ -133,6 +141,15 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
     const int64_t r0 = I * LEAF;
     const float* base = A + r0 * lda + col0;
     SqAcc acc;
+    double rp[SL];                                       // per 16-row group (PAN)
+#pragma unroll
+    for (int q = 0; q < SL; ++q) rp[q] = 0.0;
+    auto group_done = [&](int r) {                       // after row r (0-based)
+        if (PAN && (r & 15) == 15) {
+            rp[r >> 4] = acc.sum;
+            acc.sum = 0.0;
+        }
+    };
     if (VEC && col0 + 3 < n && r0 + LEAF <= n) {
         for (int r8 = 0; r8 < LEAF; r8 += 8) {
             float4 v[8];
@@ -142,9 +159,11 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc.add4(v[q]);
             acc.fold();
+            group_done(r8 + 7);
         }
     } else {
-        for (int r = 0; r < LEAF; ++r) {
+        int r = 0;
+        for (; r < LEAF; ++r) {
             if (r0 + r >= n) break;
             const float* p = base + (int64_t)r * lda;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -154,11 +173,43 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
             if (col0 + 3 < n) v.w = __ldg(p + 3);
             acc.add4(v);
             if ((r & 7) == 7) acc.fold();
+            group_done(r);
+        }
+        if (PAN && (r & 15) != 0 && r < LEAF) {          // rows ran out mid-group
+            acc.fold();
+            rp[r >> 4] = acc.sum;
+            acc.sum = 0.0;
         }
     }
-    double s = acc.result();
-    // segmented reduction over the lanes of one leaf
-    for (int off = lanes >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    double s;
+    if (PAN) {
+        s = 0.0;
+#pragma unroll
+        for (int q = 0; q < SL; ++q) s += rp[q];
+        if (acc.bad) s = __longlong_as_double(0x7ff8000000000000ll);
+        // A-role panel: the four lanes of this 16-column group
+        double pa = s;
+        pa += __shfl_xor_sync(0xffffffffu, pa, 1);
+        pa += __shfl_xor_sync(0xffffffffu, pa, 2);
+        if ((threadIdx.x & 3) == 0 && K < nl)
+            panA[((int64_t)I * nl + K) * SL + (int)((col0 % LEAF) >> 4)] = pa;
+        // B-role panels: every 16-row group over all lanes of the leaf
+#pragma unroll
+        for (int q = 0; q < SL; ++q) {
+            double pb = acc.bad ? __longlong_as_double(0x7ff8000000000000ll) : rp[q];
+            for (int off = lanes >> 1; off > 0; off >>= 1)
+                pb += __shfl_xor_sync(0xffffffffu, pb, off);
+            if ((threadIdx.x & (lanes - 1)) == 0 && K < nl)
+                panB[((int64_t)I * SL + q) * nl + K] = pb;
+        }
+        // leaf norm: the 16-column sums over the remaining lanes
+        s = pa;
+        for (int off = 4; off < lanes; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    } else {
+        s = acc.result();
+        // segmented reduction over the lanes of one leaf
+        for (int off = lanes >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    }
     if ((threadIdx.x & (lanes - 1)) == 0 && K < nl) leaf[I * nb + K] = s;
 }
 
@@ -403,12 +454,23 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const bool vec = ((reinterpret_cast<uintptr_t>(t->A) & 15) == 0) && (t->lda % 4 == 0);
     dim3 grid((unsigned)((t->nl * t->b + 511) / 512), (unsigned)t->nl);
-#define SPAMM_LN(LV)                                                                          \
-    do {                                                                                      \
-        if (vec)                                                                              \
-            k_leaf_norms<LV, true><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, leaf); \
-        else                                                                                  \
-            k_leaf_norms<LV, false><<<grid, 128, 0, s>>>(t->A, t->n, t->lda, t->nb, t->nl, leaf); \
+#define SPAMM_LN(LV)                                                                         \
+    do {                                                                                     \
+        if (t->slices) {                                                                     \
+            if (vec)                                                                         \
+                k_leaf_norms<LV, true, true><<<grid, 128, 0, s>>>(                           \
+                    t->A, t->n, t->lda, t->nb, t->nl, leaf, t->panA, t->panB);               \
+            else                                                                             \
+                k_leaf_norms<LV, false, true><<<grid, 128, 0, s>>>(                          \
+                    t->A, t->n, t->lda, t->nb, t->nl, leaf, t->panA, t->panB);               \
+        } else {                                                                             \
+            if (vec)                                                                         \
+                k_leaf_norms<LV, true, false><<<grid, 128, 0, s>>>(                          \
+                    t->A, t->n, t->lda, t->nb, t->nl, leaf, nullptr, nullptr);               \
+            else                                                                             \
+                k_leaf_norms<LV, false, false><<<grid, 128, 0, s>>>(                         \
+                    t->A, t->n, t->lda, t->nb, t->nl, leaf, nullptr, nullptr);               \
+        }                                                                                    \
     } while (0)
     if (t->b == 16) SPAMM_LN(16);
     else if (t->b == 32) SPAMM_LN(32);

@@ -74,13 +74,15 @@ spamm_status ensure_tiles(spamm_ctx* ctx, int64_t tiles) {
     cudaFree(ctx->tile_fill);
     cudaFree(ctx->tile_off);
     cudaFree(ctx->tile_steps);
-    ctx->tile_cnt = ctx->tile_fill = ctx->tile_off = ctx->tile_steps = nullptr;
+    cudaFree(ctx->tile_iters);
+    ctx->tile_cnt = ctx->tile_fill = ctx->tile_off = ctx->tile_steps = ctx->tile_iters = nullptr;
     ctx->tiles_cap = 0;
     const int64_t cap = std::max<int64_t>(tiles, 1024);
     cudaError_t e = cudaMalloc(&ctx->tile_cnt, sizeof(uint32_t) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_fill, sizeof(uint32_t) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_off, sizeof(uint32_t) * (cap + 1));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_steps, sizeof(uint32_t) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tile_iters, sizeof(uint32_t) * cap);
     if (e != cudaSuccess) return cuda_err(ctx, e, "tile arrays");
     ctx->tiles_cap = cap;
     return SPAMM_OK;
@@ -101,6 +103,9 @@ spamm_status ensure_need(spamm_ctx* ctx, int64_t nb) {
 
 void free_tree_storage(spamm_tree* t) {
     cudaFree(t->pyr);
+    cudaFree(t->panA);
+    cudaFree(t->panB);
+    t->panA = t->panB = nullptr;
     for (int i = 0; i < 2; ++i) {
         cudaFree(t->packA[i]);
         cudaFree(t->packB[i]);
@@ -118,13 +123,16 @@ spamm_status check_matrix(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda
 
 // Pool words a multiply needs: the frontiers of tiers 0..tt, then one u32
 // entry per tier-tt triple and S steps (u32 K + two u64 masks) per entry.
-int64_t words_needed(const DevCtl& c, int tt, int S) {
+int64_t words_needed(const DevCtl& c, int tt, int S, int SL) {
     unsigned long long s = 0;
     for (int t = 0; t <= tt; ++t) s += c.tier_count[t];
     const unsigned long long m = c.tier_count[tt];
     const unsigned long long ms = m * (unsigned long long)S;
-    return (int64_t)(s + (m + 1) / 2 + (ms + 1) / 2 + 2 * ms);
+    return (int64_t)(s + (m + 1) / 2 + (ms + 1) / 2 + 2 * ms * (unsigned long long)SL);
 }
+
+// Mask pairs per step: one, or one per 16-wide k-slice with the sub-leaf cull.
+int slices_of(const spamm_ctx* ctx, int b) { return ctx->cfg.slice ? b / 16 : 1; }
 
 }  // namespace
 
@@ -148,8 +156,10 @@ spamm_status spamm_create(spamm_ctx** out, void* stream, const spamm_config* cfg
     if (!valid_leaf(c.leaf)) return SPAMM_ERR_INVALID_ARG;
     if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_BF16X3) return SPAMM_ERR_INVALID_ARG;
     if (!(c.tie_rel >= 0.0 && c.tie_rel < 0.5) || c.pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (c.reserved[i]) return SPAMM_ERR_INVALID_ARG;
+    if (c.slice != 0 && c.slice != 16) return SPAMM_ERR_INVALID_ARG;
+    if (c.slice && (!precision_uses_tc(c.precision) || c.leaf < 32)) return SPAMM_ERR_UNSUPPORTED;
     spamm_ctx* ctx = new (std::nothrow) spamm_ctx();
     if (!ctx) return SPAMM_ERR_OOM;
     ctx->stream = (cudaStream_t)stream;
@@ -194,6 +204,7 @@ spamm_status spamm_destroy(spamm_ctx* ctx) {
     cudaFree(ctx->tile_fill);
     cudaFree(ctx->tile_off);
     cudaFree(ctx->tile_steps);
+    cudaFree(ctx->tile_iters);
     cudaFree(ctx->need);
     cudaFree(ctx->dA);
     cudaFree(ctx->dB);
@@ -257,7 +268,6 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
     spamm_tree* t = new (std::nothrow) spamm_tree();
     if (!t) return SPAMM_ERR_OOM;
     t->ctx = ctx;
-    ctx->trees.push_back(t);
     t->A = A;
     t->n = n;
     t->lda = lda;
@@ -268,7 +278,13 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
     t->nlp = (nl + 2 * tl - 1) / (2 * tl) * (2 * tl);
     t->nodes = (((int64_t)1 << (2 * (d + 1))) - 1) / 3;
     t->precision = ctx->cfg.precision;
+    t->slices = ctx->cfg.slice ? b / ctx->cfg.slice : 0;
     cudaError_t e = cudaMalloc(&t->pyr, sizeof(double) * t->nodes);
+    if (e == cudaSuccess && t->slices) {
+        const size_t pn = sizeof(double) * (size_t)nl * (size_t)nl * (size_t)t->slices;
+        e = cudaMalloc(&t->panA, pn);
+        if (e == cudaSuccess) e = cudaMalloc(&t->panB, pn);
+    }
     if (e == cudaSuccess && precision_uses_tc(t->precision)) {
         t->pack_bytes = pack_bytes_for(t->precision, t->nlp, b);
         const int arrays = pack_arrays_for(t->precision);
@@ -292,6 +308,7 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
         delete t;
         return st;
     }
+    ctx->trees.push_back(t);
     *out = t;
     return SPAMM_OK;
 }
@@ -332,6 +349,7 @@ spamm_status spamm_tree_footprint(const spamm_ctx* ctx, int64_t n, int64_t* byte
     if (precision_uses_tc(ctx->cfg.precision))
         total += 2 * (int64_t)pack_arrays_for(ctx->cfg.precision) *
                  (int64_t)pack_bytes_for(ctx->cfg.precision, nlp, b);
+    if (ctx->cfg.slice) total += 2 * (int64_t)sizeof(double) * nl * nl * (b / ctx->cfg.slice);
     *bytes = total;
     return SPAMM_OK;
 }
@@ -426,7 +444,7 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
         if (e != cudaSuccess) return (spamm_status)(ctx->last_status = cuda_err(ctx, e, "multiply"));
         const DevCtl& c = *ctx->ctl_host;
         if ((c.status & ST_OVERFLOW) && !(c.status & (ST_NONFINITE | ST_TIMEOUT)) && attempt < 8) {
-            const int64_t need = std::max<int64_t>(words_needed(c, ctx->last_tt, ctx->last_S),
+            const int64_t need = std::max<int64_t>(words_needed(c, ctx->last_tt, ctx->last_S, slices_of(ctx, ctx->last_b)),
                                                    2 * ctx->pool_words);
             st = alloc_pool(ctx, need * 8 + need * 2);  // 25% headroom
             if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
@@ -461,9 +479,13 @@ spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     out->tiles = ctx->last_tiles;
     const double b = ctx->last_b;
     out->kept_flops = 2.0 * b * b * b * (double)out->leaf_triples;
+    out->slice = ctx->cfg.slice;
+    out->slice_kept = (int64_t)c.slice_kept;
+    out->slice_tested = (int64_t)c.slice_tested;
+    if (ctx->cfg.slice) out->kept_flops = 2.0 * b * b * ctx->cfg.slice * (double)c.slice_kept;
     out->dense_flops = 2.0 * (double)ctx->last_n * (double)ctx->last_n * (double)ctx->last_n;
     out->pool_bytes = ctx->pool_words * 8;
-    out->pool_needed_bytes = words_needed(c, ctx->last_tt, ctx->last_S) * 8;
+    out->pool_needed_bytes = words_needed(c, ctx->last_tt, ctx->last_S, slices_of(ctx, ctx->last_b)) * 8;
     if (ctx->timed) {
         cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&out->ms_pack, ctx->ev[1], ctx->ev[3]);
@@ -485,19 +507,22 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     const DevCtl& c = *ctx->ctl_host;
     const int d = ctx->last_d;
     const int64_t m = (int64_t)c.tier_count[d];
+    const int SL = slices_of(ctx, ctx->last_b);
     *count = m;
     if (c.status & (ST_OVERFLOW | ST_NONFINITE)) {
         *count = 0;
         return status_from_ctl_pub(ctx, c);
     }
-    if (cap <= 0 || m == 0) return SPAMM_OK;
-    // expand the tile-compressed steps (K, mask) into (I, K, J) rows
+    if ((cap <= 0 && SL == 1) || m == 0) return SPAMM_OK;
+    // expand the tile-compressed steps (K, mask) into (I, K, J) rows; with the
+    // sub-leaf cull, a leaf triple is listed if any of its k-slices is kept
+    // (the count is then exact only after the expansion)
     const int64_t tiles = ctx->last_tiles;
     const int tc = ctx->last_tc;
     const int tl = kTileRows / ctx->last_b;
     const uint64_t msteps = (uint64_t)c.tier_count[ctx->last_tt] * ctx->last_S;
     std::vector<uint32_t> off((size_t)tiles + 1), nst((size_t)tiles), pk((size_t)msteps);
-    std::vector<uint64_t> pm((size_t)(2 * msteps));
+    std::vector<uint64_t> pm((size_t)(2 * msteps * SL));
     e = cudaMemcpy(off.data(), ctx->tile_off, sizeof(uint32_t) * (tiles + 1), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
         e = cudaMemcpy(nst.data(), ctx->tile_steps, sizeof(uint32_t) * tiles, cudaMemcpyDeviceToHost);
@@ -505,26 +530,31 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
         e = cudaMemcpy(pk.data(), reinterpret_cast<uint32_t*>(ctx->pool + c.pk_off),
                        sizeof(uint32_t) * msteps, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && msteps)
-        e = cudaMemcpy(pm.data(), ctx->pool + c.pm_off, sizeof(uint64_t) * 2 * msteps,
+        e = cudaMemcpy(pm.data(), ctx->pool + c.pm_off, sizeof(uint64_t) * 2 * msteps * SL,
                        cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(ctx, e, "triples copy");
     int64_t k = 0;
-    for (int64_t u = 0; u < tiles && k < cap; ++u) {
+    for (int64_t u = 0; u < tiles; ++u) {
         const uint64_t base = (uint64_t)off[u] * ctx->last_S;
-        for (uint32_t q = 0; q < nst[u] && k < cap; ++q) {
+        for (uint32_t q = 0; q < nst[u]; ++q) {
             for (int h = 0; h < kTileHalves; ++h) {
-                uint64_t mk = pm[2 * (base + q) + h];
-                while (mk && k < cap) {
+                uint64_t mk = 0;
+                for (int sl = 0; sl < SL; ++sl) mk |= pm[2 * ((base + q) * SL + sl) + h];
+                while (mk) {
                     const int bit = __builtin_ctzll(mk);
                     mk &= mk - 1;
-                    host_out[3 * k + 0] = (int32_t)((u / tc) * tl + (bit & 7));
-                    host_out[3 * k + 1] = (int32_t)pk[base + q];
-                    host_out[3 * k + 2] = (int32_t)(((u % tc) * kTileHalves + h) * tl + (bit >> 3));
+                    if (k < cap) {
+                        host_out[3 * k + 0] = (int32_t)((u / tc) * tl + (bit & 7));
+                        host_out[3 * k + 1] = (int32_t)pk[base + q];
+                        host_out[3 * k + 2] =
+                            (int32_t)(((u % tc) * kTileHalves + h) * tl + (bit >> 3));
+                    }
                     ++k;
                 }
             }
         }
     }
+    *count = k;
     return SPAMM_OK;
 }
 
@@ -718,7 +748,7 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
             if (c.status & (ST_NONFINITE | ST_TIMEOUT))
                 return (spamm_status)(ctx->last_status = status_of(ctx, c));
             if (c.status & ST_OVERFLOW) {
-                const int64_t need = std::max<int64_t>(words_needed(c, sub->last_tt, sub->last_S),
+                const int64_t need = std::max<int64_t>(words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)),
                                                        2 * sub->pool_words);
                 const spamm_status st = alloc_pool(sub, need * 8 + need * 2);
                 if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
@@ -758,9 +788,13 @@ spamm_status spamm_stats_item(spamm_ctx* ctx, int32_t index, spamm_stats_t* out)
     out->tiles = sub->last_tiles;
     const double b = sub->last_b;
     out->kept_flops = 2.0 * b * b * b * (double)out->leaf_triples;
+    out->slice = sub->cfg.slice;
+    out->slice_kept = (int64_t)c.slice_kept;
+    out->slice_tested = (int64_t)c.slice_tested;
+    if (sub->cfg.slice) out->kept_flops = 2.0 * b * b * sub->cfg.slice * (double)c.slice_kept;
     out->dense_flops = 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
     out->pool_bytes = sub->pool_words * 8;
-    out->pool_needed_bytes = words_needed(c, sub->last_tt, sub->last_S) * 8;
+    out->pool_needed_bytes = words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)) * 8;
     out->status = status_of(ctx, c);
     return (spamm_status)out->status;
 }
@@ -784,10 +818,14 @@ static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
         out->active_steps += (int64_t)c.active_steps;
         out->tiles += sub->last_tiles;
         const double b = sub->last_b;
-        out->kept_flops += 2.0 * b * b * b * (double)m;
+        out->kept_flops += sub->cfg.slice ? 2.0 * b * b * sub->cfg.slice * (double)c.slice_kept
+                                          : 2.0 * b * b * b * (double)m;
+        out->slice = sub->cfg.slice;
+        out->slice_kept += (int64_t)c.slice_kept;
+        out->slice_tested += (int64_t)c.slice_tested;
         out->dense_flops += 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
         out->pool_bytes += sub->pool_words * 8;
-        out->pool_needed_bytes += words_needed(c, sub->last_tt, sub->last_S) * 8;
+        out->pool_needed_bytes += words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)) * 8;
         const spamm_status st = status_of(ctx, c);
         if (worst == SPAMM_OK) worst = st;
     }

@@ -49,6 +49,8 @@ struct DevCtl {
     unsigned long long pk_off;      // u32 K of each (tile, K) step
     unsigned long long pm_off;      // two u64 masks (left, right half) of each step
     unsigned long long need_words;  // words the whole multiply needs
+    unsigned long long slice_kept;  // kept k-slice products (sub-leaf cull)
+    unsigned long long slice_tested;
     unsigned int status;
     unsigned int pad;
 };
@@ -120,6 +122,13 @@ struct spamm_tree {
     void* packA[2];    // hi, lo (lo only for split precisions)
     void* packB[2];
     size_t pack_bytes;  // bytes of one pack array
+    // sub-leaf cull along k: slices of 16 per leaf (b / 16) and the panel
+    // squared norms, A role [I][K][s] (rows of leaf I, columns of slice s of
+    // leaf K) and B role [K][s][J] (rows of slice s of leaf K, columns of
+    // leaf J), nl leaves per side; null when the cull is off
+    int slices;
+    double* panA;
+    double* panB;
 };
 
 struct spamm_ctx {
@@ -138,6 +147,7 @@ struct spamm_ctx {
     uint32_t* tile_fill;
     uint32_t* tile_off;   // exclusive scan, tiles + 1
     uint32_t* tile_steps; // (tile, K) steps per tile
+    uint32_t* tile_iters; // K-chunk iterations per tile (steps x chunks kept)
     uint32_t* work_ctr;   // persistent-kernel work counter
     int64_t tiles_cap;
     // per-K norm maxima for the packs of a multiply (2 x leaves per side)

@@ -85,3 +85,16 @@ def test_kernels_target_sm103a(libpath):
     the binary itself is not inspected)."""
     from paper_1203_1692_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_slice_cull_config_is_validated_before_the_gpu(libpath):
+    from paper_1203_1692_gb300 import _abi
+    L = _abi.lib()
+    h = ctypes.c_void_p()
+    for leaf, prec, sl, want in [(64, _abi.SPAMM_PREC_FP32, 16, _abi.SPAMM_ERR_UNSUPPORTED),
+                                 (16, _abi.SPAMM_PREC_TF32X3, 16, _abi.SPAMM_ERR_UNSUPPORTED),
+                                 (64, _abi.SPAMM_PREC_TF32X3, 8, _abi.SPAMM_ERR_INVALID_ARG),
+                                 (64, _abi.SPAMM_PREC_TF32X3, 32, _abi.SPAMM_ERR_INVALID_ARG)]:
+        c = _abi.spamm_config_default()
+        c.leaf, c.precision, c.slice = leaf, prec, sl
+        assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == want

@@ -146,3 +146,65 @@ def test_tc_stale_pieces_never_reach_C(prec, b):
     ctx.multiply(tree, tb, 1e-4, C=C)
     ref = O.multiply(A, Bm, b, 1e-4)
     assert rel_max_err(C.cpu().numpy(), ref.C) <= TOL[prec]
+
+
+SLICE_CASES = [
+    (640, 64, "exp", 1e-5),
+    (530, 32, "alg", 1e-6),        # ragged
+    (450, 128, "exp", 1e-4),
+    (300, 64, "dense", 0.0),       # tau = 0: every non-zero panel kept
+    (1000, 64, "water", 1e-3),
+]
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("n,b,kind,tau", SLICE_CASES)
+def test_slice_cull_parity_with_oracle(prec, n, b, kind, tau):
+    """Sub-leaf cull along k (16-wide slices of each kept leaf product,
+    the paper's SpAMM(4x4) read for tensor cores) against the oracle's
+    sliced product: C within the precision's tolerance, the same leaf
+    triples and the same number of kept slice products outside ties."""
+    import paper_1203_1692_gb300 as P
+    A = _matrix(kind, n)
+    B = _matrix("exp", n, seed=1) if kind == "dense" else A
+    ctx = P.Context(leaf=b, precision=prec, slice=16)
+    ta = ctx.build_norms(torch.from_numpy(A).cuda())
+    tb = ta if B is A else ctx.build_norms(torch.from_numpy(B).cuda())
+    C = ctx.multiply(ta, tb, tau)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    refC, m, kept, tested = O.multiply_sliced(A, B, b, 16, tau)
+    assert rel_max_err(C.cpu().numpy(), refC) <= TOL[prec]
+    if st["tie_band"] == 0:
+        assert st["leaf_triples"] == m
+        assert st["slice_tested"] == tested and st["slice_kept"] == kept
+    else:
+        assert abs(st["slice_kept"] - kept) <= st["tie_band"]
+    assert st["kept_flops"] == 2.0 * b * b * 16 * st["slice_kept"]
+
+
+def test_slice_cull_matches_plain_when_nothing_is_culled_inside_leaves():
+    """At tau = 0 every slice with two non-zero panels is kept, so the
+    sliced product equals the plain one (same accumulation order)."""
+    import paper_1203_1692_gb300 as P
+    A = _matrix("exp", 512)
+    dA = torch.from_numpy(A).cuda()
+    out = []
+    for sl in (0, 16):
+        ctx = P.Context(leaf=64, precision="tf32x3", slice=sl)
+        t = ctx.build_norms(dA)
+        out.append(ctx.multiply(t, t, 0.0).cpu().numpy())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_slice_cull_batched_equals_single():
+    import paper_1203_1692_gb300 as P
+    mats = [_matrix("exp", n, seed=n) for n in (300, 700, 1000)]
+    ctx = P.Context(leaf=64, precision="tf32x3", slice=16)
+    dm = [torch.from_numpy(A).cuda() for A in mats]
+    trees = [ctx.build_norms(A) for A in dm]
+    Cs = ctx.multiply_batched(trees, trees, [1e-5, 1e-4, 1e-6])
+    for A, t, C, tau in zip(dm, trees, Cs, [1e-5, 1e-4, 1e-6]):
+        c1 = P.Context(leaf=64, precision="tf32x3", slice=16)
+        t1 = c1.build_norms(A)
+        assert torch.equal(c1.multiply(t1, t1, tau), C)
