@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--alt", default="bf16x3",
                    help="also time this leaf precision on the same workload ('' = off)")
     p.add_argument("--slice", type=int, default=0, help="sub-leaf cull along k (16) or off (0)")
+    p.add_argument("--flat", action="store_true",
+                   help="quick mode: also time the flat, norm-sorted enumeration (Algorithm 1)")
     p.add_argument("--quick", action="store_true",
                    help="time the SpAMM step only at a fixed --tau (for profiling)")
     return p.parse_args()
@@ -274,7 +276,12 @@ def run_quick(args, P, A, n, b, stream):
     torch.cuda.synchronize()
     st = ctx.stats()
     ms = e0.elapsed_time(e1) / args.steps
+    flat = None
+    if args.flat and tree.handle is not None:
+        _, cnt, fms = ctx.cull_flat(tree, tree, tau, triples=False)
+        flat = {"triples": cnt, "ms": fms}
     print(json.dumps({"mode": "quick", "n": n, "leaf": b, "tau": tau, "slice": args.slice,
+                      "flat_enumeration": flat,
                       "slice_kept": st["slice_kept"], "slice_tested": st["slice_tested"],
                       "precision": args.precision, "ms_per_step": ms,
                       "kept_tflops": st["kept_flops"] / (ms * 1e-3) / 1e12,

@@ -223,6 +223,21 @@ spamm_status spamm_multiply_batched(spamm_ctx *ctx, int32_t count, const spamm_t
                                     const float *alpha, const float *beta, float *const *C,
                                     const int64_t *ldc);
 
+/* The paper's flat enumeration of the leaf triples (Sec. III.D.2, Algorithm
+ * 1) on the GPU: per leaf column K the leaves of A (column K) and of B (row
+ * K) sorted by descending norm, and for each A leaf the prefix of B leaves
+ * whose norm product passes the SpAMM condition (the early exit).  It
+ * returns the same set as the hierarchical cull of spamm_multiply (a
+ * parent's norm is never below its children's), as an alternative cull and
+ * a cross-check.  Trees as for spamm_multiply; at most 2048 leaves per
+ * side (UNSUPPORTED beyond).  host_out receives min(count, cap) rows (I, K,
+ * J) sorted by (I, J, K); *count the number of triples; *ms (may be NULL)
+ * the device time of the enumeration.  Synchronises.  INVALID_ARG,
+ * NONFINITE, UNSUPPORTED, OOM, CUDA. */
+spamm_status spamm_cull_flat(spamm_ctx *ctx, const spamm_tree *A, const spamm_tree *B,
+                             double tau, int32_t *host_out, int64_t cap, int64_t *count,
+                             float *ms);
+
 /* Statistics of product `index` of the last spamm_multiply_batched on ctx
  * (same fields as spamm_stats, without the timings).  Synchronises.
  * INVALID_ARG (no such product), or the product's own status. */

@@ -199,6 +199,18 @@ class Context:
         """Kept flops of each product of the last batched multiply."""
         return [spamm_stats_item(self.handle, p).kept_flops for p in range(count)]
 
+    def cull_flat(self, A: Tree, B: Tree, tau: float, triples: bool = True):
+        """The flat, norm-sorted enumeration (Algorithm 1) on the GPU:
+        (rows (I, K, J) sorted by (I, J, K) or None, count, device ms)."""
+        if not triples:
+            cnt, ms = _abi.spamm_cull_flat(self.handle, A.handle, B.handle, tau, 0, 0)
+            return None, cnt, ms
+        cnt, _ = _abi.spamm_cull_flat(self.handle, A.handle, B.handle, tau, 0, 0)
+        out = np.empty((max(cnt, 1), 3), dtype=np.int32)
+        cnt, ms = _abi.spamm_cull_flat(self.handle, A.handle, B.handle, tau, out.ctypes.data,
+                                       cnt)
+        return out[:cnt], cnt, ms
+
     def triples(self) -> np.ndarray:
         count = ctypes.c_int64()
         _abi.lib().spamm_triples(self.handle, None, 0, ctypes.byref(count))

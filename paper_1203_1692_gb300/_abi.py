@@ -87,6 +87,8 @@ SIGNATURES = {
     "spamm_stats": (_i32, [_vp, ctypes.POINTER(spamm_stats_t)]),
     "spamm_stats_item": (_i32, [_vp, _i32, ctypes.POINTER(spamm_stats_t)]),
     "spamm_triples": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "spamm_cull_flat": (_i32, [_vp, _vp, _vp, _dbl, _vp, _i64, ctypes.POINTER(_i64),
+                               ctypes.POINTER(_flt)]),
     "spamm_multiply_static": (_i32, [_vp, _i64, _vp, _i64, _i64, _dbl, _flt, _flt, _vp, _i64,
                                      _vp, _vp]),
 }
@@ -243,6 +245,15 @@ def spamm_triples(ctx, out_ptr: int, cap: int) -> int:
     cnt = _i64()
     check(lib().spamm_triples(ctx, _vp(out_ptr), cap, ctypes.byref(cnt)), ctx)
     return cnt.value
+
+
+def spamm_cull_flat(ctx, A_tree, B_tree, tau: float, out_ptr: int, cap: int):
+    """(count, ms) of the flat enumeration; rows (I, K, J) into out_ptr."""
+    cnt = _i64()
+    ms = _flt()
+    check(lib().spamm_cull_flat(ctx, A_tree, B_tree, float(tau), _vp(out_ptr) if out_ptr else None,
+                                cap, ctypes.byref(cnt), ctypes.byref(ms)), ctx)
+    return cnt.value, ms.value
 
 
 def spamm_multiply_static(A_ptr: int, lda: int, B_ptr: int, ldb: int, n: int, tau: float,

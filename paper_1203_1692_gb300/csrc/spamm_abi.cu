@@ -558,6 +558,68 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     return SPAMM_OK;
 }
 
+spamm_status spamm_cull_flat(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                             double tau, int32_t* host_out, int64_t cap, int64_t* count,
+                             float* ms) {
+    if (!ctx || !A || !B || !count || cap < 0 || (cap > 0 && !host_out))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL argument");
+    if (!(tau >= 0.0) || !std::isfinite(tau))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tau must be finite and >= 0");
+    if (A->n != B->n || A->b != B->b || A->precision != B->precision ||
+        A->precision != ctx->cfg.precision || A->b != ctx->cfg.leaf)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "trees differ from the configuration");
+    if (A->nl > flat_max_leaves())
+        return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "flat enumeration: more than 2048 leaves per side");
+    *count = 0;
+    double roots[2];
+    cudaError_t e = cudaMemcpyAsync(&roots[0], A->pyr, sizeof(double), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&roots[1], B->pyr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "flat enumeration");
+    if (!std::isfinite(roots[0]) || !std::isfinite(roots[1]))
+        return set_err(ctx, SPAMM_ERR_NONFINITE, "an operand holds Inf or NaN");
+    void* scratch = nullptr;
+    unsigned long long* total = nullptr;
+    uint64_t* out = nullptr;
+    e = cudaMalloc(&scratch, flat_scratch_bytes(A->nl));
+    if (e == cudaSuccess) e = cudaMalloc(&total, sizeof(unsigned long long));
+    const unsigned long long dcap = (unsigned long long)cap;
+    if (e == cudaSuccess && dcap) e = cudaMalloc(&out, sizeof(uint64_t) * dcap);
+    unsigned long long htotal = 0;
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], ctx->stream);
+    if (e == cudaSuccess) e = launch_cull_flat(ctx, A, B, tau, out, dcap, scratch, total);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&htotal, total, sizeof(htotal), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && ms) e = cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]);
+    std::vector<uint64_t> h;
+    const unsigned long long got = std::min<unsigned long long>(htotal, dcap);
+    if (e == cudaSuccess && got) {
+        h.resize((size_t)got);
+        e = cudaMemcpy(h.data(), out, sizeof(uint64_t) * got, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(out);
+    cudaFree(total);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "flat enumeration");
+    // (I, J, K) order, as the tile-grouped list is read row by row
+    std::sort(h.begin(), h.end(), [](uint64_t x, uint64_t y) {
+        const uint64_t kx = ((uint64_t)tri_I(x) << 42) | ((uint64_t)tri_J(x) << 21) | tri_K(x);
+        const uint64_t ky = ((uint64_t)tri_I(y) << 42) | ((uint64_t)tri_J(y) << 21) | tri_K(y);
+        return kx < ky;
+    });
+    for (size_t q = 0; q < h.size(); ++q) {
+        host_out[3 * q + 0] = (int32_t)tri_I(h[q]);
+        host_out[3 * q + 1] = (int32_t)tri_K(h[q]);
+        host_out[3 * q + 2] = (int32_t)tri_J(h[q]);
+    }
+    *count = (int64_t)htotal;
+    return SPAMM_OK;
+}
+
 static spamm_status status_of(spamm_ctx* ctx, const DevCtl& c) { return status_from_ctl(ctx, c); }
 
 static spamm_status ensure_aux(spamm_ctx* ctx) {

@@ -214,6 +214,13 @@ cudaError_t launch_group(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* 
 cudaError_t launch_symbolic_batched(spamm_ctx* ctx, spamm_ctx* const* subs,
                                     const spamm_tree* const* A, const spamm_tree* const* B,
                                     const double* tau, int count, cudaStream_t stream);
+// flat.cu: the flat, norm-sorted enumeration of the leaf triples (Algorithm 1)
+cudaError_t launch_cull_flat(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                             double tau, uint64_t* out, unsigned long long cap,
+                             void* scratch, unsigned long long* total_dev);
+size_t flat_scratch_bytes(int64_t nl);
+int flat_max_leaves();
+
 // Zero the control blocks of subs[0..count) (out == nullptr) or gather them
 // into out[0..count).
 cudaError_t launch_ctl_batch(spamm_ctx* const* subs, int count, DevCtl* out, cudaStream_t s);

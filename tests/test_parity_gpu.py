@@ -272,3 +272,32 @@ def test_tree_outliving_its_context_is_freed_safely():
         ctx.multiply(t, t, 1e-6)
         ctx.close()
         t.close()
+
+
+FLAT_CASES = [(1024, 16, "exp", 1e-6), (700, 32, "water", 1e-3), (515, 16, "alg", 1e-5),
+              (333, 16, "dense", 0.0), (1000, 64, "exp", 1e-4), (17, 16, "exp", 1e-3)]
+
+
+@pytest.mark.parametrize("n,b,kind,tau", FLAT_CASES)
+def test_flat_enumeration_equals_hierarchy_and_oracle(n, b, kind, tau):
+    """Algorithm 1's flat, norm-sorted enumeration on the GPU keeps exactly
+    the leaf triples of the tier-by-tier cull (same leaf test, parent norms
+    never below their children's), and the oracle's outside the tie band."""
+    A = _matrix(kind, n)
+    B = _matrix("exp", n, seed=1) if kind == "dense" else A
+    P = _spamm()
+    ctx = P.Context(leaf=b, precision="fp32")
+    ta = ctx.build_norms(_dev(A))
+    tb = ctx.build_norms(_dev(B))
+    ctx.multiply(ta, tb, tau)
+    hier = ctx.triples()
+    flat, cnt, ms = ctx.cull_flat(ta, tb, tau)
+    assert cnt == len(flat) == len(hier)
+    assert as_set(flat) == as_set(hier)
+    _, cnt_only, _ = ctx.cull_flat(ta, tb, tau, triples=False)
+    assert cnt_only == cnt
+    ref = O.multiply(A, B, b, tau)
+    compare_triples(flat, ref.triples, O.pyramid(A, b), O.pyramid(B, b), O.depth(n, b), tau)
+    linkless = O.cull_linkless(O.pyramid(A, b), O.pyramid(B, b), O.depth(n, b), tau)
+    if ctx.stats()["tie_band"] == 0:
+        assert as_set(flat) == as_set(linkless)
