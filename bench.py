@@ -148,6 +148,46 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def leaf_roofline(precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_ms, kernel_traffic,
+                  dev_sms):
+    """Roofline of the leaf-product kernel.  Its algorithmic flops are the
+    kept leaf flops; its algorithmic bytes are the operands read once and C
+    written once (SURVEY-style 4n^2 per matrix).  The bound is the one the
+    arithmetic intensity selects against the ridge point of the two peaks."""
+    hbm = peaks["hbm_gbs"]
+    if precision == "fp32":
+        mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        fpeak = dev_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        kernel, fsrc = "k_leaf_simt", (f"{dev_sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} "
+                                       "MHz (median sampled SM clock)")
+        fbound = "alu"
+    else:
+        key = "bf16_tflops_sustained"
+        tf = precision.startswith("tf32")
+        fpeak = peaks[key] * (TF32_OVER_BF16 if tf else 1.0)
+        kernel = "k_leaf_tc"
+        fsrc = f"{key} of {peak_src} x {'1.1/2.25 (tf32/bf16 nominal)' if tf else '1'}"
+        fbound = "tensor"
+    flops_rate = kept_flops / (leaf_ms * 1e-3) / 1e12
+    bytes_rate = alg_bytes / (leaf_ms * 1e-3) / 1e9
+    intensity = kept_flops / alg_bytes
+    ridge = fpeak * 1e12 / (hbm * 1e9)
+    if intensity >= ridge:
+        roof = {"bound": fbound, "achieved": flops_rate, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": flops_rate / fpeak, "peak_source": fsrc}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_rate, "peak": hbm, "unit": "GB/s",
+                "frac": bytes_rate / hbm, "peak_source": f"hbm_gbs of {peak_src}"}
+    roof.update({"kernel": kernel, "traffic": kernel_traffic,
+                 "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+                 "flops_tflops": flops_rate, "flops_frac": flops_rate / fpeak,
+                 "bytes_gbs": bytes_rate, "bytes_frac": bytes_rate / hbm,
+                 "note": f"of {peak_src}; algorithmic flops = 2 b^3 per kept leaf triple "
+                         "(2 b^2 x 16 per kept slice product); algorithmic bytes = operands "
+                         "read once + C written once"})
+    return roof
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def cpu_sample(A, b, tau, seconds, seed=0):
@@ -473,24 +513,10 @@ def run_batched(args, P, dev, rank, world, dist):
     if rank != 0:
         return
     peaks, peak_src = measured_peaks()
-    if args.precision == "fp32":
-        mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "k_leaf_simt", "unit": "TFLOP/s",
-                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz"}
-    else:
-        key = "bf16_tflops_sustained"
-        tf = args.precision.startswith("tf32")
-        peak = peaks[key] * (TF32_OVER_BF16 if tf else 1.0)
-        roof = {"bound": "tensor", "kernel": "k_leaf_tc", "unit": "TFLOP/s",
-                "peak_source": f"{key} of {peak_src} x "
-                               f"{'1.1/2.25 (tf32/bf16 nominal)' if tf else '1'}"}
-    achieved = kept_flops / (leaf_ms * 1e-3) / 1e12
-    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision, b)),
-                 "note": f"of {peak_src}; algorithmic flops = 2 b^3 x kept leaf triples of "
-                         "the whole batch, one leaf launch"})
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alg_bytes = sum(2 * 4.0 * n * n for n in ns)        # A (= B) read, C written
+    roof = leaf_roofline(args.precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_ms,
+                         TRAFFIC.get(("k_leaf_tc", args.workload, args.precision, b)), sms)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         q = sorted(range(count), key=lambda q: ns[perm[q]])[count // 2]
@@ -808,24 +834,11 @@ def main():
     if rank != 0:
         return
     peaks, peak_src = measured_peaks()
-    if args.precision == "fp32":
-        mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "k_leaf_simt", "unit": "TFLOP/s",
-                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz (median "
-                               "sampled SM clock)"}
-    else:
-        key = "bf16_tflops_sustained"
-        peak = peaks[key] * (TF32_OVER_BF16 if args.precision.startswith("tf32") else 1.0)
-        roof = {"bound": "tensor", "kernel": "k_leaf_tc", "unit": "TFLOP/s",
-                "peak_source": f"{key} of {peak_src} x "
-                               f"{'1.1/2.25 (tf32/bf16 nominal)' if args.precision.startswith('tf32') else '1'}"}
-    achieved = kept_flops / (leaf_ms * 1e-3) / 1e12
-    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": TRAFFIC.get((roof["kernel"], args.workload, args.precision, b)),
-                 "traffic_unit": "GB per launch",
-                 "note": f"of {peak_src}; algorithmic flops = 2 b^3 x kept leaf triples"})
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = leaf_roofline(args.precision, peaks, peak_src, clk, kept_flops, 2 * 4.0 * n * n,
+                         leaf_ms, TRAFFIC.get(("k_leaf_tc", args.workload, args.precision, b)),
+                         sms)
+    roof["traffic_unit"] = "GB per launch"
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, threads, desc, _ = cpu_sample(A_h, b, tau, args.cpu_seconds)
