@@ -69,6 +69,8 @@ def lib():
         L.oracle_multiply_sliced.restype = _c_i64
         L.oracle_multiply_sliced.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _c_i64,
                                              _c_dbl, _c_dbl, _c_dbl, _p, _c_i64, _p]
+        L.oracle_sparsify.restype = _c_i64
+        L.oracle_sparsify.argtypes = [_p, _c_i64, _c_i64, _c_i64, _c_dbl, _c_dbl, _p]
         L.oracle_block.restype = _c_i64
         L.oracle_block.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _p, _p, _c_dbl,
                                    _c_i64, _c_i64, _p]
@@ -224,6 +226,18 @@ def multiply_sliced(A, B, b: int, g: int, tau: float, alpha: float = 1.0, beta: 
     if m < 0:
         raise RuntimeError(f"oracle_multiply_sliced failed ({m})")
     return Cd, int(m), int(stats[0]), int(stats[1])
+
+
+def sparsify(A, b: int, tau: float, norm2_max: float):
+    """(A with the dropped leaves zeroed (float32), stored leaf count):
+    a leaf is dropped iff ||A_IK||^2 * norm2_max < tau^2 or it is zero."""
+    A = _f32(A)
+    n = A.shape[0]
+    out = np.empty((n, n), dtype=np.float32)
+    m = lib().oracle_sparsify(_ptr(A), n, n, b, tau, norm2_max, _ptr(out))
+    if m < 0:
+        raise RuntimeError(f"oracle_sparsify failed ({m})")
+    return out, int(m)
 
 
 def blocks(A, B, b: int, tau: float, ij, pyrA=None, pyrB=None):

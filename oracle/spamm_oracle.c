@@ -29,7 +29,10 @@
  *   R5  within a C block the kept products are accumulated in ascending k;
  *   R14 the sub-leaf cull (oracle_multiply_sliced) splits the k dimension of
  *       a kept leaf product into slices of g and keeps a slice product iff
- *       the norms of its two panels pass the same condition.
+ *       the norms of its two panels pass the same condition;
+ *   R15 sparsification (oracle_sparsify) drops a leaf iff its product with
+ *       the largest operand norm fails the condition (epsilon = tau / max
+ *       Frobenius norm, tested in squared form).
  */
 #include <math.h>
 #include <stdint.h>
@@ -451,6 +454,30 @@ int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int6
         stats[1] = tested;
     }
     return cnt;
+}
+
+/* Sparsification with a drop tolerance (Sec. II.D): out = A with every leaf
+ * block dropped (zeroed) whose product with the largest norm it can meet
+ * fails the SpAMM condition, i.e. ||A_IK||^2 * norm2_max < tau^2 (squared,
+ * FP64, R2), and every zero block dropped (R3).  With norm2_max the larger
+ * of the two operands' squared Frobenius norms this is the paper's
+ * epsilon = tau / max(||A||_F, ||B||_F) (reading R15).  Returns the number
+ * of stored (kept, non-zero) leaves; out must hold n * n floats (ld n). */
+int64_t oracle_sparsify(const float *A, int64_t lda, int64_t n, int64_t b, double tau,
+                        double norm2_max, float *out)
+{
+    if (n <= 0 || b <= 0 || lda < n || !(tau >= 0.0)) return OR_EARG;
+    int64_t nl = (n + b - 1) / b, stored = 0;
+    for (int64_t I = 0; I < nl; I++)
+        for (int64_t K = 0; K < nl; K++) {
+            double s = panel_norm2(A, lda, n, I * b, b, K * b, b);
+            int keep_leaf = keep(s, norm2_max, tau * tau);
+            stored += keep_leaf;
+            for (int64_t r = I * b; r < I * b + b && r < n; r++)
+                for (int64_t c = K * b; c < K * b + b && c < n; c++)
+                    out[r * n + c] = keep_leaf ? A[r * lda + c] : 0.0f;
+        }
+    return stored;
 }
 
 /* One C block without the epilogue, for spot checks at sizes where the full

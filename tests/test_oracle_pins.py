@@ -368,3 +368,55 @@ def test_sliced_error_bound_and_monotone(b, g, tau):
     assert err <= (tested - kept) * tau * (1 + 1e-12)
     _, _, kept2, _ = O.multiply_sliced(A, A, b, g, tau * 3)
     assert kept2 <= kept
+
+
+# ----------------------------------------- sparsification (Sec. II.D, R15)
+
+def _norm2(A):
+    return float((A.astype(np.float64) ** 2).sum())
+
+
+def test_sparsify_at_the_consistent_tolerance_changes_no_product():
+    """With epsilon = tau / max(||A||_F, ||B||_F), a dropped leaf's product
+    with any leaf of the other operand is below tau (a leaf's norm never
+    exceeds the whole matrix's), so the SpAMM product of the sparsified
+    operands keeps the same leaf triples and gives the same C."""
+    A = gen.exp_decay(160, 0.8, seed=2)
+    B = gen.exp_decay_nonsym(160, 0.85, seed=3)
+    for b, tau in [(8, 1e-4), (16, 1e-6), (16, 1e-2)]:
+        m2 = max(_norm2(A), _norm2(B))
+        As, na = O.sparsify(A, b, tau, m2)
+        Bs, nb = O.sparsify(B, b, tau, m2)
+        assert na < (160 // b) ** 2 or tau < 1e-5
+        ref = O.multiply(A, B, b, tau)
+        got = O.multiply(As, Bs, b, tau)
+        assert np.array_equal(got.C, ref.C)
+        assert sorted(map(tuple, got.triples)) == sorted(map(tuple, ref.triples))
+
+
+def test_sparsify_drops_exactly_the_small_and_zero_leaves():
+    n, b = 64, 8
+    A = gen.uniform_dense(n, seed=9, symmetric=False)
+    A[:8, 8:16] = 0.0                                   # a zero leaf
+    A[16:24, :8] *= 1e-6                                # a small leaf
+    As, m = O.sparsify(A, b, 1e-3, 1.0)
+    assert m == 64 - 2
+    assert not As[:8, 8:16].any() and not As[16:24, :8].any()
+    mask = np.ones((n, n), bool)
+    mask[:8, 8:16] = mask[16:24, :8] = False
+    assert np.array_equal(As[mask], A[mask])
+    # tau = 0 keeps every non-zero leaf
+    As0, m0 = O.sparsify(A, b, 0.0, 1.0)
+    assert m0 == 63 and np.array_equal(As0, A)
+
+
+def test_sparsify_error_bound():
+    """||A - A_s||_F^2 = sum of the dropped leaves' norms^2 < dropped *
+    tau^2 / norm2_max."""
+    A = gen.exp_decay(200, 0.85, seed=4)
+    b, tau = 8, 3e-3
+    m2 = _norm2(A)
+    As, m = O.sparsify(A, b, tau, m2)
+    dropped = (200 // b) ** 2 - m
+    err2 = _norm2(A - As)
+    assert dropped > 0 and err2 < dropped * tau * tau / m2
