@@ -170,6 +170,28 @@ spamm_status spamm_tree_rebuild(spamm_ctx *ctx, spamm_tree *tree, const float *A
 spamm_status spamm_tree_rebuild_batched(spamm_ctx *ctx, int32_t count, spamm_tree *const *trees,
                                         const float *const *A, const int64_t *lda);
 
+/* Sparsified storage (Sec. II.D: a drop tolerance on the operands).  Like
+ * spamm_build_norms, but every leaf whose squared norm times
+ * max(||A||_F^2, partner_norm2) fails the SpAMM test at tau is dropped (a
+ * NULL block, R3), and the kept leaves are copied into storage of their own:
+ * each leaf row keeps the FP32 columns of its band of kept leaves, and the
+ * tensor-core packs hold pieces only inside the bands.  For matrices with
+ * decay in a locality-preserving order the storage is O(n) (band width
+ * times n) instead of O(n^2).  With partner_norm2 = the other operand's
+ * squared Frobenius norm this is the paper's epsilon = tau / max(||A||_F,
+ * ||B||_F), and spamm_multiply of two trees sparsified at that tau keeps
+ * exactly the leaf products of the dense trees (a dropped leaf's product
+ * with any leaf is below tau) and gives the same C.  The tree does not
+ * reference A after the call (synchronises).  Tensor-core precisions only;
+ * spamm_tree_rebuild does not apply (UNSUPPORTED).  INVALID_ARG,
+ * NONFINITE, UNSUPPORTED, OOM, CUDA. */
+spamm_status spamm_sparsify(spamm_ctx *ctx, const float *A, int64_t n, int64_t lda, double tau,
+                            double partner_norm2, spamm_tree **out);
+
+/* Device bytes a tree holds, and for a sparsified tree the number of kept
+ * leaves (-1 for a dense tree). */
+spamm_status spamm_tree_bytes(const spamm_tree *tree, int64_t *bytes, int64_t *stored);
+
 /* Free a tree.  Synchronises its context's stream first. */
 spamm_status spamm_tree_destroy(spamm_tree *tree);
 

@@ -47,15 +47,32 @@ def _check_matrix(A):
 
 
 class Tree:
-    """Norm quadtree of a matrix (holds a reference to the matrix)."""
+    """Norm quadtree of a matrix (holds a reference to the matrix, unless it
+    is a sparsified tree, which holds its own copy of the kept leaves)."""
 
-    def __init__(self, ctx: "Context", A):
+    def __init__(self, ctx: "Context", A, sparsify=None):
         n, lda = _check_matrix(A)
         self.ctx = ctx
-        self.A = A
         self.n = n
-        self.handle = spamm_build_norms(ctx.handle, A.data_ptr(), n, lda)
+        self.device = A.device
+        if sparsify is None:
+            self.A = A
+            self.handle = spamm_build_norms(ctx.handle, A.data_ptr(), n, lda)
+        else:
+            tau, partner_norm2 = sparsify
+            self.A = None
+            self.handle = _abi.spamm_sparsify(ctx.handle, A.data_ptr(), n, lda, tau,
+                                              partner_norm2)
         self.depth, self.nodes = spamm_tree_shape(self.handle)
+
+    @property
+    def bytes(self) -> int:
+        return _abi.spamm_tree_bytes(self.handle)[0]
+
+    @property
+    def stored_leaves(self) -> int:
+        """Kept leaves of a sparsified tree (-1 for a dense tree)."""
+        return _abi.spamm_tree_bytes(self.handle)[1]
 
     def rebuild(self, A):
         n, lda = _check_matrix(A)
@@ -103,6 +120,13 @@ class Context:
     def build_norms(self, A) -> Tree:
         return Tree(self, A)
 
+    def sparsify(self, A, tau: float, partner_norm2: float = 0.0) -> Tree:
+        """A sparsified tree of A: leaves whose product with max(||A||_F^2,
+        partner_norm2) fails the SpAMM test at tau are dropped, the rest
+        stored band by band (the paper's drop tolerance epsilon = tau /
+        max(||A||_F, ||B||_F) when partner_norm2 = ||B||_F^2)."""
+        return Tree(self, A, sparsify=(tau, partner_norm2))
+
     def tree_footprint(self, n: int) -> int:
         """Device bytes of a tree of order n under this configuration."""
         return _abi.spamm_tree_footprint(self.handle, n)
@@ -111,7 +135,7 @@ class Context:
                  C=None):
         torch = _torch()
         if C is None:
-            C = torch.empty((A.n, A.n), dtype=torch.float32, device=A.A.device)
+            C = torch.empty((A.n, A.n), dtype=torch.float32, device=A.device)
         n, ldc = _check_matrix(C)
         if n != A.n:
             raise ValueError("C has the wrong size")
@@ -146,7 +170,7 @@ class Context:
         alphas = bcast(alphas, 1.0)
         betas = bcast(betas, 0.0)
         if Cs is None:
-            Cs = [torch.empty((a.n, a.n), dtype=torch.float32, device=a.A.device) for a in As]
+            Cs = [torch.empty((a.n, a.n), dtype=torch.float32, device=a.device) for a in As]
         ldcs = []
         for a, C in zip(As, Cs):
             n, ldc = _check_matrix(C)

@@ -77,6 +77,8 @@ SIGNATURES = {
     "spamm_tree_destroy": (_i32, [_vp]),
     "spamm_tree_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "spamm_tree_footprint": (_i32, [_vp, _i64, ctypes.POINTER(_i64)]),
+    "spamm_sparsify": (_i32, [_vp, _vp, _i64, _i64, _dbl, _dbl, ctypes.POINTER(_vp)]),
+    "spamm_tree_bytes": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "spamm_tree_norms": (_i32, [_vp, _vp, _vp, _i64]),
     "spamm_multiply": (_i32, [_vp, _vp, _vp, _dbl, _flt, _flt, _vp, _i64]),
     "spamm_multiply_batched": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -189,6 +191,20 @@ def spamm_tree_footprint(ctx, n: int) -> int:
     out = _i64()
     check(lib().spamm_tree_footprint(ctx, n, ctypes.byref(out)), ctx)
     return out.value
+
+
+def spamm_sparsify(ctx, A_ptr: int, n: int, lda: int, tau: float, partner_norm2: float):
+    h = _vp()
+    check(lib().spamm_sparsify(ctx, _vp(A_ptr), n, lda, float(tau), float(partner_norm2),
+                               ctypes.byref(h)), ctx)
+    return h
+
+
+def spamm_tree_bytes(tree):
+    b = _i64()
+    st = _i64()
+    check(lib().spamm_tree_bytes(tree, ctypes.byref(b), ctypes.byref(st)))
+    return b.value, st.value
 
 
 def spamm_tree_norms(ctx, tree, out_ptr: int, count: int) -> None:

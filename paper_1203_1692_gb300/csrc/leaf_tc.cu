@@ -219,6 +219,15 @@ struct TcProd {
     int tr, tc, S;
     int sl;    // mask pairs per step: 1, or one per K-chunk (sub-leaf cull)
     int base;  // first work item (tile) of this product in the batch
+    // sparsified operands (BAND kernels): per K the band of pieces the pack
+    // holds, A role over leaf rows [lo, hi] of column K, B role over leaf
+    // columns [lo, hi] of row K, and the band's first piece; null if dense
+    const int32_t* a_lo;
+    const int32_t* a_hi;
+    const int64_t* a_off;
+    const int32_t* b_lo;
+    const int32_t* b_hi;
+    const int64_t* b_off;
 };
 
 constexpr int kMaxBatch = 64;
@@ -233,7 +242,10 @@ struct TcBatch {
     unsigned int* status;  // timeout status word
 };
 
-template <int LEAF, int PREC>
+// BAND: at least one operand of the batch is sparsified; its pieces are
+// copied from inside their band (the rows or columns of a tile outside the
+// band have no kept product and are not loaded).
+template <int LEAF, int PREC, bool BAND>
 __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     using T = PrecTraits<PREC>;
     constexpr int TL = 128 / LEAF;      // row leaves = column leaves per half
@@ -331,6 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const uint32_t ns = q.steps[u];
             const uint64_t sb = (uint64_t)q.off[u] * q.S;
             // lane 0: one K-chunk slot into the current stage
+            int64_t bandK = -1;
+            int64_t a_lo = 0, a_hi = -1, a_off = 0, b_lo = 0, b_hi = -1, b_off = 0;
             auto issue = [&](int64_t K, int kc, unsigned long long m0, unsigned long long m1) {
                 if (fill == 0) {
                     s = (int)(stage_it % ST);
@@ -339,21 +353,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 }
                 if (!ok) return;
                 const uint32_t full = smem_u32(&bar_full[s]);
-                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                             "r"((uint32_t)T::kIter)
-                             : "memory");
-                const int64_t row = (K * CHUNKS + kc) * q.nlp;
                 unsigned char* slot = stages + (size_t)s * T::kStage + (size_t)fill * T::kIter;
+                if constexpr (BAND) {
+                    if (K != bandK) {
+                        bandK = K;
+                        if (q.a_lo) {
+                            a_lo = q.a_lo[K];
+                            a_hi = q.a_hi[K];
+                            a_off = q.a_off[K];
+                        }
+                        if (q.b_lo) {
+                            b_lo = q.b_lo[K];
+                            b_hi = q.b_hi[K];
+                            b_off = q.b_off[K];
+                        }
+                    }
+                    // pieces of this K-chunk: [first piece, count, smem position]
+                    const int64_t row = (K * CHUNKS + kc) * q.nlp;
+                    int64_t sa = row + srow, na = TL, da = 0;
+                    if (q.a_lo) {
+                        const int64_t lo = srow > a_lo ? srow : a_lo;
+                        const int64_t hi = srow + TL - 1 < a_hi ? srow + TL - 1 : a_hi;
+                        na = hi >= lo ? hi - lo + 1 : 0;
+                        sa = a_off + kc * (a_hi - a_lo + 1) + (lo - a_lo);
+                        da = lo - srow;
+                    }
+                    int64_t sb2 = row + scol, nb2 = TLC, db = 0;
+                    if (q.b_lo) {
+                        const int64_t lo = scol > b_lo ? scol : b_lo;
+                        const int64_t hi = scol + TLC - 1 < b_hi ? scol + TLC - 1 : b_hi;
+                        nb2 = hi >= lo ? hi - lo + 1 : 0;
+                        sb2 = b_off + kc * (b_hi - b_lo + 1) + (lo - b_lo);
+                        db = lo - scol;
+                    }
+                    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
+                                 "r"((uint32_t)(T::kParts * (na + nb2) * piece))
+                                 : "memory");
 #pragma unroll
-                for (int part = 0; part < T::kParts; ++part) {
-                    bulk_g2s(smem_u32(slot + part * T::kSlice),
-                             static_cast<const unsigned char*>(q.pa[part]) +
-                                 (size_t)(row + srow) * piece,
-                             T::kSlice, full);
-                    bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
-                             static_cast<const unsigned char*>(q.pb[part]) +
-                                 (size_t)(row + scol) * piece,
-                             2 * T::kSlice, full);
+                    for (int part = 0; part < T::kParts; ++part) {
+                        if (na)
+                            bulk_g2s(smem_u32(slot + part * T::kSlice + da * piece),
+                                     static_cast<const unsigned char*>(q.pa[part]) +
+                                         (size_t)sa * piece,
+                                     (uint32_t)(na * piece), full);
+                        if (nb2)
+                            bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice +
+                                              db * piece),
+                                     static_cast<const unsigned char*>(q.pb[part]) +
+                                         (size_t)sb2 * piece,
+                                     (uint32_t)(nb2 * piece), full);
+                    }
+                } else {
+                    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
+                                 "r"((uint32_t)T::kIter)
+                                 : "memory");
+                    const int64_t row = (K * CHUNKS + kc) * q.nlp;
+#pragma unroll
+                    for (int part = 0; part < T::kParts; ++part) {
+                        bulk_g2s(smem_u32(slot + part * T::kSlice),
+                                 static_cast<const unsigned char*>(q.pa[part]) +
+                                     (size_t)(row + srow) * piece,
+                                 T::kSlice, full);
+                        bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
+                                 static_cast<const unsigned char*>(q.pb[part]) +
+                                     (size_t)(row + scol) * piece,
+                                 2 * T::kSlice, full);
+                    }
                 }
                 st_mask[s][fill][0] = m0;
                 st_mask[s][fill][1] = m1;
@@ -711,17 +776,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     }
 }
 
-template <int LEAF, int PREC>
-cudaError_t launch_t(spamm_ctx* ctx, const TcBatch& bt) {
+template <int LEAF, int PREC, bool BAND>
+cudaError_t launch_b(spamm_ctx* ctx, const TcBatch& bt) {
     using T = PrecTraits<PREC>;
     const size_t smem = 1024 + kZeroBytes + (size_t)T::kStages * T::kStage;
-    cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, PREC>,
+    cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, PREC, BAND>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = bt.total < ctx->sm_count ? bt.total : ctx->sm_count;
     if (grid <= 0) return cudaSuccess;
-    k_leaf_tc<LEAF, PREC><<<grid, kThreads, smem, ctx->stream>>>(bt);
+    k_leaf_tc<LEAF, PREC, BAND><<<grid, kThreads, smem, ctx->stream>>>(bt);
     return cudaGetLastError();
+}
+
+template <int LEAF, int PREC>
+cudaError_t launch_t(spamm_ctx* ctx, const TcBatch& bt, bool band) {
+    return band ? launch_b<LEAF, PREC, true>(ctx, bt) : launch_b<LEAF, PREC, false>(ctx, bt);
 }
 
 }  // namespace
@@ -735,6 +805,7 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
         bt.count = count - j0 < kMaxBatch ? count - j0 : kMaxBatch;
         bt.status = &ctx->ctl->status;
         int base = 0;
+        bool band = false;
         for (int i = 0; i < bt.count; ++i) {
             const LeafJob& jb = jobs[j0 + i];
             TcProd& q = bt.prods[i];
@@ -753,6 +824,20 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
             q.off = jb.sub->tile_off;
             q.steps = jb.sub->tile_steps;
             q.iters = jb.sub->tile_iters;
+            if (jb.A->sparse) {
+                const BandView v = band_view(jb.A);
+                q.a_lo = v.imin;
+                q.a_hi = v.imax;
+                q.a_off = v.aoff;
+                band = true;
+            }
+            if (jb.B->sparse) {
+                const BandView v = band_view(jb.B);
+                q.b_lo = v.kmin;
+                q.b_hi = v.kmax;
+                q.b_off = v.boff;
+                band = true;
+            }
             q.sl = (jb.A->slices && jb.B->slices) ? jb.A->slices : 1;
             q.tr = tile_rows(jb.A);
             q.tc = tile_cols(jb.A);
@@ -765,21 +850,21 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
         const int b = ctx->cfg.leaf;
         cudaError_t e;
         if (b == 16) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt);
-            else e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt);
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band);
+            else e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band);
         } else if (b == 32) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt);
-            else e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt);
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt, band);
+            else e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band);
         } else if (b == 64) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt);
-            else e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt);
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt, band);
+            else e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band);
         } else if (b == 128) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt);
-            else e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt);
+            if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt, band);
+            else e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band);
         } else {
             e = cudaErrorNotSupported;
         }

@@ -269,14 +269,17 @@ __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ lea
 // pieces of one leaf and the B-role pieces of one K-chunk are contiguous in
 // HBM, so consecutive threads write consecutive 16-byte units: every global
 // store is coalesced.  PK: 1 tf32 hi, 2 tf32 hi+lo, 3 bf16 hi+lo.
-template <int PK, int LEAF>
+// BAND: a sparsified tree; the strip comes from the leaf row's slab and the
+// pieces go to their place inside the column (A role) or row (B role) band.
+template <int PK, int LEAF, bool BAND>
 __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, int64_t n,
                                                    int64_t lda, int64_t nb, int64_t nl, int64_t nlp,
                                                    const double* __restrict__ leaf,
                                                    const double* __restrict__ rowmaxB,
                                                    const double* __restrict__ colmaxA, Thresh th,
                                                    void* __restrict__ pa0, void* __restrict__ pa1,
-                                                   void* __restrict__ pb0, void* __restrict__ pb1) {
+                                                   void* __restrict__ pb0, void* __restrict__ pb1,
+                                                   BandView bv) {
     constexpr int TL = 128 / LEAF;
     constexpr int CH = LEAF / 16;
     constexpr int ES = PK == 3 ? 2 : 4;                  // element bytes
@@ -307,24 +310,39 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     }
     __syncthreads();
     if (!any) return;
-    const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
     const int cq = 4 * lane;
+    if constexpr (BAND) {
+        // the slab holds the columns [kmin b, (kmax + 1) b) of this leaf row
+        const int kmin = bv.kmin[I], kmax = bv.kmax[I];
+        const int64_t w = (int64_t)(kmax - kmin + 1) * LEAF;
+        const float* srow = bv.slab + bv.roff[I];
 #pragma unroll 4
-    for (int r = warp; r < LEAF; r += 4) {
-        const int64_t row = r0 + r, col = c0 + cq;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row < n) {
-            const float* p = A + row * lda + col;
-            if (vec && col + 3 < n) {
-                v = __ldg(reinterpret_cast<const float4*>(p));
-            } else {
-                if (col + 0 < n) v.x = __ldg(p + 0);
-                if (col + 1 < n) v.y = __ldg(p + 1);
-                if (col + 2 < n) v.z = __ldg(p + 2);
-                if (col + 3 < n) v.w = __ldg(p + 3);
-            }
+        for (int r = warp; r < LEAF; r += 4) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int64_t sc = c0 + cq - (int64_t)kmin * LEAF;    // slab column
+            if (kmin <= kmax && sc >= 0 && sc + 3 < w)
+                v = __ldg(reinterpret_cast<const float4*>(srow + r * w + sc));
+            *reinterpret_cast<float4*>(&raw[r][cq]) = v;
         }
-        *reinterpret_cast<float4*>(&raw[r][cq]) = v;
+    } else {
+        const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
+#pragma unroll 4
+        for (int r = warp; r < LEAF; r += 4) {
+            const int64_t row = r0 + r, col = c0 + cq;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < n) {
+                const float* p = A + row * lda + col;
+                if (vec && col + 3 < n) {
+                    v = __ldg(reinterpret_cast<const float4*>(p));
+                } else {
+                    if (col + 0 < n) v.x = __ldg(p + 0);
+                    if (col + 1 < n) v.y = __ldg(p + 1);
+                    if (col + 2 < n) v.z = __ldg(p + 2);
+                    if (col + 3 < n) v.w = __ldg(p + 3);
+                }
+            }
+            *reinterpret_cast<float4*>(&raw[r][cq]) = v;
+        }
     }
     __syncthreads();
     // pieces, in output order
@@ -338,7 +356,14 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
         if (pa0 && needA[pc / CH]) {
             const int xa = pc / CH, kca = pc % CH;
             const float* src = &raw[prow][xa * LEAF + kca * 16 + core * EPU];
-            const size_t g = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * PIECE + (size_t)w * 16;
+            size_t g;
+            if constexpr (BAND) {
+                const int64_t K = Q0 + xa;
+                const int64_t len = bv.imax[K] - bv.imin[K] + 1;
+                g = (size_t)(bv.aoff[K] + kca * len + (I - bv.imin[K])) * PIECE + (size_t)w * 16;
+            } else {
+                g = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * PIECE + (size_t)w * 16;
+            }
             if (PK != 3) {
                 const float4 v = *reinterpret_cast<const float4*>(src);
                 uint4 h, l;
@@ -374,7 +399,14 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
             const int kcb = pc / TL, xb = pc % TL;
             const int colj = xb * LEAF + prow;           // staged column
             const int k0 = kcb * 16 + core * EPU;        // staged first row
-            const size_t g = ((size_t)(I * CH + kcb) * nlp + (Q0 + xb)) * PIECE + (size_t)w * 16;
+            size_t g;
+            if constexpr (BAND) {
+                const int64_t len = bv.kmax[I] - bv.kmin[I] + 1;
+                g = (size_t)(bv.boff[I] + kcb * len + (Q0 + xb - bv.kmin[I])) * PIECE +
+                    (size_t)w * 16;
+            } else {
+                g = ((size_t)(I * CH + kcb) * nlp + (Q0 + xb)) * PIECE + (size_t)w * 16;
+            }
             if (PK != 3) {
                 float f[4];
 #pragma unroll
@@ -479,17 +511,138 @@ cudaError_t launch_build_norms(spamm_tree* t, cudaStream_t s) {
 #undef SPAMM_LN
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_pyramid(t, s);
+}
+
+cudaError_t launch_pyramid(spamm_tree* t, cudaStream_t s) {
     int L = t->d;
     while (L > 0) {
         const int levels = L < 5 ? L : 5;
         const int64_t wL = (int64_t)1 << L;
         const int64_t blocks = wL < 32 ? 1 : wL / 32;
         k_pyramid_up<<<dim3((unsigned)blocks, (unsigned)blocks), 256, 0, s>>>(t->pyr, L, levels);
-        e = cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         L -= levels;
     }
     return cudaSuccess;
+}
+
+// ------------------------------------------------------- sparsification
+// A leaf is kept iff its squared norm passes the SpAMM test against
+// norm2_max, the largest squared Frobenius norm it can meet in a product
+// (the paper's drop tolerance epsilon = tau / max ||.||_F in squared form);
+// a dropped leaf's norm and panel norms become zero, so no cull ever keeps
+// it.  Then the bands of the kept leaves: per leaf row I the first and last
+// kept column (kmin, kmax), per leaf column K the first and last kept row
+// (imin, imax); an empty band has min > max.
+__global__ void __launch_bounds__(256) k_sparse_mark(double* __restrict__ leaf, int64_t nb,
+                                                     int64_t nl, Thresh th, double norm2_max,
+                                                     int SL, double* __restrict__ panA,
+                                                     double* __restrict__ panB,
+                                                     unsigned long long* __restrict__ stored) {
+    unsigned long long kept = 0;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nl * nl;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = g / nl, K = g % nl;
+        bool tie;
+        if (spamm_keep(leaf[I * nb + K], norm2_max, th, &tie)) {
+            ++kept;
+            continue;
+        }
+        leaf[I * nb + K] = 0.0;
+        for (int q = 0; q < SL; ++q) {
+            panA[(I * nl + K) * SL + q] = 0.0;
+            panB[(I * SL + q) * nl + K] = 0.0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(stored, kept);
+}
+
+// blockIdx.y = 0: a warp per leaf row (kmin, kmax); 1: a thread per leaf
+// column (imin, imax).
+__global__ void __launch_bounds__(256) k_bands(const double* __restrict__ leaf, int64_t nb,
+                                               int64_t nl, int32_t* __restrict__ band) {
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.y == 0) {
+        const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+        for (int64_t I = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); I < nl;
+             I += warps) {
+            int lo = (int)nl, hi = -1;
+            for (int64_t K = lane; K < nl; K += 32)
+                if (leaf[I * nb + K] > 0.0) {
+                    lo = min(lo, (int)K);
+                    hi = max(hi, (int)K);
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) {
+                band[I] = lo;
+                band[nl + I] = hi;
+            }
+        }
+    } else {
+        for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < nl;
+             K += (int64_t)gridDim.x * blockDim.x) {
+            int lo = (int)nl, hi = -1;
+            for (int64_t I = 0; I < nl; ++I)
+                if (leaf[I * nb + K] > 0.0) {
+                    lo = min(lo, (int)I);
+                    hi = max(hi, (int)I);
+                }
+            band[2 * nl + K] = lo;
+            band[3 * nl + K] = hi;
+        }
+    }
+}
+
+cudaError_t launch_sparsify_mark(spamm_tree* t, double tau, double norm2_max, double rel,
+                                 int32_t* band, unsigned long long* stored, cudaStream_t s) {
+    const int64_t off_leaf = (((int64_t)1 << (2 * t->d)) - 1) / 3;
+    double* leaf = t->pyr + off_leaf;
+    const Thresh th = make_thresh(tau, rel);
+    const int64_t m = t->nl * t->nl;
+    const int blocks = (int)std::min<int64_t>((m + 255) / 256, 4096);
+    cudaError_t e = cudaMemsetAsync(stored, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_sparse_mark<<<std::max(blocks, 1), 256, 0, s>>>(leaf, t->nb, t->nl, th, norm2_max,
+                                                      t->slices, t->panA, t->panB, stored);
+    const int bb = (int)std::max<int64_t>(1, std::min<int64_t>((t->nl + 7) / 8, 4096));
+    k_bands<<<dim3(bb, 2), 256, 0, s>>>(leaf, t->nb, t->nl, band);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_pyramid(t, s);
+}
+
+// One matrix row per block: the columns of its leaf row's band, kept leaves
+// copied and dropped ones zeroed (zero beyond n).
+__global__ void __launch_bounds__(256) k_slab_copy(const float* __restrict__ A, int64_t lda,
+                                                   int64_t n, int b, int64_t nb,
+                                                   const double* __restrict__ leaf, BandView bv,
+                                                   float* __restrict__ slab) {
+    const int64_t row = blockIdx.x;                     // 0 .. nl * b - 1
+    const int64_t I = row / b, r = row % b;
+    const int kmin = bv.kmin[I], kmax = bv.kmax[I];
+    if (kmin > kmax) return;
+    const int64_t w = (int64_t)(kmax - kmin + 1) * b;
+    float* dst = slab + bv.roff[I] + r * w;
+    for (int64_t c = threadIdx.x; c < w; c += blockDim.x) {
+        const int64_t col = (int64_t)kmin * b + c;
+        const bool live = row < n && col < n && leaf[I * nb + col / b] > 0.0;
+        dst[c] = live ? A[row * lda + col] : 0.f;
+    }
+}
+
+cudaError_t launch_slab_copy(spamm_tree* t, const float* A, int64_t lda, cudaStream_t s) {
+    const int64_t off_leaf = (((int64_t)1 << (2 * t->d)) - 1) / 3;
+    const int64_t rows = t->nl * t->b;
+    if (rows == 0) return cudaSuccess;
+    k_slab_copy<<<(unsigned)rows, 256, 0, s>>>(A, lda, t->n, t->b, t->nb, t->pyr + off_leaf,
+                                                band_view(t), t->slab);
+    return cudaGetLastError();
 }
 
 // Packs for one multiply: the per-K maxima of the two leaf tiers, then the
@@ -519,14 +672,19 @@ cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, d
         void* pb1 = roleB ? t->packB[1] : nullptr;
         const double* leaf = t->pyr + off_leaf;
         dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));
-#define SPAMM_LP(PKV, LV)                                                                    \
+#define SPAMM_LP2(PKV, LV, BV)                                                               \
     do {                                                                                     \
         if (smem > 48 * 1024)                                                                \
-            cudaFuncSetAttribute(k_leaf_pack<PKV, LV>,                                       \
+            cudaFuncSetAttribute(k_leaf_pack<PKV, LV, BV>,                                   \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-        k_leaf_pack<PKV, LV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,       \
-                                                     t->nlp, leaf, rmB, cmA, th, pa0, pa1,   \
-                                                     pb0, pb1);                              \
+        k_leaf_pack<PKV, LV, BV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,   \
+                                                         t->nlp, leaf, rmB, cmA, th, pa0,    \
+                                                         pa1, pb0, pb1, band_view(t));       \
+    } while (0)
+#define SPAMM_LP(PKV, LV)                                                                    \
+    do {                                                                                     \
+        if (t->sparse) SPAMM_LP2(PKV, LV, true);                                             \
+        else SPAMM_LP2(PKV, LV, false);                                                      \
     } while (0)
 #define SPAMM_LP_B(LV)                     \
     do {                                   \
@@ -540,6 +698,7 @@ cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, d
         else SPAMM_LP_B(128);
 #undef SPAMM_LP_B
 #undef SPAMM_LP
+#undef SPAMM_LP2
         return cudaGetLastError();
     };
     if (A == B) return one(A, rowmaxB, colmaxA);

@@ -106,6 +106,12 @@ void free_tree_storage(spamm_tree* t) {
     cudaFree(t->panA);
     cudaFree(t->panB);
     t->panA = t->panB = nullptr;
+    cudaFree(t->slab);
+    cudaFree(t->band);
+    cudaFree(t->offs);
+    t->slab = nullptr;
+    t->band = nullptr;
+    t->offs = nullptr;
     for (int i = 0; i < 2; ++i) {
         cudaFree(t->packA[i]);
         cudaFree(t->packB[i]);
@@ -253,12 +259,10 @@ static spamm_status build_into(spamm_ctx* ctx, spamm_tree* t) {
     return cuda_err(ctx, e, "norm build launch");
 }
 
-spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda,
-                               spamm_tree** out) {
-    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
-    *out = nullptr;
-    spamm_status st = check_matrix(ctx, A, n, lda);
-    if (st != SPAMM_OK) return st;
+// A tree's shape and norm storage; with packs = true also the dense pack
+// arrays.  On failure nothing is left allocated.
+static spamm_status new_tree(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda, bool packs,
+                             spamm_tree** out) {
     const int b = ctx->cfg.leaf;
     const int d = depth_for(n, b);
     const int64_t nl = (n + b - 1) / b;
@@ -285,7 +289,7 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
         e = cudaMalloc(&t->panA, pn);
         if (e == cudaSuccess) e = cudaMalloc(&t->panB, pn);
     }
-    if (e == cudaSuccess && precision_uses_tc(t->precision)) {
+    if (e == cudaSuccess && packs && precision_uses_tc(t->precision)) {
         t->pack_bytes = pack_bytes_for(t->precision, t->nlp, b);
         const int arrays = pack_arrays_for(t->precision);
         for (int i = 0; i < arrays && e == cudaSuccess; ++i) {
@@ -296,11 +300,28 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
         }
     }
     if (e != cudaSuccess) {
-        st = cuda_err(ctx, e, "tree allocation");
+        const spamm_status st = cuda_err(ctx, e, "tree allocation");
         free_tree_storage(t);
         delete t;
         return st;
     }
+    t->bytes = (int64_t)sizeof(double) * t->nodes +
+               (t->slices ? 2 * (int64_t)sizeof(double) * nl * nl * t->slices : 0) +
+               (int64_t)t->pack_bytes * 2 * (packs && precision_uses_tc(t->precision)
+                                                 ? pack_arrays_for(t->precision) : 0);
+    *out = t;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda,
+                               spamm_tree** out) {
+    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    spamm_status st = check_matrix(ctx, A, n, lda);
+    if (st != SPAMM_OK) return st;
+    spamm_tree* t = nullptr;
+    st = new_tree(ctx, A, n, lda, true, &t);
+    if (st != SPAMM_OK) return st;
     st = build_into(ctx, t);
     if (st != SPAMM_OK) {
         cudaStreamSynchronize(ctx->stream);
@@ -313,8 +334,117 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
     return SPAMM_OK;
 }
 
+spamm_status spamm_sparsify(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda, double tau,
+                            double partner_norm2, spamm_tree** out) {
+    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    spamm_status st = check_matrix(ctx, A, n, lda);
+    if (st != SPAMM_OK) return st;
+    if (!(tau >= 0.0) || !std::isfinite(tau) || !(partner_norm2 >= 0.0) ||
+        !std::isfinite(partner_norm2))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tau and partner_norm2 must be finite and >= 0");
+    if (!precision_uses_tc(ctx->cfg.precision))
+        return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "sparsified trees need a tensor-core precision");
+    spamm_tree* t = nullptr;
+    st = new_tree(ctx, A, n, lda, false, &t);
+    if (st != SPAMM_OK) return st;
+    auto fail = [&](cudaError_t e, const char* what) {
+        cudaStreamSynchronize(ctx->stream);
+        free_tree_storage(t);
+        delete t;
+        return cuda_err(ctx, e, what);
+    };
+    cudaStream_t s = ctx->stream;
+    const int64_t nl = t->nl;
+    const int b = t->b;
+    // 1. dense norms (and panels) of A, then its squared Frobenius norm
+    cudaError_t e = launch_build_norms(t, s);
+    double root = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&root, t->pyr, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e, "sparsify norms");
+    if (!std::isfinite(root)) {
+        free_tree_storage(t);
+        delete t;
+        return set_err(ctx, SPAMM_ERR_NONFINITE, "an operand holds Inf or NaN");
+    }
+    const double norm2_max = std::max(root, partner_norm2);
+    // 2. drop, bands, upper tiers
+    unsigned long long* stored_dev = nullptr;
+    e = cudaMalloc(&t->band, sizeof(int32_t) * 4 * (size_t)std::max<int64_t>(nl, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&stored_dev, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = launch_sparsify_mark(t, tau, norm2_max, ctx->cfg.tie_rel, t->band, stored_dev, s);
+    std::vector<int32_t> band((size_t)(4 * nl));
+    unsigned long long stored = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(band.data(), t->band, sizeof(int32_t) * 4 * nl, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&stored, stored_dev, sizeof(stored), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(stored_dev);
+    if (e != cudaSuccess) return fail(e, "sparsify bands");
+    // 3. slab and pack layout (host), storage
+    const int32_t* kmin = band.data();
+    const int32_t* kmax = kmin + nl;
+    const int32_t* imin = kmin + 2 * nl;
+    const int32_t* imax = kmin + 3 * nl;
+    const int CH = b / 16;
+    std::vector<int64_t> offs((size_t)(3 * nl + 2));
+    int64_t* roff = offs.data();
+    int64_t* aoff = roff + nl;
+    int64_t* boff = aoff + nl + 1;
+    int64_t slab = 0, pa = 0, pb = 0;
+    for (int64_t q = 0; q < nl; ++q) {
+        roff[q] = slab;
+        aoff[q] = pa;
+        boff[q] = pb;
+        if (kmin[q] <= kmax[q]) {
+            slab += (int64_t)b * (kmax[q] - kmin[q] + 1) * b;
+            pb += (int64_t)CH * (kmax[q] - kmin[q] + 1);
+        }
+        if (imin[q] <= imax[q]) pa += (int64_t)CH * (imax[q] - imin[q] + 1);
+    }
+    aoff[nl] = pa;
+    boff[nl] = pb;
+    const int64_t piece = (int64_t)b * 16 * (t->precision == SPAMM_PREC_BF16X3 ? 2 : 4);
+    e = cudaMalloc(&t->offs, sizeof(int64_t) * offs.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t->offs, offs.data(), sizeof(int64_t) * offs.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&t->slab, sizeof(float) * (size_t)std::max<int64_t>(slab, 64));
+    const int arrays = pack_arrays_for(t->precision);
+    for (int i = 0; i < arrays && e == cudaSuccess; ++i) {
+        e = cudaMalloc(&t->packA[i], (size_t)std::max<int64_t>(pa * piece, 256));
+        if (e == cudaSuccess) e = cudaMalloc(&t->packB[i], (size_t)std::max<int64_t>(pb * piece, 256));
+    }
+    t->sparse = 1;
+    if (e == cudaSuccess) e = launch_slab_copy(t, A, lda, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e, "sparsify storage");
+    t->A = nullptr;       // the tree holds its own copy of the kept leaves
+    t->lda = 0;
+    t->stored = (int64_t)stored;
+    t->bytes = (int64_t)sizeof(double) * t->nodes + (int64_t)sizeof(int32_t) * 4 * nl +
+               (int64_t)sizeof(int64_t) * (3 * nl + 2) + (int64_t)sizeof(float) * slab +
+               (int64_t)arrays * (pa + pb) * piece +
+               (t->slices ? 2 * (int64_t)sizeof(double) * nl * nl * t->slices : 0);
+    ctx->trees.push_back(t);
+    *out = t;
+    return SPAMM_OK;
+}
+
+spamm_status spamm_tree_bytes(const spamm_tree* t, int64_t* bytes, int64_t* stored) {
+    if (!t || !bytes) return SPAMM_ERR_INVALID_ARG;
+    *bytes = t->bytes;
+    if (stored) *stored = t->sparse ? t->stored : -1;
+    return SPAMM_OK;
+}
+
 spamm_status spamm_tree_rebuild(spamm_ctx* ctx, spamm_tree* t, const float* A, int64_t lda) {
     if (!ctx || !t) return SPAMM_ERR_INVALID_ARG;
+    if (t->sparse)
+        return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "a sparsified tree is rebuilt by spamm_sparsify");
     spamm_status st = check_matrix(ctx, A, t->n, lda);
     if (st != SPAMM_OK) return st;
     if (t->precision != ctx->cfg.precision || t->b != ctx->cfg.leaf)
@@ -685,6 +815,8 @@ spamm_status spamm_tree_rebuild_batched(spamm_ctx* ctx, int32_t count, spamm_tre
     for (int p = 0; p < count; ++p) {
         spamm_tree* t = trees[p];
         if (!t) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL tree");
+        if (t->sparse)
+            return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "a sparsified tree is rebuilt by spamm_sparsify");
         const spamm_status st = check_matrix(ctx, A[p], t->n, lda[p]);
         if (st != SPAMM_OK) return st;
         if (t->precision != ctx->cfg.precision || t->b != ctx->cfg.leaf)

@@ -129,7 +129,45 @@ struct spamm_tree {
     int slices;
     double* panA;
     double* panB;
+    // sparsified storage (spamm_sparsify): leaf row I keeps the columns of
+    // its band of leaves [kmin, kmax] as an FP32 slab (dropped leaves zero),
+    // and the packs hold pieces only inside the bands: A role per leaf
+    // column K over [imin, imax], B role per leaf row K over [kmin, kmax].
+    // Zero for dense trees.
+    int sparse;
+    float* slab;
+    int32_t* band;      // kmin, kmax, imin, imax: 4 x nl (device)
+    int64_t* offs;      // roff (nl), aoff (nl + 1), boff (nl + 1) (device)
+    int64_t stored;     // leaves kept
+    int64_t bytes;      // device bytes the tree holds
 };
+
+// Device view of a sparsified tree's bands (see spamm_tree).
+struct BandView {
+    const float* slab;
+    const int32_t* kmin;
+    const int32_t* kmax;
+    const int32_t* imin;
+    const int32_t* imax;
+    const int64_t* roff;   // slab element offset of leaf row I
+    const int64_t* aoff;   // first A-role piece of leaf column K
+    const int64_t* boff;   // first B-role piece of leaf row K
+};
+
+inline BandView band_view(const spamm_tree* t) {
+    BandView v{};
+    if (!t->sparse) return v;
+    const int64_t nl = t->nl;
+    v.slab = t->slab;
+    v.kmin = t->band;
+    v.kmax = t->band + nl;
+    v.imin = t->band + 2 * nl;
+    v.imax = t->band + 3 * nl;
+    v.roff = t->offs;
+    v.aoff = t->offs + nl;
+    v.boff = t->offs + 2 * nl + 1;
+    return v;
+}
 
 struct spamm_ctx {
     cudaStream_t stream;
@@ -229,6 +267,15 @@ cudaError_t launch_ctl_batch(spamm_ctx* const* subs, int count, DevCtl* out, cud
 // A x B at tau (norms.cu); scratch holds 2 x (leaves per side) doubles.
 cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, double rel,
                          double* scratch, int sm_count, cudaStream_t s);
+
+// Sparsification (norms.cu): drop the leaves whose product with norm2_max
+// fails the SpAMM test at tau (norms and panels zeroed), then the row and
+// column bands of the kept leaves (4 x nl int32: kmin, kmax, imin, imax).
+cudaError_t launch_sparsify_mark(spamm_tree* t, double tau, double norm2_max, double rel,
+                                 int32_t* band, unsigned long long* stored, cudaStream_t s);
+// Copy the kept leaves of the dense A into the tree's slab.
+cudaError_t launch_slab_copy(spamm_tree* t, const float* A, int64_t lda, cudaStream_t s);
+cudaError_t launch_pyramid(spamm_tree* t, cudaStream_t s);
 
 // leaf_simt.cu
 cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
