@@ -45,6 +45,9 @@ WORKLOADS = {
                "tau in {1e-6, 1e-8}, each a chain of 8 squarings X <- X^2 of an exponential-"
                "decay matrix (lambda=0.9) scaled by 1/max row-sum, continuous batching under "
                "a 150 GB device-memory budget, leaf size autotuned",
+    "sparse65536": "exponential decay a_ij = u_ij 0.9^|i-j| (n=65536), squared at tau=1e-6 "
+                   "with sparsified storage (drop tolerance tau / ||A||_F, banded leaves and "
+                   "packs) against the dense trees, leaf 64",
     "batched64": "64 independent products C_p = A_p A_p, n log-uniform in [512, 8192], "
                  "a_ij = u_ij lambda^|i-j| with lambda uniform in [0.8, 0.95], tau=1e-7, "
                  "one persistent leaf launch in a captured CUDA graph, leaf size and "
@@ -640,6 +643,85 @@ def run_serving(args, P, dev, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_sparse(args, P, dev, rank, world, dist):
+    """Sparsified storage at scale: one step is tree + multiply for C = A A,
+    with the dense tree (norms + full packs) and with the sparsified tree
+    (norms, drop, banded slab and packs); both give the same C."""
+    import torch
+    from spamm_inputs import device as D
+    n, b = 65536, (64 if args.leaf == "auto" else int(args.leaf))
+    tau = 1e-6 if args.tau == "auto" else float(args.tau)
+    A = D.exp_decay(n, 0.9, seed=0, device=dev)
+    C_dense = torch.empty_like(A)
+    C_sparse = torch.empty_like(A)
+    torch.cuda.synchronize()
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True)
+
+    def timed(fn, reps):
+        for _ in range(max(2, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, (time.perf_counter() - t0) * 1e3 / reps
+
+    dense_tree = ctx.build_norms(A)
+    dense_bytes = dense_tree.bytes
+
+    def dense_step():
+        dense_tree.rebuild(A)
+        ctx.multiply(dense_tree, dense_tree, tau, C=C_dense)
+
+    ms_dense, _ = timed(dense_step, args.steps)
+    st_dense = ctx.stats()
+    dense_tree.close()
+    torch.cuda.empty_cache()
+    holder = {}
+
+    def sparse_step():
+        t = ctx.sparsify(A, tau, 0.0)
+        ctx.multiply(t, t, tau, C=C_sparse)
+        if "t" in holder:
+            holder["t"].close()
+        holder["t"] = t
+
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    ms_sparse_dev, ms_sparse_host = timed(sparse_step, args.steps)
+    clk = clocks.stop()
+    st = ctx.stats()
+    t = holder["t"]
+    sparse_bytes, stored = t.bytes, t.stored_leaves
+    same = bool(torch.equal(C_dense, C_sparse))
+    if rank != 0:
+        return
+    nl = -(-n // b)
+    line = {
+        "metric": "SpAMM with sparsified storage: kept leaf TFLOP/s per step (tree + multiply)",
+        "value": st["kept_flops"] / (ms_sparse_host * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_sparse_host, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS["sparse65536"], "n": n, "leaf": b, "tau": tau,
+                   "precision": args.precision, "l2": "inputs larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "sparse_tree_bytes": sparse_bytes, "dense_tree_bytes": dense_bytes,
+        "bytes_ratio": dense_bytes / sparse_bytes, "stored_leaves": stored,
+        "leaves": nl * nl, "dense_ms_per_step": ms_dense,
+        "sparse_ms_per_step_device": ms_sparse_dev,
+        "sparse_ms_per_step_wall": ms_sparse_host,
+        "kept_leaf_triples": st["leaf_triples"], "dense_kept_leaf_triples": st_dense["leaf_triples"],
+        "C_equal_to_dense": same, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def kernels_per_step(d, leaf, precision="tf32x3", same_tree=True):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
@@ -670,6 +752,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, P, dev, rank, world, dist)
+        return
+    if args.workload == "sparse65536":
+        run_sparse(args, P, dev, rank, world, dist)
         return
     A_h = make_matrix(args.workload, args.sites)
     n = A_h.shape[0]
