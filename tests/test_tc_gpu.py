@@ -120,6 +120,43 @@ def test_tc_water_like_n7500_sampled(prec):
     assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL[prec]
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tc_water_like_n7500_bench_configuration(prec):
+    """The bench's own launch configuration (leaf 64, the equal-error tau
+    1e-4) on the n = 7500 workload, sampled C blocks against the oracle."""
+    A = gen.water_like()
+    n, b, tau = A.shape[0], 64, 1e-4
+    ctx, C = _run(A, A, b, tau, prec)
+    ij = sample_blocks(n, b, 24)
+    pa = O.pyramid(A, b)
+    ref, _ = O.blocks(A, A, b, tau, ij, pa, pa)
+    got = blocks_from(C, ij, b, n)
+    assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL[prec]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 16), ("tf32", 16),
+                                    ("tf32x3", 64)])
+def test_tc_algebraic_n16384_sampled(prec, b):
+    """The algebraic-decay configuration at full size (n = 16384, tau =
+    1e-8, leaf products in TF32, split BF16 x3 and 3xTF32): sampled C blocks
+    against the oracle, and the kept count against the sign-free closed
+    form (|s_ij| = 1, so every leaf norm is deterministic)."""
+    A = gen.algebraic_decay(16384, seed=0)
+    n, tau = A.shape[0], 1e-8
+    ctx, C = _run(A, A, b, tau, prec)
+    ij = sample_blocks(n, b, 16)
+    pa = O.pyramid(A, b)
+    ref, _ = O.blocks(A, A, b, tau, ij, pa, pa)
+    got = blocks_from(C, ij, b, n)
+    assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL[prec]
+    # kept leaf triples against the oracle's flat count on the same norms
+    d = O.depth(n, b)
+    flat = O.cull_linkless(pa, pa, d, tau)
+    assert ctx.stats()["leaf_triples"] == len(flat)
+
+
 @pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 32), ("tf32x3", 64)])
 def test_tc_stale_pieces_never_reach_C(prec, b):
     """A multiply packs only the leaves that can take part in a kept product
