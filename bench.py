@@ -68,7 +68,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="spamm", choices=["spamm", "reference"])
     p.add_argument("--workload", default="water7500", choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "tf32", "bf16x3"])
+    p.add_argument("--precision", default="f16x3",
+                   choices=["fp32", "tf32x3", "tf32", "bf16x3", "f16x3"])
     p.add_argument("--leaf", default="auto",
                    help="leaf size b, or 'auto': the fastest of 16/32/64/128 at equal error")
     p.add_argument("--tau", default="auto")
@@ -77,7 +78,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--sites", type=int, default=300,
                    help="water-like workload: number of sites (n = 25 x sites)")
-    p.add_argument("--alt", default="bf16x3",
+    p.add_argument("--alt", default="tf32x3",
                    help="also time this leaf precision on the same workload ('' = off)")
     p.add_argument("--slice", type=int, default=0, help="sub-leaf cull along k (16) or off (0)")
     p.add_argument("--flat", action="store_true",
@@ -181,7 +182,9 @@ def leaf_roofline(precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_m
     else:
         roof = {"bound": "hbm", "achieved": bytes_rate, "peak": hbm, "unit": "GB/s",
                 "frac": bytes_rate / hbm, "peak_source": f"hbm_gbs of {peak_src}"}
-    roof.update({"kernel": kernel, "traffic": kernel_traffic,
+    passes = 3 if precision.endswith("x3") else 1     # tensor-core passes per leaf product
+    roof.update({"kernel": kernel, "traffic": kernel_traffic, "mma_passes": passes,
+                 "issued_mma_frac": passes * flops_rate / fpeak,
                  "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
                  "flops_tflops": flops_rate, "flops_frac": flops_rate / fpeak,
                  "bytes_gbs": bytes_rate, "bytes_frac": bytes_rate / hbm,

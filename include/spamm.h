@@ -54,7 +54,10 @@ typedef enum {
     SPAMM_PREC_FP32 = 0,    /* FP32 FFMA on the CUDA cores, FP32 accumulate */
     SPAMM_PREC_TF32X3 = 1,  /* tcgen05 kind::tf32, hi*hi + hi*lo + lo*hi, FP32 accumulate */
     SPAMM_PREC_TF32 = 2,    /* tcgen05 kind::tf32, one pass, FP32 accumulate */
-    SPAMM_PREC_BF16X3 = 3   /* tcgen05 kind::f16 on bf16 hi/lo splits, FP32 accumulate */
+    SPAMM_PREC_BF16X3 = 3,  /* tcgen05 kind::f16 on bf16 hi/lo splits, FP32 accumulate */
+    SPAMM_PREC_F16X3 = 4    /* tcgen05 kind::f16 on fp16 hi/lo splits of each operand scaled
+                               by a power of two (its largest leaf norm to 2^15), FP32
+                               accumulate: 3xTF32-class accuracy with 2-byte operands */
 } spamm_precision;
 
 typedef struct {

@@ -27,7 +27,8 @@ SPAMM_PREC_FP32 = 0
 SPAMM_PREC_TF32X3 = 1
 SPAMM_PREC_TF32 = 2
 SPAMM_PREC_BF16X3 = 3
-PRECISIONS = {"fp32": 0, "tf32x3": 1, "tf32": 2, "bf16x3": 3}
+SPAMM_PREC_F16X3 = 4
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "tf32": 2, "bf16x3": 3, "f16x3": 4}
 
 SPAMM_MAX_TIERS = 32
 

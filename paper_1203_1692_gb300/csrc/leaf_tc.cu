@@ -6,12 +6,16 @@
 // (TL = 128 / b), and the tile's steps (K, two half masks) in ascending K
 // from the grouping stage.  For every step and every 16-wide K chunk the
 // tile needs A's 128 x 16 slice (its row leaves at column leaf K) and B's
-// 16 x 256 slice; both were stored by the norm build as contiguous runs
-// already in the no-swizzle K-major layout of tcgen05 (8-row x 16-byte core
-// matrices), so one 1-D bulk copy per operand part moves them into shared
-// memory.  A 256-wide tile halves the MMA instructions per flop compared
-// with 128 x 128: on this part an MMA's issue cost, not its arithmetic,
-// dominates at N = 128.
+// 16 x 256 slice, hi and lo parts; the packs hold them already in the
+// no-swizzle K-major layout of tcgen05 (8-row x 16-byte core matrices),
+// grouped so that all chunks and parts a tile reads from one operand at one
+// K are a single contiguous run.  One 1-D bulk copy per operand moves a run
+// of K-chunks into shared memory: at b = 64 one step is two copies.  The
+// copies, not their bytes, set the pace of the producer (each costs on the
+// order of fifty cycles to issue and complete), so fewer and larger copies
+// are what keeps the tensor pipe fed.  A 256-wide tile halves the MMA
+// instructions per flop compared with 128 x 128: on this part an MMA's
+// issue cost, not its arithmetic, dominates at N = 128.
 //
 // Exactness of the cull: a kept leaf product (x, K, y) must be added and a
 // culled one must not.  One MMA over a run of consecutive column leaves
@@ -133,7 +137,7 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
 
 // Instruction descriptor: FP32 accumulator, A/B format (1 = BF16 under
 // kind::f16, 2 = TF32 under kind::tf32), both K-major, M x N.
-__device__ __forceinline__ uint32_t make_idesc(uint32_t ab, int M, int N) {
+__device__ __forceinline__ constexpr uint32_t make_idesc(uint32_t ab, int M, int N) {
     return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
@@ -157,7 +161,7 @@ __device__ __forceinline__ uint32_t chunks_of(uint32_t iters) {
 template <int PREC>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                     const uint32_t (&dis)[4], uint32_t acc) {
-    if (PREC == SPAMM_PREC_BF16X3) {
+    if (PREC == SPAMM_PREC_BF16X3 || PREC == SPAMM_PREC_F16X3) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, {%5, %6, %7, %8}, p;\n\t}"
@@ -170,6 +174,25 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, {%5, %6, %7, %8}, p;\n\t}"
             ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(dis[0]), "r"(dis[1]),
             "r"(dis[2]), "r"(dis[3])
+            : "memory");
+    }
+}
+
+// The same MMA without the disable-output-lane operand (every lane written).
+template <int PREC>
+__device__ __forceinline__ void mma_all(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+    if (PREC == SPAMM_PREC_BF16X3 || PREC == SPAMM_PREC_F16X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
             : "memory");
     }
 }
@@ -191,16 +214,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 template <int PREC>
 struct PrecTraits {
-    static constexpr int kEsize = PREC == SPAMM_PREC_BF16X3 ? 2 : 4;
+    static constexpr bool k16 = PREC == SPAMM_PREC_BF16X3 || PREC == SPAMM_PREC_F16X3;
+    static constexpr int kEsize = k16 ? 2 : 4;
     static constexpr int kParts = PREC == SPAMM_PREC_TF32 ? 1 : 2;      // arrays per role
     static constexpr int kSlice = 128 * 16 * kEsize;                   // bytes of one 128x16 slice
-    static constexpr int kIter = 3 * kParts * kSlice;                   // A (128) + B (256) rows
+    static constexpr int kASlot = kParts * kSlice;                      // A of one K-chunk
+    static constexpr int kBSlot = 2 * kParts * kSlice;                  // B of one K-chunk
+    static constexpr int kIter = kASlot + kBSlot;                       // A (128) + B (256) rows
     static constexpr int kSPS = kIter <= 24576 ? 4 : 2;                 // K-chunks per stage
     static constexpr int kStage = kSPS * kIter;                         // 96 KB
     static constexpr int kStages = 2;
-    static constexpr int kKInstr = PREC == SPAMM_PREC_BF16X3 ? 16 : 8;  // K per MMA
+    static constexpr int kKInstr = k16 ? 16 : 8;                        // K per MMA
     static constexpr uint32_t kSBO = 8 * 16 * kEsize;                   // row-group stride
-    static constexpr uint32_t kAB = PREC == SPAMM_PREC_BF16X3 ? 1u : 2u;
+    // operand format of the instruction descriptor: kind::tf32 -> TF32 (2);
+    // kind::f16 -> BF16 (1) or F16 (0)
+    static constexpr uint32_t kAB = PREC == SPAMM_PREC_BF16X3 ? 1u
+                                    : PREC == SPAMM_PREC_F16X3 ? 0u : 2u;
 };
 
 // One product of a (possibly one-element) batch, as the host prepares it.
@@ -228,6 +257,8 @@ struct TcProd {
     const int32_t* b_lo;
     const int32_t* b_hi;
     const int64_t* b_off;
+    // FP16 split: largest squared leaf norms of A and B (their scales)
+    const double* gmax;
 };
 
 constexpr int kMaxBatch = 64;
@@ -266,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     // as tight as with a single product.
     __shared__ unsigned long long sp_pk[kMaxBatch], sp_pm[kMaxBatch];
     __shared__ int sp_skip[kMaxBatch], sp_end[kMaxBatch];
+    __shared__ float2 sp_uns[PREC == SPAMM_PREC_F16X3 ? kMaxBatch : 1];  // 2^-(kA + kB)
 
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -280,6 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         // a product whose cull failed is left untouched (its status says why)
         sp_skip[i] = (g.ctl->status & (ST_OVERFLOW | ST_NONFINITE)) ? 1 : 0;
         sp_end[i] = g.base + g.tr * g.tc;
+        if constexpr (PREC == SPAMM_PREC_F16X3)
+            sp_uns[i] = f16_unscale(g.gmax[0], g.gmax[1]);
     }
 
     for (int i = threadIdx.x; i < (int)(kZeroBytes / 16); i += kThreads)
@@ -320,10 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         // The whole warp walks the step list in batches of 32 (each lane
         // loads one step's K and masks; the next batch is prefetched while
         // this one is issued) and lane 0 fills the stages: up to kSPS
-        // K-chunk slots per stage, never across tiles.  For every slot it
-        // adds the slot's bytes to the stage's expected transaction count
-        // and issues the bulk copies; closing a stage records the slots'
-        // masks and count in shared memory and arrives on the full barrier.
+        // K-chunk slots per stage, never across tiles.  For every run of
+        // slots it adds the run's bytes to the stage's expected transaction
+        // count and issues the bulk copies; closing a stage records the
+        // slots' masks and count in shared memory and arrives on the full
+        // barrier.
         unsigned long long stage_it = 0;
         int fill = 0;
         int s = 0;
@@ -342,10 +377,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const int64_t scol = (int64_t)(u % q.tc) * TLC;
             const uint32_t ns = q.steps[u];
             const uint64_t sb = (uint64_t)q.off[u] * q.S;
-            // lane 0: one K-chunk slot into the current stage
+            // lane 0: m consecutive K-chunks kc0.. of the step at K into slots
+            // fill.. of the current stage (m <= kSPS - fill).  A stage keeps the
+            // A parts of its slots together, then the B parts, and the dense
+            // packs keep a tile's chunks of one K together in the same order,
+            // so the run is one bulk copy per operand.
+            const int64_t ga = srow / TL, gb = scol / TLC;          // tile's pack groups
             int64_t bandK = -1;
             int64_t a_lo = 0, a_hi = -1, a_off = 0, b_lo = 0, b_hi = -1, b_off = 0;
-            auto issue = [&](int64_t K, int kc, unsigned long long m0, unsigned long long m1) {
+            auto issue = [&](int64_t K, int kc0, int m, unsigned long long m0,
+                             unsigned long long m1) {
                 if (fill == 0) {
                     s = (int)(stage_it % ST);
                     const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
@@ -353,8 +394,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 }
                 if (!ok) return;
                 const uint32_t full = smem_u32(&bar_full[s]);
-                unsigned char* slot = stages + (size_t)s * T::kStage + (size_t)fill * T::kIter;
+                unsigned char* const stg = stages + (size_t)s * T::kStage;
+                unsigned char* const sa_dst = stg + (size_t)fill * T::kASlot;
+                unsigned char* const sb_dst =
+                    stg + (size_t)T::kSPS * T::kASlot + (size_t)fill * T::kBSlot;
+                // dense operand: its run of m chunks, all parts
+                const size_t a_src = ((size_t)(K * (q.nlp / TL) + ga) * CHUNKS + kc0) * T::kASlot;
+                const size_t b_src = ((size_t)(K * (q.nlp / TLC) + gb) * CHUNKS + kc0) * T::kBSlot;
                 if constexpr (BAND) {
+                    // m == 1 here: a sparsified operand's chunk comes from
+                    // inside its band, one copy per part
                     if (K != bandK) {
                         bandK = K;
                         if (q.a_lo) {
@@ -368,61 +417,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                             b_off = q.b_off[K];
                         }
                     }
-                    // pieces of this K-chunk: [first piece, count, smem position]
-                    const int64_t row = (K * CHUNKS + kc) * q.nlp;
-                    int64_t sa = row + srow, na = TL, da = 0;
+                    uint32_t bytes = 0;
+                    int64_t sa = 0, na = TL, da = 0;
                     if (q.a_lo) {
                         const int64_t lo = srow > a_lo ? srow : a_lo;
                         const int64_t hi = srow + TL - 1 < a_hi ? srow + TL - 1 : a_hi;
                         na = hi >= lo ? hi - lo + 1 : 0;
-                        sa = a_off + kc * (a_hi - a_lo + 1) + (lo - a_lo);
+                        sa = a_off + kc0 * (a_hi - a_lo + 1) + (lo - a_lo);
                         da = lo - srow;
+                        bytes += (uint32_t)(T::kParts * na * piece);
+                    } else {
+                        bytes += (uint32_t)T::kASlot;
                     }
-                    int64_t sb2 = row + scol, nb2 = TLC, db = 0;
+                    int64_t sb2 = 0, nb2 = TLC, db = 0;
                     if (q.b_lo) {
                         const int64_t lo = scol > b_lo ? scol : b_lo;
                         const int64_t hi = scol + TLC - 1 < b_hi ? scol + TLC - 1 : b_hi;
                         nb2 = hi >= lo ? hi - lo + 1 : 0;
-                        sb2 = b_off + kc * (b_hi - b_lo + 1) + (lo - b_lo);
+                        sb2 = b_off + kc0 * (b_hi - b_lo + 1) + (lo - b_lo);
                         db = lo - scol;
+                        bytes += (uint32_t)(T::kParts * nb2 * piece);
+                    } else {
+                        bytes += (uint32_t)T::kBSlot;
                     }
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                 "r"((uint32_t)(T::kParts * (na + nb2) * piece))
+                                 "r"(bytes)
                                  : "memory");
+                    if (q.a_lo) {
 #pragma unroll
-                    for (int part = 0; part < T::kParts; ++part) {
-                        if (na)
-                            bulk_g2s(smem_u32(slot + part * T::kSlice + da * piece),
-                                     static_cast<const unsigned char*>(q.pa[part]) +
-                                         (size_t)sa * piece,
-                                     (uint32_t)(na * piece), full);
-                        if (nb2)
-                            bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice +
-                                              db * piece),
-                                     static_cast<const unsigned char*>(q.pb[part]) +
-                                         (size_t)sb2 * piece,
-                                     (uint32_t)(nb2 * piece), full);
+                        for (int part = 0; part < T::kParts; ++part)
+                            if (na)
+                                bulk_g2s(smem_u32(sa_dst + part * T::kSlice + da * piece),
+                                         static_cast<const unsigned char*>(q.pa[part]) +
+                                             (size_t)sa * piece,
+                                         (uint32_t)(na * piece), full);
+                    } else {
+                        bulk_g2s(smem_u32(sa_dst),
+                                 static_cast<const unsigned char*>(q.pa[0]) + a_src,
+                                 (uint32_t)T::kASlot, full);
+                    }
+                    if (q.b_lo) {
+#pragma unroll
+                        for (int part = 0; part < T::kParts; ++part)
+                            if (nb2)
+                                bulk_g2s(smem_u32(sb_dst + 2 * part * T::kSlice + db * piece),
+                                         static_cast<const unsigned char*>(q.pb[part]) +
+                                             (size_t)sb2 * piece,
+                                         (uint32_t)(nb2 * piece), full);
+                    } else {
+                        bulk_g2s(smem_u32(sb_dst),
+                                 static_cast<const unsigned char*>(q.pb[0]) + b_src,
+                                 (uint32_t)T::kBSlot, full);
                     }
                 } else {
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                 "r"((uint32_t)T::kIter)
+                                 "r"((uint32_t)(m * T::kIter))
                                  : "memory");
-                    const int64_t row = (K * CHUNKS + kc) * q.nlp;
-#pragma unroll
-                    for (int part = 0; part < T::kParts; ++part) {
-                        bulk_g2s(smem_u32(slot + part * T::kSlice),
-                                 static_cast<const unsigned char*>(q.pa[part]) +
-                                     (size_t)(row + srow) * piece,
-                                 T::kSlice, full);
-                        bulk_g2s(smem_u32(slot + (T::kParts + 2 * part) * T::kSlice),
-                                 static_cast<const unsigned char*>(q.pb[part]) +
-                                     (size_t)(row + scol) * piece,
-                                 2 * T::kSlice, full);
-                    }
+                    bulk_g2s(smem_u32(sa_dst), static_cast<const unsigned char*>(q.pa[0]) + a_src,
+                             (uint32_t)(m * T::kASlot), full);
+                    bulk_g2s(smem_u32(sb_dst), static_cast<const unsigned char*>(q.pb[0]) + b_src,
+                             (uint32_t)(m * T::kBSlot), full);
                 }
-                st_mask[s][fill][0] = m0;
-                st_mask[s][fill][1] = m1;
-                if (++fill == T::kSPS) {
+                for (int j = 0; j < m; ++j) {
+                    st_mask[s][fill + j][0] = m0;
+                    st_mask[s][fill + j][1] = m1;
+                }
+                fill += m;
+                if (fill == T::kSPS) {
                     st_count[s] = (uint32_t)fill;
                     mbar_arrive(full);
                     issued_s = ++stage_it;
@@ -444,9 +505,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         const int64_t K = __shfl_sync(0xffffffffu, ck, j);
                         const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
                         const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
-                        for (int kc = 0; kc < CHUNKS && ok; ++kc) {
-                            if (lane == 0) issue(K, kc, m0, m1);
+                        // the step's chunks in runs that end at stage boundaries
+                        // (one chunk per run when an operand is sparsified)
+                        for (int kc = 0; kc < CHUNKS && ok;) {
+                            int m = 1;
+                            if (lane == 0) {
+                                if (!BAND) m = min(CHUNKS - kc, T::kSPS - fill);
+                                issue(K, kc, m, m0, m1);
+                            }
+                            m = __shfl_sync(0xffffffffu, m, 0);
                             ok = __shfl_sync(0xffffffffu, ok, 0);
+                            kc += m;
                         }
                     }
                     ck = nk;
@@ -482,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
                         const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
                         if ((m0 | m1) == 0ull) continue;
-                        if (lane == 0) issue(K, (int)((base + j) % CHUNKS), m0, m1);
+                        if (lane == 0) issue(K, (int)((base + j) % CHUNKS), 1, m0, m1);
                         ok = __shfl_sync(0xffffffffu, ok, 0);
                     }
                     ck = nk;
@@ -543,10 +612,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         }
                         const unsigned long long mask0 = st_mask[s][jj][0];
                         const unsigned long long mask1 = st_mask[s][jj][1];
-                        const uint32_t sbuf =
-                            smem_u32(stages + (size_t)s * T::kStage + (size_t)jj * T::kIter);
-                        const uint32_t a_hi = sbuf, a_lo = sbuf + T::kSlice;
-                        const uint32_t b_hi = sbuf + T::kParts * T::kSlice;
+                        const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
+                        const uint32_t a_hi = sbuf + jj * (uint32_t)T::kASlot;
+                        const uint32_t a_lo = a_hi + T::kSlice;
+                        const uint32_t b_hi =
+                            sbuf + (uint32_t)(T::kSPS * T::kASlot) + jj * (uint32_t)T::kBSlot;
                         const uint32_t b_lo = b_hi + 2 * T::kSlice;
                         // Runs of column leaves with the same kept row leaves:
                         // a column y starts a run when its row mask is non-zero
@@ -557,78 +627,98 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                             : TL == 4 ? 0x0000000001010101ull
                             : TL == 2 ? 0x0000000000000101ull
                                       : 0x0000000000000001ull;
-                        const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
-                        const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
-                        const bool u0 = mask0 == (unsigned long long)x0 * kRep;
-                        const bool u1 = mask1 == (unsigned long long)x1 * kRep;
-                        uint32_t starts, nz;
-                        if (u0 && u1) {
-                            starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
-                            nz = (x0 ? (1u << TL) - 1u : 0u) |
-                                 (x1 ? ((1u << TL) - 1u) << TL : 0u);
-                        } else {
-                            starts = 0u;
-                            nz = 0u;
-                            uint32_t prev = 0u;
-#pragma unroll
-                            for (int yy = 0; yy < TLC; ++yy) {
-                                const uint32_t xm =
-                                    yy < TL ? (uint32_t)(mask0 >> (8 * yy)) & 0xFFu
-                                            : (uint32_t)(mask1 >> (8 * (yy - TL))) & 0xFFu;
-                                if (xm) nz |= 1u << yy;
-                                if (xm && xm != prev) starts |= 1u << yy;
-                                prev = xm;
-                            }
-                        }
+                        constexpr unsigned long long kFull =
+                            (unsigned long long)((1u << TL) - 1u) * kRep;
                         uint64_t ah[2], al[2];
 #pragma unroll
                         for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
                             ah[kk] = make_desc(a_hi + (uint32_t)kk * 256u, 128, T::kSBO);
                             al[kk] = make_desc(a_lo + (uint32_t)kk * 256u, 128, T::kSBO);
                         }
-                        while (starts) {
-                            const int y = __ffs(starts) - 1;
-                            starts &= starts - 1;
-                            const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
-                            const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
-                            const int len = yend - y;
-                            const uint32_t xm = y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
-                                                       : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
-                            // disable-output-lane bits: row r of the tile is
-                            // lane r, and a dropped row leaf x masks its b rows
-                            uint32_t dis[4];
-#pragma unroll
-                            for (int w = 0; w < 4; ++w) {
-                                uint32_t v = 0;
-                                if (LEAF <= 32) {
-#pragma unroll
-                                    for (int q = 0; q < 32 / LEAF; ++q) {
-                                        const int x = w * (32 / LEAF) + q;
-                                        if (!((xm >> x) & 1u))
-                                            v |= (LEAF == 32 ? 0xFFFFFFFFu
-                                                             : (0xFFFFu << (16 * q)));
-                                    }
-                                } else {
-                                    const int x = (w * 32) / LEAF;
-                                    if (!((xm >> x) & 1u)) v = 0xFFFFFFFFu;
-                                }
-                                dis[w] = v;
-                            }
-                            const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
-                            const uint32_t d = dacc + (uint32_t)(y * LEAF);
-                            const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
+                        if (mask0 == kFull && mask1 == kFull) {
+                            // every product of the step kept (the common case on
+                            // dense blocks): one 128 x 256 MMA per pass, no masks
+                            constexpr uint32_t idesc_full = make_idesc(T::kAB, 128, 256);
 #pragma unroll
                             for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
                                 const uint32_t koff = (uint32_t)kk * 256u;
-                                const uint64_t bh =
-                                    make_desc(b_hi + boff + koff, 128, T::kSBO);
+                                const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
                                 if (PREC != SPAMM_PREC_TF32) {
-                                    const uint64_t bl =
-                                        make_desc(b_lo + boff + koff, 128, T::kSBO);
-                                    mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
-                                    mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
+                                    const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
+                                    mma_all<PREC>(dacc, al[kk], bh, idesc_full, 1u);
+                                    mma_all<PREC>(dacc, ah[kk], bl, idesc_full, 1u);
                                 }
-                                mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
+                                mma_all<PREC>(dacc, ah[kk], bh, idesc_full, 1u);
+                            }
+                        } else {
+                            const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
+                            const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
+                            const bool u0 = mask0 == (unsigned long long)x0 * kRep;
+                            const bool u1 = mask1 == (unsigned long long)x1 * kRep;
+                            uint32_t starts, nz;
+                            if (u0 && u1) {
+                                starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
+                                nz = (x0 ? (1u << TL) - 1u : 0u) |
+                                     (x1 ? ((1u << TL) - 1u) << TL : 0u);
+                            } else {
+                                starts = 0u;
+                                nz = 0u;
+                                uint32_t prev = 0u;
+#pragma unroll
+                                for (int yy = 0; yy < TLC; ++yy) {
+                                    const uint32_t xm =
+                                        yy < TL ? (uint32_t)(mask0 >> (8 * yy)) & 0xFFu
+                                                : (uint32_t)(mask1 >> (8 * (yy - TL))) & 0xFFu;
+                                    if (xm) nz |= 1u << yy;
+                                    if (xm && xm != prev) starts |= 1u << yy;
+                                    prev = xm;
+                                }
+                            }
+                            while (starts) {
+                                const int y = __ffs(starts) - 1;
+                                starts &= starts - 1;
+                                const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
+                                const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
+                                const int len = yend - y;
+                                const uint32_t xm =
+                                    y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
+                                           : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
+                                // disable-output-lane bits: row r of the tile is
+                                // lane r, and a dropped row leaf x masks its b rows
+                                uint32_t dis[4];
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) {
+                                    uint32_t v = 0;
+                                    if (LEAF <= 32) {
+#pragma unroll
+                                        for (int q = 0; q < 32 / LEAF; ++q) {
+                                            const int x = w * (32 / LEAF) + q;
+                                            if (!((xm >> x) & 1u))
+                                                v |= (LEAF == 32 ? 0xFFFFFFFFu
+                                                                 : (0xFFFFu << (16 * q)));
+                                        }
+                                    } else {
+                                        const int x = (w * 32) / LEAF;
+                                        if (!((xm >> x) & 1u)) v = 0xFFFFFFFFu;
+                                    }
+                                    dis[w] = v;
+                                }
+                                const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
+                                const uint32_t d = dacc + (uint32_t)(y * LEAF);
+                                const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
+#pragma unroll
+                                for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                    const uint32_t koff = (uint32_t)kk * 256u;
+                                    const uint64_t bh =
+                                        make_desc(b_hi + boff + koff, 128, T::kSBO);
+                                    if (PREC != SPAMM_PREC_TF32) {
+                                        const uint64_t bl =
+                                            make_desc(b_lo + boff + koff, 128, T::kSBO);
+                                        mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
+                                        mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
+                                    }
+                                    mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
+                                }
                             }
                         }
                         if (i % kChunkIters == kChunkIters - 1 || i == iters - 1) {
@@ -717,7 +807,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             if (!ok) break;
             float* const Cp = q.C;
             const int64_t ldc = q.ldc, n = q.n;
-            const float alpha = q.alpha, beta = q.beta;
+            // FP16 split: the products come scaled by 2^(kA + kB); undoing it
+            // is exact (powers of two) unless the result leaves the float range
+            float alpha = q.alpha;
+            if constexpr (PREC == SPAMM_PREC_F16X3) {
+                const float2 us = sp_uns[pi];
+                alpha *= us.x;
+#pragma unroll
+                for (int v = 0; v < 128; ++v) master[v] *= us.y;
+            }
+            const float beta = q.beta;
             const int64_t row = (int64_t)(u / q.tc) * 128 + qq * 32 + lane;
             const int64_t col0 = (int64_t)(u % q.tc) * 256 + hcol * 128;
             if (row < n && col0 < n) {
@@ -824,6 +923,7 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
             q.off = jb.sub->tile_off;
             q.steps = jb.sub->tile_steps;
             q.iters = jb.sub->tile_iters;
+            q.gmax = jb.sub->need + 2 * jb.A->nb;
             if (jb.A->sparse) {
                 const BandView v = band_view(jb.A);
                 q.a_lo = v.imin;
@@ -852,19 +952,23 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
         if (b == 16) {
             if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band);
             else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band);
-            else e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_BF16X3) e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else e = launch_t<16, SPAMM_PREC_F16X3>(ctx, bt, band);
         } else if (b == 32) {
             if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt, band);
             else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt, band);
-            else e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_BF16X3) e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else e = launch_t<32, SPAMM_PREC_F16X3>(ctx, bt, band);
         } else if (b == 64) {
             if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt, band);
             else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt, band);
-            else e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_BF16X3) e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else e = launch_t<64, SPAMM_PREC_F16X3>(ctx, bt, band);
         } else if (b == 128) {
             if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt, band);
             else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt, band);
-            else e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else if (p == SPAMM_PREC_BF16X3) e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band);
+            else e = launch_t<128, SPAMM_PREC_F16X3>(ctx, bt, band);
         } else {
             e = cudaErrorNotSupported;
         }

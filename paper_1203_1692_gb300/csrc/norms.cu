@@ -18,16 +18,23 @@
 // Inside a piece the rows are grouped by 8: a row group holds the core
 // matrices (8 rows x 16 bytes) of the chunk one after another (leading byte
 // offset 128 B), and row groups follow each other at the stride-byte offset
-// (512 B for TF32, 256 B for BF16): the no-swizzle K-major canonical layout
-// of tcgen05.  Pieces are stored with the leaf index innermost:
-//     piece(P, Q, kc) at ((P * (b/16) + kc) * nlp + Q) * piece_bytes   (B role)
-//     piece(P, Q, kc) at ((Q * (b/16) + kc) * nlp + P) * piece_bytes   (A role)
-// so the 128 / b consecutive leaves of one C tile row/column strip form one
-// contiguous 8 KB (TF32) / 4 KB (BF16) run that a single bulk copy moves
-// into shared memory, already in the layout the MMA reads.  The A role holds
-// leaf (I, K) with rows = i (K-major as stored); the B role holds leaf (K, J)
-// transposed, rows = j.
+// (512 B for TF32, 256 B for 16-bit parts): the no-swizzle K-major canonical
+// layout of tcgen05.  The A role holds leaf (I, K) with rows = i (K-major as
+// stored); the B role holds leaf (K, J) transposed, rows = j.  Pieces are
+// grouped the way one C tile reads them: a tile's rows are TL = 128 / b
+// consecutive leaves, its columns 2 TL, so with G the group size (TL for the
+// A role, 2 TL for the B role), P the parts (hi, lo) and CH = b / 16,
+//     piece(K, x, kc, part) at ((((K * nlp/G + x/G) * CH + kc) * P + part) * G
+//                               + x % G) * piece_bytes
+// (K = the shared index, x = the leaf's other index).  The G pieces of one
+// group, chunk and part form the 128 x 16 (A) or 256 x 16 (B) operand slice
+// of one MMA, the parts of a chunk follow each other, and the chunks of one
+// K follow each other: everything a tile needs from one operand at one K is
+// one contiguous run, which a single bulk copy moves into shared memory
+// already in the layout the MMA reads.  Sparsified trees keep their own
+// banded layout (one array per part, see k_leaf_pack).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -39,7 +46,9 @@ bool precision_uses_tc(int p) { return p != SPAMM_PREC_FP32; }
 
 int pack_arrays_for(int p) { return p == SPAMM_PREC_TF32 ? 1 : 2; }
 
-static int elem_bytes(int p) { return p == SPAMM_PREC_BF16X3 ? 2 : 4; }
+static int elem_bytes(int p) {
+    return (p == SPAMM_PREC_BF16X3 || p == SPAMM_PREC_F16X3) ? 2 : 4;
+}
 
 size_t pack_bytes_for(int p, int64_t nlp, int b) {
     if (!precision_uses_tc(p)) return 0;
@@ -50,6 +59,32 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
+}
+
+// Eight values into hi and lo 16-bit parts, two per word: BF16 (PK 3) as
+// they are, FP16 (PK 4) after scaling by the operand's power of two.
+template <int PK>
+__device__ __forceinline__ void split16(const float (&f)[8], float sc, uint32_t (&hw)[4],
+                                        uint32_t (&lw)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if constexpr (PK == 3) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * q]);
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * q + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * q] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * q + 1] - __bfloat162float(h1));
+            hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        } else {
+            const float x0 = __fmul_rn(f[2 * q], sc), x1 = __fmul_rn(f[2 * q + 1], sc);
+            const __half h0 = __float2half_rn(x0);
+            const __half h1 = __float2half_rn(x1);
+            const __half l0 = __float2half_rn(__fsub_rn(x0, __half2float(h0)));
+            const __half l1 = __float2half_rn(__fsub_rn(x1, __half2float(h1)));
+            hw[q] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+            lw[q] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+        }
+    }
 }
 
 // Leaf squared norms without the FP64 pipe, which is narrow on GB300.
@@ -224,7 +259,8 @@ __global__ void __launch_bounds__(128) k_leaf_norms(const float* __restrict__ A,
 __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ leafA,
                                                   const double* __restrict__ leafB, int64_t nb,
                                                   int64_t nl, double* __restrict__ colmaxA,
-                                                  double* __restrict__ rowmaxB) {
+                                                  double* __restrict__ rowmaxB,
+                                                  double* __restrict__ gmax) {
     __shared__ double part[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.y == 0) {
@@ -242,6 +278,9 @@ __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ lea
 #pragma unroll
                 for (int w = 1; w < 8; ++w) r = fmax(r, part[w][lane]);
                 colmaxA[K] = r;
+                // largest leaf of A (non-negative doubles order like their bits)
+                atomicMax(reinterpret_cast<unsigned long long*>(gmax),
+                          (unsigned long long)__double_as_longlong(r));
             }
             __syncthreads();
         }
@@ -252,7 +291,11 @@ __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ lea
 #pragma unroll 4
             for (int64_t J = lane; J < nl; J += 32) m = fmax(m, leafB[K * nb + J]);
             for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) rowmaxB[K] = m;
+            if (lane == 0) {
+                rowmaxB[K] = m;
+                atomicMax(reinterpret_cast<unsigned long long*>(gmax + 1),
+                          (unsigned long long)__double_as_longlong(m));
+            }
         }
     }
 }
@@ -265,10 +308,10 @@ __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ lea
 // the needed pieces in output order: thread t writes the t-th, (t+128)-th, ...
 // 16-byte unit of each piece, reading the elements that unit holds from the
 // staged strip (a row quad for the A role, a column quad for the B role),
-// splitting them into hi/lo parts and storing both parts.  The A-role
-// pieces of one leaf and the B-role pieces of one K-chunk are contiguous in
-// HBM, so consecutive threads write consecutive 16-byte units: every global
-// store is coalesced.  PK: 1 tf32 hi, 2 tf32 hi+lo, 3 bf16 hi+lo.
+// splitting them into hi/lo parts and storing both parts.  Every piece is
+// a contiguous run of at least 512 bytes and consecutive threads write its
+// consecutive 16-byte units: every global store is coalesced.  PK: 1 tf32
+// hi, 2 tf32 hi+lo, 3 bf16 hi+lo, 4 scaled fp16 hi+lo.
 // BAND: a sparsified tree; the strip comes from the leaf row's slab and the
 // pieces go to their place inside the column (A role) or row (B role) band.
 template <int PK, int LEAF, bool BAND>
@@ -279,15 +322,17 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                                                    const double* __restrict__ colmaxA, Thresh th,
                                                    void* __restrict__ pa0, void* __restrict__ pa1,
                                                    void* __restrict__ pb0, void* __restrict__ pb1,
-                                                   BandView bv) {
+                                                   BandView bv, const double* __restrict__ gmax_a,
+                                                   const double* __restrict__ gmax_b) {
     constexpr int TL = 128 / LEAF;
     constexpr int CH = LEAF / 16;
-    constexpr int ES = PK == 3 ? 2 : 4;                  // element bytes
+    constexpr int ES = PK >= 3 ? 2 : 4;                  // element bytes
     constexpr int EPU = 16 / ES;                         // elements per 16-byte unit
     constexpr int PIECE = LEAF * 16 * ES;                // bytes of one piece
     constexpr int UPP = PIECE / 16;                      // units per piece
     constexpr int CPC = 16 / EPU;                        // core matrices per 16-wide K chunk
     constexpr int LDS = 128 + 4;                         // padded staging row
+    constexpr int NPART = PK == 1 ? 1 : 2;               // hi (and lo) parts
     extern __shared__ __align__(16) float raw_dyn[];     // LEAF x LDS staged strip
     float (*raw)[LDS] = reinterpret_cast<float (*)[LDS]>(raw_dyn);
     __shared__ int needA[TL], needB[TL], any;
@@ -298,6 +343,12 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     const int64_t r0 = I * LEAF, c0 = Q0 * LEAF;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
+    // FP16 split: the operand's power-of-two scale, per role
+    float sc_a = 1.f, sc_b = 1.f;
+    if constexpr (PK == 4) {
+        sc_a = ldexpf(1.f, f16_scale_exp(*gmax_a));
+        sc_b = ldexpf(1.f, f16_scale_exp(*gmax_b));
+    }
     if (t == 0) any = 0;
     __syncthreads();
     if (t < TL) {
@@ -362,9 +413,10 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                 const int64_t len = bv.imax[K] - bv.imin[K] + 1;
                 g = (size_t)(bv.aoff[K] + kca * len + (I - bv.imin[K])) * PIECE + (size_t)w * 16;
             } else {
-                g = ((size_t)((Q0 + xa) * CH + kca) * nlp + I) * PIECE + (size_t)w * 16;
+                g = ((size_t)((((Q0 + xa) * (nlp / TL) + I / TL) * CH + kca) * NPART) * TL +
+                     I % TL) * PIECE + (size_t)w * 16;
             }
-            if (PK != 3) {
+            if (PK <= 2) {
                 const float4 v = *reinterpret_cast<const float4*>(src);
                 uint4 h, l;
                 h.x = to_tf32(v.x); l.x = to_tf32(v.x - __uint_as_float(h.x));
@@ -378,15 +430,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                 const float4 v1 = *reinterpret_cast<const float4*>(src + 4);
                 const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * q]);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * q + 1]);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * q] - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * q + 1] - __bfloat162float(h1));
-                    hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                }
+                split16<PK>(f, sc_a, hw, lw);
                 *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pa0) + g) =
                     make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pa1) + g) =
@@ -405,9 +449,10 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                 g = (size_t)(bv.boff[I] + kcb * len + (Q0 + xb - bv.kmin[I])) * PIECE +
                     (size_t)w * 16;
             } else {
-                g = ((size_t)(I * CH + kcb) * nlp + (Q0 + xb)) * PIECE + (size_t)w * 16;
+                g = ((size_t)(((I * (nlp / (2 * TL)) + (Q0 + xb) / (2 * TL)) * CH + kcb) * NPART) *
+                         (2 * TL) + (Q0 + xb) % (2 * TL)) * PIECE + (size_t)w * 16;
             }
-            if (PK != 3) {
+            if (PK <= 2) {
                 float f[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) f[q] = raw[k0 + q][colj];
@@ -423,15 +468,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
 #pragma unroll
                 for (int q = 0; q < 8; ++q) f[q] = raw[k0 + q][colj];
                 uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * q]);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * q + 1]);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * q] - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * q + 1] - __bfloat162float(h1));
-                    hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                }
+                split16<PK>(f, sc_b, hw, lw);
                 *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pb0) + g) =
                     make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4*>(static_cast<unsigned char*>(pb1) + g) =
@@ -655,21 +692,37 @@ cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, d
     const double* lb = B->pyr + off_leaf;
     double* colmaxA = scratch;
     double* rowmaxB = scratch + A->nb;
+    double* gmax = scratch + 2 * A->nb;          // largest leaf of A, of B
     const int blocks = (int)std::min<int64_t>((A->nl + 31) / 32 * 4, 8 * (int64_t)sm_count);
+    cudaError_t e = cudaMemsetAsync(gmax, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
     k_leaf_max<<<dim3((unsigned)std::max(blocks, 1), 2), 256, 0, s>>>(la, lb, A->nb, A->nl,
-                                                                        colmaxA, rowmaxB);
-    cudaError_t e = cudaGetLastError();
+                                                                        colmaxA, rowmaxB, gmax);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const Thresh th = make_thresh(tau, rel);
-    const int pk = A->precision == SPAMM_PREC_TF32 ? 1 : A->precision == SPAMM_PREC_TF32X3 ? 2 : 3;
+    const int pk = A->precision == SPAMM_PREC_TF32     ? 1
+                   : A->precision == SPAMM_PREC_TF32X3 ? 2
+                   : A->precision == SPAMM_PREC_BF16X3 ? 3
+                                                       : 4;
     const int tl = 128 / A->b;
     const size_t smem = (size_t)A->b * (128 + 4) * sizeof(float);
     auto one = [&](const spamm_tree* t, const double* rmB, const double* cmA) -> cudaError_t {
         const bool roleA = rmB != nullptr, roleB = cmA != nullptr;
         void* pa0 = roleA ? t->packA[0] : nullptr;
-        void* pa1 = roleA ? t->packA[1] : nullptr;
         void* pb0 = roleB ? t->packB[0] : nullptr;
-        void* pb1 = roleB ? t->packB[1] : nullptr;
+        void* pa1 = nullptr;
+        void* pb1 = nullptr;
+        if (t->sparse) {
+            // banded layout: one array per part
+            pa1 = roleA ? t->packA[1] : nullptr;
+            pb1 = roleB ? t->packB[1] : nullptr;
+        } else if (pk != 1) {
+            // grouped layout: the lo part of a group follows its hi part
+            const size_t slice = (size_t)128 * 16 * (pk >= 3 ? 2 : 4);   // TL pieces
+            pa1 = pa0 ? static_cast<unsigned char*>(pa0) + slice : nullptr;
+            pb1 = pb0 ? static_cast<unsigned char*>(pb0) + 2 * slice : nullptr;
+        }
         const double* leaf = t->pyr + off_leaf;
         dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));
 #define SPAMM_LP2(PKV, LV, BV)                                                               \
@@ -679,7 +732,8 @@ cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, d
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
         k_leaf_pack<PKV, LV, BV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,   \
                                                          t->nlp, leaf, rmB, cmA, th, pa0,    \
-                                                         pa1, pb0, pb1, band_view(t));       \
+                                                         pa1, pb0, pb1, band_view(t), gmax,  \
+                                                         gmax + 1);                          \
     } while (0)
 #define SPAMM_LP(PKV, LV)                                                                    \
     do {                                                                                     \
@@ -690,7 +744,8 @@ cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, d
     do {                                   \
         if (pk == 1) SPAMM_LP(1, LV);      \
         else if (pk == 2) SPAMM_LP(2, LV); \
-        else SPAMM_LP(3, LV);              \
+        else if (pk == 3) SPAMM_LP(3, LV); \
+        else SPAMM_LP(4, LV);              \
     } while (0)
         if (t->b == 16) SPAMM_LP_B(16);
         else if (t->b == 32) SPAMM_LP_B(32);

@@ -89,12 +89,12 @@ spamm_status ensure_tiles(spamm_ctx* ctx, int64_t tiles) {
 }
 
 spamm_status ensure_need(spamm_ctx* ctx, int64_t nb) {
-    if (2 * nb <= ctx->need_cap) return SPAMM_OK;
+    if (2 * nb + 2 <= ctx->need_cap) return SPAMM_OK;
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->need);
     ctx->need = nullptr;
     ctx->need_cap = 0;
-    const int64_t cap = std::max<int64_t>(2 * nb, 1024);
+    const int64_t cap = std::max<int64_t>(2 * nb + 2, 1024);
     cudaError_t e = cudaMalloc(&ctx->need, sizeof(double) * cap);
     if (e != cudaSuccess) return cuda_err(ctx, e, "norm maxima");
     ctx->need_cap = cap;
@@ -160,7 +160,7 @@ spamm_status spamm_create(spamm_ctx** out, void* stream, const spamm_config* cfg
     spamm_config c;
     if (cfg) c = *cfg; else spamm_config_default(&c);
     if (!valid_leaf(c.leaf)) return SPAMM_ERR_INVALID_ARG;
-    if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_BF16X3) return SPAMM_ERR_INVALID_ARG;
+    if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_F16X3) return SPAMM_ERR_INVALID_ARG;
     if (!(c.tie_rel >= 0.0 && c.tie_rel < 0.5) || c.pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
     for (int i = 0; i < 6; ++i)
         if (c.reserved[i]) return SPAMM_ERR_INVALID_ARG;
@@ -290,14 +290,13 @@ static spamm_status new_tree(spamm_ctx* ctx, const float* A, int64_t n, int64_t 
         if (e == cudaSuccess) e = cudaMalloc(&t->panB, pn);
     }
     if (e == cudaSuccess && packs && precision_uses_tc(t->precision)) {
+        // grouped layout: every part of a role in one array (packA[1] unused)
         t->pack_bytes = pack_bytes_for(t->precision, t->nlp, b);
-        const int arrays = pack_arrays_for(t->precision);
-        for (int i = 0; i < arrays && e == cudaSuccess; ++i) {
-            e = cudaMalloc(&t->packA[i], t->pack_bytes);
-            if (e == cudaSuccess) e = cudaMalloc(&t->packB[i], t->pack_bytes);
-            if (e == cudaSuccess) e = cudaMemsetAsync(t->packA[i], 0, t->pack_bytes, ctx->stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(t->packB[i], 0, t->pack_bytes, ctx->stream);
-        }
+        const size_t all = t->pack_bytes * (size_t)pack_arrays_for(t->precision);
+        e = cudaMalloc(&t->packA[0], all);
+        if (e == cudaSuccess) e = cudaMalloc(&t->packB[0], all);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->packA[0], 0, all, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->packB[0], 0, all, ctx->stream);
     }
     if (e != cudaSuccess) {
         const spamm_status st = cuda_err(ctx, e, "tree allocation");
@@ -407,7 +406,7 @@ spamm_status spamm_sparsify(spamm_ctx* ctx, const float* A, int64_t n, int64_t l
     }
     aoff[nl] = pa;
     boff[nl] = pb;
-    const int64_t piece = (int64_t)b * 16 * (t->precision == SPAMM_PREC_BF16X3 ? 2 : 4);
+    const int64_t piece = (int64_t)b * 16 * ((t->precision == SPAMM_PREC_BF16X3 || t->precision == SPAMM_PREC_F16X3) ? 2 : 4);
     e = cudaMalloc(&t->offs, sizeof(int64_t) * offs.size());
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(t->offs, offs.data(), sizeof(int64_t) * offs.size(),

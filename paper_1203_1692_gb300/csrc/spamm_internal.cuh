@@ -71,6 +71,29 @@ struct Thresh {
     int e_lo, e_hi;  // biased FP64 exponents of lo2 and hi2
 };
 
+// FP16 split precision: an operand is scaled by 2^k so that its largest leaf
+// norm (an upper bound of every element) lands just below 2^15, inside the
+// fp16 range; k from the largest squared leaf norm.  Scaling by a power of
+// two is exact, and the product is scaled back by 2^-(kA + kB).  FP32 leaf
+// norms stay below 2^136, so k >= -120; k is capped at 126 so that 2^k and
+// 2^-k are normal floats (an operand whose largest leaf norm is below
+// 2^-111 is then scaled less than fully, into fp16's subnormal range).
+__device__ inline int f16_scale_exp(double gmax2) {
+    if (!(gmax2 > 0.0)) return 0;
+    int e;
+    frexp(sqrt(gmax2), &e);                // max leaf norm in [2^(e-1), 2^e)
+    const int k = 15 - e;
+    return k < -126 ? -126 : (k > 126 ? 126 : k);
+}
+
+// The unscale 2^-(kA + kB) as two normal floats whose product it is
+// (kA + kB lies in [-252, 252], beyond one float's exponent range).
+__device__ inline float2 f16_unscale(double gmax2_a, double gmax2_b) {
+    const int s = f16_scale_exp(gmax2_a) + f16_scale_exp(gmax2_b);
+    const int h = s / 2;
+    return make_float2(ldexpf(1.f, -h), ldexpf(1.f, -(s - h)));
+}
+
 // Exact keep decision for finite non-negative squared norms a, b, and the
 // tie-band flag.  On GB300 the FP64 pipe is narrow, so the exponent fields
 // settle every pair whose product lies clearly outside [lo2, hi2] with

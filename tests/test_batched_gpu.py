@@ -15,7 +15,7 @@ from tests.spamm_check import rel_max_err
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4, "tf32": 5e-3}
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "f16x3": 1e-5, "bf16x3": 1e-4, "tf32": 5e-3}
 
 
 def _mix(seed=0):
@@ -60,7 +60,7 @@ def _batched(P, prec, cases, ctx=None):
     return [C.cpu().numpy() for C in Cs], ctx
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp32", "tf32", "f16x3"])
 def test_batched_equals_single_bit_for_bit(prec):
     import paper_1203_1692_gb300 as P
     cases = _mix()
@@ -73,7 +73,7 @@ def test_batched_equals_single_bit_for_bit(prec):
     assert ctx.stats()["leaf_triples"] == total
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "f16x3"])
 def test_batched_matches_oracle(prec):
     import paper_1203_1692_gb300 as P
     cases = _mix(seed=1)[:4]

@@ -12,7 +12,7 @@ from tests.spamm_check import as_set, rel_max_err
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4}
+TOL = {"tf32x3": 1e-5, "f16x3": 1e-5, "bf16x3": 1e-4}
 
 
 def _n2(A):
@@ -20,7 +20,7 @@ def _n2(A):
 
 
 @pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("tf32x3", 64), ("bf16x3", 32),
-                                    ("tf32x3", 128)])
+                                    ("tf32x3", 128), ("f16x3", 64)])
 @pytest.mark.parametrize("n,tau", [(1000, 1e-6), (777, 1e-4), (1500, 1e-8)])
 def test_sparsified_product_equals_dense_product(prec, b, n, tau):
     """At the consistent tolerance the sparsified operands keep exactly the

@@ -22,7 +22,7 @@ from tests.spamm_check import (as_set, blocks_from, compare_triples, rel_max_err
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4, "tf32": 5e-3}
+TOL = {"tf32x3": 1e-5, "f16x3": 1e-5, "bf16x3": 1e-4, "tf32": 5e-3}
 
 
 def _run(A, B, b, tau, precision, alpha=1.0, beta=0.0, C0=None):
@@ -77,7 +77,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "f16x3"])
 @pytest.mark.parametrize("n,b,kind,tau", CASES)
 def test_tc_parity_with_oracle(prec, n, b, kind, tau):
     A = _matrix(kind, n)
@@ -89,7 +89,7 @@ def test_tc_parity_with_oracle(prec, n, b, kind, tau):
     assert rel_max_err(C, ref.C) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "f16x3"])
 def test_tc_alpha_beta(prec):
     n, b = 260, 16
     A = gen.exp_decay_nonsym(n, 0.85, seed=2)
@@ -121,7 +121,7 @@ def test_tc_water_like_n7500_sampled(prec):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "f16x3"])
 def test_tc_water_like_n7500_bench_configuration(prec):
     """The bench's own launch configuration (leaf 64, the equal-error tau
     1e-4) on the n = 7500 workload, sampled C blocks against the oracle."""
@@ -137,7 +137,7 @@ def test_tc_water_like_n7500_bench_configuration(prec):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 16), ("tf32", 16),
-                                    ("tf32x3", 64)])
+                                    ("tf32x3", 64), ("f16x3", 64)])
 def test_tc_algebraic_n16384_sampled(prec, b):
     """The algebraic-decay configuration at full size (n = 16384, tau =
     1e-8, leaf products in TF32, split BF16 x3 and 3xTF32): sampled C blocks
@@ -157,7 +157,8 @@ def test_tc_algebraic_n16384_sampled(prec, b):
     assert ctx.stats()["leaf_triples"] == len(flat)
 
 
-@pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 32), ("tf32x3", 64)])
+@pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 32), ("tf32x3", 64),
+                                    ("f16x3", 64)])
 def test_tc_stale_pieces_never_reach_C(prec, b):
     """A multiply packs only the leaves that can take part in a kept product
     (Sec. III culling is monotone in each norm).  Pieces it does not pack
@@ -194,7 +195,7 @@ SLICE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "f16x3"])
 @pytest.mark.parametrize("n,b,kind,tau", SLICE_CASES)
 def test_slice_cull_parity_with_oracle(prec, n, b, kind, tau):
     """Sub-leaf cull along k (16-wide slices of each kept leaf product,
@@ -245,3 +246,36 @@ def test_slice_cull_batched_equals_single():
         c1 = P.Context(leaf=64, precision="tf32x3", slice=16)
         t1 = c1.build_norms(A)
         assert torch.equal(c1.multiply(t1, t1, tau), C)
+
+
+def test_f16x3_wide_dynamic_range():
+    """The FP16 split scales each operand by a power of two so its largest
+    leaf norm sits just below 2^15; entries many decades smaller (down to
+    fp16 subnormals after scaling) still reach 3xTF32-class accuracy in the
+    max-norm."""
+    n, b, tau = 600, 32, 0.0
+    rng = np.random.default_rng(3)
+    A = (gen.uniform_dense(n, seed=1, symmetric=False).astype(np.float64)
+         * 10.0 ** rng.uniform(-12, 6, size=(n, n))).astype(np.float32)
+    B = (gen.uniform_dense(n, seed=2, symmetric=False).astype(np.float64) * 1e-20).astype(np.float32)
+    ref = O.multiply(A, B, b, tau)
+    for prec in ("f16x3", "tf32x3"):
+        _, C = _run(A, B, b, tau, prec)
+        assert rel_max_err(C, ref.C) <= TOL[prec], prec
+
+
+@pytest.mark.parametrize("sa,sb", [(110, -120), (-120, 100), (-50, -45)])
+def test_f16x3_extreme_operand_scales(sa, sb):
+    """Operands near the ends of the float range: the power-of-two scales
+    (one per operand, up to 2^126 each way) keep every split inside fp16's
+    range, and the unscale 2^-(kA + kB), which can lie outside one float's
+    exponent range, is applied as two exact factors."""
+    n, b, tau = 520, 32, 0.0
+    A = (gen.uniform_dense(n, seed=5, symmetric=False).astype(np.float64) * 2.0 ** sa).astype(np.float32)
+    B = (gen.uniform_dense(n, seed=6, symmetric=False).astype(np.float64) * 2.0 ** sb).astype(np.float32)
+    assert np.isfinite(A).all() and np.isfinite(B).all() and np.abs(B).max() > 2.0 ** -126
+    ref = O.multiply(A, B, b, tau)
+    assert np.abs(ref.C).max() > 2.0 ** -100          # a normal-range product
+    _, C = _run(A, B, b, tau, "f16x3")
+    assert np.isfinite(C).all()
+    assert rel_max_err(C, ref.C) <= TOL["f16x3"]
