@@ -598,7 +598,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     }
                     const uint32_t cnt = st_count[s];
                     consumed_s = stage_it + 1;
-                    for (uint32_t jj = 0; jj < cnt && ok; ++jj, ++i) {
+                    // the stage's masks in one go, then its slots unrolled (slot
+                    // offsets become constants); this loop is the MMA issue path
+                    unsigned long long mk0[T::kSPS], mk1[T::kSPS];
+#pragma unroll
+                    for (int jj = 0; jj < T::kSPS; ++jj) {
+                        mk0[jj] = st_mask[s][jj][0];
+                        mk1[jj] = st_mask[s][jj][1];
+                    }
+                    const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
+#pragma unroll
+                    for (int jj = 0; jj < T::kSPS; ++jj) {
+                        if ((uint32_t)jj >= cnt || !ok) break;
                         if (i % kChunkIters == 0) {
                             const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
                             if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
@@ -610,9 +621,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                             // clear the chunk accumulator: 0 * 0, input accumulator off
                             mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256), dis0, 0u);
                         }
-                        const unsigned long long mask0 = st_mask[s][jj][0];
-                        const unsigned long long mask1 = st_mask[s][jj][1];
-                        const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
+                        const unsigned long long mask0 = mk0[jj];
+                        const unsigned long long mask1 = mk1[jj];
                         const uint32_t a_hi = sbuf + jj * (uint32_t)T::kASlot;
                         const uint32_t a_lo = a_hi + T::kSlice;
                         const uint32_t b_hi =
@@ -725,6 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                             tc_commit(smem_u32(&bar_accf[ccount & 1]));
                             ++ccount;
                         }
+                        ++i;
                     }
                     // the stage's MMAs have read its shared memory once they complete
                     tc_commit(smem_u32(&bar_empty[s]));
