@@ -343,12 +343,6 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     const int64_t r0 = I * LEAF, c0 = Q0 * LEAF;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
-    // FP16 split: the operand's power-of-two scale, per role
-    float sc_a = 1.f, sc_b = 1.f;
-    if constexpr (PK == 4) {
-        sc_a = ldexpf(1.f, f16_scale_exp(*gmax_a));
-        sc_b = ldexpf(1.f, f16_scale_exp(*gmax_b));
-    }
     if (t == 0) any = 0;
     __syncthreads();
     if (t < TL) {
@@ -361,6 +355,12 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     }
     __syncthreads();
     if (!any) return;
+    // FP16 split: the operand's power-of-two scale, per role
+    float sc_a = 1.f, sc_b = 1.f;
+    if constexpr (PK == 4) {
+        sc_a = ldexpf(1.f, f16_scale_exp(*gmax_a));
+        sc_b = ldexpf(1.f, f16_scale_exp(*gmax_b));
+    }
     const int cq = 4 * lane;
     if constexpr (BAND) {
         // the slab holds the columns [kmin b, (kmax + 1) b) of this leaf row

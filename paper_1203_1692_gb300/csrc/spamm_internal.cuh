@@ -78,10 +78,13 @@ struct Thresh {
 // norms stay below 2^136, so k >= -120; k is capped at 126 so that 2^k and
 // 2^-k are normal floats (an operand whose largest leaf norm is below
 // 2^-111 is then scaled less than fully, into fp16's subnormal range).
+// Integer work only (the FP64 pipe is narrow): with gmax2 in [2^E, 2^(E+1)),
+// the largest leaf norm sqrt(gmax2) lies below 2^e for e = floor(E/2) + 1.
 __device__ inline int f16_scale_exp(double gmax2) {
     if (!(gmax2 > 0.0)) return 0;
-    int e;
-    frexp(sqrt(gmax2), &e);                // max leaf norm in [2^(e-1), 2^e)
+    const long long bits = __double_as_longlong(gmax2);
+    const int E = (int)((bits >> 52) & 0x7FF) - 1023;   // subnormals: -1023
+    const int e = (E >> 1) + 1;
     const int k = 15 - e;
     return k < -126 ? -126 : (k > 126 ? 126 : k);
 }
