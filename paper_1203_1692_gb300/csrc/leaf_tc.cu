@@ -51,6 +51,8 @@
 // the block drain its copies and MMAs, free TMEM and exit.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "spamm_internal.cuh"
 
 namespace spamm {
@@ -272,7 +274,8 @@ constexpr int kMaxBatch = 64;
 struct TcBatch {
     TcProd prods[kMaxBatch];
     int count;             // products
-    int total;             // work items (tiles) of all products
+    int first;             // first work item of this launch (0 but for banded launches)
+    int total;             // work items (tiles) of all products; this launch ends here
     unsigned int* status;  // timeout status word
 };
 
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         bool ok = true;
         const size_t piece = (size_t)LEAF * 16 * T::kEsize;
         int pi = 0;
-        for (int k = blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+        for (int k = bt.first + blockIdx.x; k < bt.total && ok; k += gridDim.x) {
             product_of(k, pi);
             if (sp_skip[pi]) continue;
             const TcProd& q = bt.prods[pi];
@@ -585,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
             uint32_t dacc = tmem;
             int pi = 0;
-            for (int k = blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+            for (int k = bt.first + blockIdx.x; k < bt.total && ok; k += gridDim.x) {
                 product_of(k, pi);
                 if (sp_skip[pi]) continue;
                 const TcProd& q = bt.prods[pi];
@@ -757,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         uint32_t ccount = 0;
         bool ok = true;
         int pi = 0;
-        for (int k = blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+        for (int k = bt.first + blockIdx.x; k < bt.total && ok; k += gridDim.x) {
             product_of(k, pi);
             if (sp_skip[pi]) continue;
             const TcProd& q = bt.prods[pi];
@@ -896,7 +899,8 @@ cudaError_t launch_b(spamm_ctx* ctx, const TcBatch& bt) {
     cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, PREC, BAND>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = bt.total < ctx->sm_count ? bt.total : ctx->sm_count;
+    const int items = bt.total - bt.first;
+    const int grid = items < ctx->sm_count ? items : ctx->sm_count;
     if (grid <= 0) return cudaSuccess;
     k_leaf_tc<LEAF, PREC, BAND><<<grid, kThreads, smem, ctx->stream>>>(bt);
     return cudaGetLastError();
@@ -909,84 +913,131 @@ cudaError_t launch_t(spamm_ctx* ctx, const TcBatch& bt, bool band) {
 
 }  // namespace
 
+// The launch table for jobs[0, count) (count <= kMaxBatch); returns whether
+// any operand is sparsified (the BAND kernels).
+static bool fill_batch(spamm_ctx* ctx, const LeafJob* jobs, int count, TcBatch& bt) {
+    memset(&bt, 0, sizeof(bt));
+    bt.count = count;
+    bt.status = &ctx->ctl->status;
+    int base = 0;
+    bool band = false;
+    for (int i = 0; i < bt.count; ++i) {
+        const LeafJob& jb = jobs[i];
+        TcProd& q = bt.prods[i];
+        for (int h = 0; h < 2; ++h) {
+            q.pa[h] = jb.A->packA[h] ? jb.A->packA[h] : jb.A->packA[0];
+            q.pb[h] = jb.B->packB[h] ? jb.B->packB[h] : jb.B->packB[0];
+        }
+        q.nlp = jb.A->nlp;
+        q.C = jb.C;
+        q.ldc = jb.ldc;
+        q.n = jb.A->n;
+        q.alpha = jb.alpha;
+        q.beta = jb.beta;
+        q.ctl = jb.sub->ctl;
+        q.pool = jb.sub->pool;
+        q.off = jb.sub->tile_off;
+        q.steps = jb.sub->tile_steps;
+        q.iters = jb.sub->tile_iters;
+        q.gmax = jb.sub->need + 2 * jb.A->nb;
+        if (jb.A->sparse) {
+            const BandView v = band_view(jb.A);
+            q.a_lo = v.imin;
+            q.a_hi = v.imax;
+            q.a_off = v.aoff;
+            band = true;
+        }
+        if (jb.B->sparse) {
+            const BandView v = band_view(jb.B);
+            q.b_lo = v.kmin;
+            q.b_hi = v.kmax;
+            q.b_off = v.boff;
+            band = true;
+        }
+        q.sl = (jb.A->slices && jb.B->slices) ? jb.A->slices : 1;
+        q.tr = tile_rows(jb.A);
+        q.tc = tile_cols(jb.A);
+        q.S = jb.sub->last_S;
+        q.base = base;
+        base += q.tr * q.tc;
+    }
+    bt.total = base;
+    return band;
+}
+
+static cudaError_t dispatch(spamm_ctx* ctx, const TcBatch& bt, bool band) {
+    const int p = ctx->cfg.precision;
+    const int b = ctx->cfg.leaf;
+    cudaError_t e;
+    if (b == 16) {
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band);
+        else e = launch_t<16, SPAMM_PREC_F16X3>(ctx, bt, band);
+    } else if (b == 32) {
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt, band);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt, band);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band);
+        else e = launch_t<32, SPAMM_PREC_F16X3>(ctx, bt, band);
+    } else if (b == 64) {
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt, band);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt, band);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band);
+        else e = launch_t<64, SPAMM_PREC_F16X3>(ctx, bt, band);
+    } else if (b == 128) {
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt, band);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt, band);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band);
+        else e = launch_t<128, SPAMM_PREC_F16X3>(ctx, bt, band);
+    } else {
+        e = cudaErrorNotSupported;
+    }
+    return e;
+}
+
 // All jobs share the context's leaf size and precision.  At most kMaxBatch
 // products go into one launch.
 cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) {
     for (int j0 = 0; j0 < count; j0 += kMaxBatch) {
         TcBatch bt;
-        memset(&bt, 0, sizeof(bt));
-        bt.count = count - j0 < kMaxBatch ? count - j0 : kMaxBatch;
-        bt.status = &ctx->ctl->status;
-        int base = 0;
-        bool band = false;
-        for (int i = 0; i < bt.count; ++i) {
-            const LeafJob& jb = jobs[j0 + i];
-            TcProd& q = bt.prods[i];
-            for (int h = 0; h < 2; ++h) {
-                q.pa[h] = jb.A->packA[h] ? jb.A->packA[h] : jb.A->packA[0];
-                q.pb[h] = jb.B->packB[h] ? jb.B->packB[h] : jb.B->packB[0];
-            }
-            q.nlp = jb.A->nlp;
-            q.C = jb.C;
-            q.ldc = jb.ldc;
-            q.n = jb.A->n;
-            q.alpha = jb.alpha;
-            q.beta = jb.beta;
-            q.ctl = jb.sub->ctl;
-            q.pool = jb.sub->pool;
-            q.off = jb.sub->tile_off;
-            q.steps = jb.sub->tile_steps;
-            q.iters = jb.sub->tile_iters;
-            q.gmax = jb.sub->need + 2 * jb.A->nb;
-            if (jb.A->sparse) {
-                const BandView v = band_view(jb.A);
-                q.a_lo = v.imin;
-                q.a_hi = v.imax;
-                q.a_off = v.aoff;
-                band = true;
-            }
-            if (jb.B->sparse) {
-                const BandView v = band_view(jb.B);
-                q.b_lo = v.kmin;
-                q.b_hi = v.kmax;
-                q.b_off = v.boff;
-                band = true;
-            }
-            q.sl = (jb.A->slices && jb.B->slices) ? jb.A->slices : 1;
-            q.tr = tile_rows(jb.A);
-            q.tc = tile_cols(jb.A);
-            q.S = jb.sub->last_S;
-            q.base = base;
-            base += q.tr * q.tc;
-        }
-        bt.total = base;
-        const int p = ctx->cfg.precision;
-        const int b = ctx->cfg.leaf;
-        cudaError_t e;
-        if (b == 16) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band);
-            else if (p == SPAMM_PREC_BF16X3) e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band);
-            else e = launch_t<16, SPAMM_PREC_F16X3>(ctx, bt, band);
-        } else if (b == 32) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt, band);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt, band);
-            else if (p == SPAMM_PREC_BF16X3) e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band);
-            else e = launch_t<32, SPAMM_PREC_F16X3>(ctx, bt, band);
-        } else if (b == 64) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt, band);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt, band);
-            else if (p == SPAMM_PREC_BF16X3) e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band);
-            else e = launch_t<64, SPAMM_PREC_F16X3>(ctx, bt, band);
-        } else if (b == 128) {
-            if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt, band);
-            else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt, band);
-            else if (p == SPAMM_PREC_BF16X3) e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band);
-            else e = launch_t<128, SPAMM_PREC_F16X3>(ctx, bt, band);
-        } else {
-            e = cudaErrorNotSupported;
-        }
+        const bool band =
+            fill_batch(ctx, jobs + j0, count - j0 < kMaxBatch ? count - j0 : kMaxBatch, bt);
+        const cudaError_t e = dispatch(ctx, bt, band);
         if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One product in `bands` launches, each a run of whole tile-row groups (the
+// work order walks kGroupRows tile rows at a time), so that after each
+// launch the rows of C it finished are final; `done` is told which rows
+// (e.g. to start copying them out while the next band computes).  Every
+// tile is computed by exactly one launch, as in the single launch, so C is
+// the same bit for bit.
+cudaError_t launch_leaf_tc_banded(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                                  float alpha, float beta, float* C, int64_t ldc, int bands,
+                                  cudaError_t (*done)(void*, int64_t, int64_t), void* user) {
+    LeafJob jb{A, B, ctx, alpha, beta, C, ldc};
+    TcBatch bt;
+    const bool band = fill_batch(ctx, &jb, 1, bt);
+    const int tr = bt.prods[0].tr, tc = bt.prods[0].tc;
+    const int groups = (tr + kGroupRows - 1) / kGroupRows;
+    if (bands > groups) bands = groups;
+    if (bands < 1) bands = 1;
+    int g0 = 0;
+    for (int i = 0; i < bands; ++i) {
+        const int g1 = (int)((int64_t)groups * (i + 1) / bands);
+        bt.first = g0 * kGroupRows * tc;
+        bt.total = (g1 * kGroupRows < tr ? g1 * kGroupRows : tr) * tc;
+        cudaError_t e = dispatch(ctx, bt, band);
+        if (e != cudaSuccess) return e;
+        const int64_t r0 = (int64_t)g0 * kGroupRows * kTileRows;
+        const int64_t r1 = std::min<int64_t>((int64_t)g1 * kGroupRows * kTileRows, A->n);
+        if (done && r1 > r0) {
+            e = done(user, r0, r1);
+            if (e != cudaSuccess) return e;
+        }
+        g0 = g1;
     }
     return cudaSuccess;
 }

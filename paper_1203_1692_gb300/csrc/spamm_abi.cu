@@ -499,6 +499,20 @@ spamm_status spamm_tree_norms(spamm_ctx* ctx, const spamm_tree* t, double* host_
     return cuda_err(ctx, e, "norm copy");
 }
 
+// Copy-out hook of the banded leaf launch: rows [r0, r1) of the staged C
+// go to the host on aux[0] once the band that finished them has run.
+static cudaError_t copy_rows_out(void* user, int64_t r0, int64_t r1) {
+    spamm_ctx* ctx = static_cast<spamm_ctx*>(user);
+    const int64_t n = ctx->last_n;
+    cudaError_t e = cudaEventRecord(ctx->aux_ev[0], ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux[0], ctx->aux_ev[0], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->band_host + r0 * n, ctx->dC + r0 * n,
+                            sizeof(float) * (size_t)((r1 - r0) * n), cudaMemcpyDeviceToHost,
+                            ctx->aux[0]);
+    return e;
+}
+
 static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
                                          const spamm_tree* B, double tau, float alpha,
                                          float beta, float* C, int64_t ldc) {
@@ -515,6 +529,9 @@ static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
     if (e == cudaSuccess) {
         if (ctx->cfg.precision == SPAMM_PREC_FP32)
             e = launch_leaf_simt(ctx, A, B, alpha, beta, C, ldc);
+        else if (ctx->band_host)
+            e = launch_leaf_tc_banded(ctx, A, B, alpha, beta, C, ldc, ctx->band_count,
+                                      copy_rows_out, ctx);
         else
             e = launch_leaf_tc(ctx, A, B, alpha, beta, C, ldc);
     }
@@ -1080,9 +1097,28 @@ spamm_status spamm_multiply_host(spamm_ctx* ctx, const float* A, const float* B,
         if (st != SPAMM_OK) return st;
         tb = ctx->hostTreeB;
     }
+    // tensor-core path: C leaves in three bands, each copied out (aux[0])
+    // while the next band computes; the FP32 path copies it after the fact
+    const bool banded = precision_uses_tc(ctx->cfg.precision);
+    if (banded) {
+        st = ensure_aux(ctx);
+        if (st != SPAMM_OK) return st;
+        ctx->band_host = C;
+        ctx->band_count = 3;
+    }
     st = spamm_multiply(ctx, ctx->hostTreeA, tb, tau, alpha, beta, ctx->dC, n);
-    if (st != SPAMM_OK) return st;
-    e = cudaMemcpyAsync(C, ctx->dC, bytes, cudaMemcpyDeviceToHost, s);
+    ctx->band_host = nullptr;
+    ctx->band_count = 0;
+    if (st != SPAMM_OK) {
+        if (banded) cudaStreamSynchronize(ctx->aux[0]);
+        return st;
+    }
+    if (banded) {
+        e = cudaEventRecord(ctx->aux_ev[1], ctx->aux[0]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->aux_ev[1], 0);
+    } else {
+        e = cudaMemcpyAsync(C, ctx->dC, bytes, cudaMemcpyDeviceToHost, s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "device to host copy");
     return status_from_ctl(ctx, *ctx->ctl_host);

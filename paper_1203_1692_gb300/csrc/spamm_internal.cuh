@@ -230,6 +230,10 @@ struct spamm_ctx {
     int64_t stage_elems;
     spamm_tree* hostTreeA;
     spamm_tree* hostTreeB;
+    // set by spamm_multiply_host around its multiply: copy the rows of C out
+    // to this host array band by band, on aux[0], while later bands compute
+    float* band_host;
+    int band_count;
     // batched multiplies: one sub-context (pool, control block, tile arrays)
     // per product, created on demand and reused
     std::vector<spamm_ctx*> subs;
@@ -309,6 +313,11 @@ cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tr
 // leaf_tc.cu
 cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                            float alpha, float beta, float* C, int64_t ldc);
+// The same product in `bands` launches of whole tile-row groups; after each,
+// done(user, row0, row1) is told which rows of C are final.
+cudaError_t launch_leaf_tc_banded(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
+                                  float alpha, float beta, float* C, int64_t ldc, int bands,
+                                  cudaError_t (*done)(void*, int64_t, int64_t), void* user);
 // One product of a batched leaf launch: its trees, the context that ran its
 // cull and grouping (pool, control block, tile arrays), and its C.
 struct LeafJob {

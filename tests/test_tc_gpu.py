@@ -279,3 +279,34 @@ def test_f16x3_extreme_operand_scales(sa, sb):
     _, C = _run(A, B, b, tau, "f16x3")
     assert np.isfinite(C).all()
     assert rel_max_err(C, ref.C) <= TOL["f16x3"]
+
+
+@pytest.mark.parametrize("prec,b,n,pinned", [("f16x3", 64, 2600, True), ("tf32x3", 32, 1500, False),
+                                             ("f16x3", 16, 700, True), ("bf16x3", 128, 300, False),
+                                             ("tf32", 64, 5000, True)])
+def test_host_entry_bands_equal_device_multiply(prec, b, n, pinned):
+    """The host entry point runs the leaf products in (up to) three launches
+    of whole tile-row groups and copies each group's rows of C out while the
+    next computes.  C is the device multiply's, bit for bit, with alpha and
+    beta, from pageable and from pinned host memory."""
+    import paper_1203_1692_gb300 as P
+    A = gen.exp_decay(n, 0.9, seed=3)
+    B = gen.uniform_dense(n, seed=4, symmetric=False)
+    C0 = gen.uniform_dense(n, seed=5, symmetric=False)
+    tau, alpha, beta = 1e-5, 0.75, -0.5
+    _, Cd = _run(A, B, b, tau, prec, alpha, beta, C0)
+    ctx = P.Context(leaf=b, precision=prec)
+    if pinned:
+        Ah = torch.from_numpy(A).pin_memory()
+        Bh = torch.from_numpy(B).pin_memory()
+        Ch = torch.from_numpy(C0.copy()).pin_memory()
+        ctx.multiply_host(Ah, Bh, tau, alpha, beta, C=Ch)
+        Ch = Ch.numpy()
+    else:
+        Ch = C0.copy()
+        ctx.multiply_host(A, B, tau, alpha, beta, C=Ch)
+    assert np.array_equal(Ch, Cd)
+    # and again on the same context (staging and trees reused)
+    Ch2 = C0.copy()
+    ctx.multiply_host(A, B, tau, alpha, beta, C=Ch2)
+    assert np.array_equal(Ch2, Cd)
