@@ -48,6 +48,9 @@ WORKLOADS = {
     "sparse65536": "exponential decay a_ij = u_ij 0.9^|i-j| (n=65536), squared at tau=1e-6 "
                    "with sparsified storage (drop tolerance tau / ||A||_F, banded leaves and "
                    "packs) against the dense trees, leaf 64",
+    "nsweep": "exponential decay a_ij = u_ij 0.9^|i-j| (the n=1024 configuration's matrix "
+              "family) for n = 256 ... 16384, A=B, b=16, tau=1e-6: SpAMM (FP32 and "
+              "tensor-core) against cuBLAS SGEMM at every n",
     "batched64": "64 independent products C_p = A_p A_p, n log-uniform in [512, 8192], "
                  "a_ij = u_ij lambda^|i-j| with lambda uniform in [0.8, 0.95], tau=1e-7, "
                  "one persistent leaf launch in a captured CUDA graph, leaf size and "
@@ -152,6 +155,16 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def leaf_alg_bytes(st, n_sq, b, precision):
+    """Algorithmic bytes of one leaf-product launch: C written once (4 n^2)
+    plus every operand leaf a kept product needs read once at 4 B per element
+    (the packed A-role and B-role leaves the library counts; at most 4 n^2
+    each).  The FP32 SIMT kernel reads A itself: A read once, C written once."""
+    if precision == "fp32":
+        return 2 * 4.0 * n_sq
+    return 4.0 * n_sq + 4.0 * b * b * (st["packed_leaves_a"] + st["packed_leaves_b"])
+
+
 def leaf_roofline(precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_ms, kernel_traffic,
                   dev_sms):
     """Roofline of the leaf-product kernel.  Its algorithmic flops are the
@@ -189,8 +202,9 @@ def leaf_roofline(precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_m
                  "flops_tflops": flops_rate, "flops_frac": flops_rate / fpeak,
                  "bytes_gbs": bytes_rate, "bytes_frac": bytes_rate / hbm,
                  "note": f"of {peak_src}; algorithmic flops = 2 b^3 per kept leaf triple "
-                         "(2 b^2 x 16 per kept slice product); algorithmic bytes = operands "
-                         "read once + C written once"})
+                         "(2 b^2 x 16 per kept slice product); algorithmic bytes = C written "
+                         "once + every operand leaf a kept product needs read once (4 B per "
+                         "element)"})
     return roof
 
 
@@ -520,7 +534,7 @@ def run_batched(args, P, dev, rank, world, dist):
         return
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    alg_bytes = sum(2 * 4.0 * n * n for n in ns)        # A (= B) read, C written
+    alg_bytes = leaf_alg_bytes(st, sum(float(n) * n for n in ns), b, args.precision)
     roof = leaf_roofline(args.precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_ms,
                          TRAFFIC.get(("k_leaf_tc", args.workload, args.precision, b)), sms)
     cpu = None
@@ -725,6 +739,111 @@ def run_sparse(args, P, dev, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_nsweep(args, P, dev, rank, world, dist):
+    """SpAMM against dense SGEMM as n grows (the paper's effective-rate and
+    cycle-count-versus-n figures, on GB300): per n one step (norm tree +
+    multiply) of plain FP32 SpAMM and of the tensor-core precision, and one
+    cuBLAS SGEMM, each the median of CUDA-event timed runs."""
+    import torch
+    from spamm_inputs import device as D
+    torch.backends.cuda.matmul.allow_tf32 = False
+    b = 16 if args.leaf == "auto" else int(args.leaf)
+    tau = 1e-6 if args.tau == "auto" else float(args.tau)
+    ns = [256, 512, 1024, 2048, 4096, 8192, 16384]
+    reps = max(3, args.steps)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def med(fn):
+        for _ in range(max(2, args.warmup)):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()            # L2 flushed between timed runs (small n fits in it)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    rows, launches = [], 0
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    for n in ns:
+        A = D.exp_decay(n, 0.9, seed=0, device=dev)
+        Cs = torch.empty_like(A)
+        ms_sgemm = med(lambda: torch.mm(A, A, out=Cs))
+        row = {"n": n, "sgemm_ms": ms_sgemm,
+               "sgemm_effective_tflops": 2.0 * n ** 3 / (ms_sgemm * 1e-3) / 1e12}
+        for prec in ("fp32", args.precision):
+            ctx = P.Context(leaf=b, precision=prec, checked=True)
+            tree = ctx.build_norms(A)
+            C = torch.empty_like(A)
+            ctx.multiply(tree, tree, tau, C=C)
+            ctx.set_checked(False)
+
+            def step():
+                tree.rebuild(A)
+                ctx.multiply(tree, tree, tau, C=C)
+
+            ms = med(step)
+            st = ctx.stats()
+            launches += kernels_per_step(st["depth"], b, prec) * reps
+            scale = float(Cs.abs().max())
+            row[prec] = {"ms": ms, "ms_numeric": st["ms_numeric"],
+                         "kept_leaf_triples": st["leaf_triples"],
+                         "kept_fraction": st["leaf_triples"] / float(-(-n // b)) ** 3,
+                         "kept_tflops": st["kept_flops"] / (ms * 1e-3) / 1e12,
+                         "effective_tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                         "speedup_vs_sgemm": ms_sgemm / ms,
+                         "max_rel_diff_vs_sgemm": float((C - Cs).abs().max()) / scale,
+                         "alg_bytes": leaf_alg_bytes(st, float(n) * n, b, prec)}
+            tree.close()
+            ctx.close()
+        rows.append(row)
+        del A, Cs
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    tc = args.precision
+    cross = next((r["n"] for r in rows if r[tc]["speedup_vs_sgemm"] > 1.0), None)
+    cross32 = next((r["n"] for r in rows if r["fp32"]["speedup_vs_sgemm"] > 1.0), None)
+    big = [r for r in rows if r["n"] >= 2048]
+    slope = {p: float(np.polyfit(np.log([r["n"] for r in big]),
+                                 np.log([r[p]["ms"] for r in big]), 1)[0]) for p in ("fp32", tc)}
+    slope["sgemm"] = float(np.polyfit(np.log([r["n"] for r in big]),
+                                      np.log([r["sgemm_ms"] for r in big]), 1)[0])
+    last = rows[-1]
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        A1 = gen.exp_decay(4096, 0.9, seed=0)
+        v, threads, desc, _ = cpu_sample(A1, b, tau, args.cpu_seconds)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": desc + " (n = 4096 of the sweep)"}
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = leaf_roofline(tc, peaks, peak_src, clk, last[tc]["kept_tflops"] * 1e12 *
+                         last[tc]["ms"] * 1e-3, last[tc]["alg_bytes"],
+                         last[tc]["ms_numeric"], None, sms)
+    line = {
+        "metric": "SpAMM vs dense SGEMM across n: kept leaf TFLOP/s and speedup (exp decay, b=16)",
+        "value": last[tc]["kept_tflops"], "unit": "TFLOP/s", "n_gpus": world, "steps": reps,
+        "warmup": args.warmup, "ms_per_step": last[tc]["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": tc, "data": "synthetic",
+        "config": {"workload": WORKLOADS["nsweep"], "leaf": b, "tau": tau,
+                   "l2": "L2 flushed (256 MB write) before every timed run",
+                   "parallelism": f"replicas x{world}"},
+        "sweep": rows, "crossover_n": {tc: cross, "fp32": cross32},
+        "time_vs_n_exponent_n_ge_2048": slope,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def kernels_per_step(d, leaf, precision="tf32x3", same_tree=True):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
@@ -758,6 +877,9 @@ def main():
         return
     if args.workload == "sparse65536":
         run_sparse(args, P, dev, rank, world, dist)
+        return
+    if args.workload == "nsweep":
+        run_nsweep(args, P, dev, rank, world, dist)
         return
     A_h = make_matrix(args.workload, args.sites)
     n = A_h.shape[0]
@@ -923,7 +1045,8 @@ def main():
         return
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    roof = leaf_roofline(args.precision, peaks, peak_src, clk, kept_flops, 2 * 4.0 * n * n,
+    roof = leaf_roofline(args.precision, peaks, peak_src, clk, kept_flops,
+                         leaf_alg_bytes(st, float(n) * n, b, args.precision),
                          leaf_ms, TRAFFIC.get(("k_leaf_tc", args.workload, args.precision, b)),
                          sms)
     roof["traffic_unit"] = "GB per launch"

@@ -118,6 +118,9 @@ typedef struct {
     int32_t pad;
     int64_t slice_kept;                /* kept k-slice products (slice != 0) */
     int64_t slice_tested;              /* tested k-slice products (slice != 0) */
+    int64_t packed_leaves_a;           /* leaves packed as A-role tensor-core operands
+                                          (those a kept product can read) */
+    int64_t packed_leaves_b;           /* leaves packed as B-role operands */
 } spamm_stats_t;
 
 /* Create a context bound to the current CUDA device and to `stream` (a

@@ -217,6 +217,7 @@ class Context:
             "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
             "ms_pack": s.ms_pack, "slice": s.slice, "slice_kept": s.slice_kept,
             "slice_tested": s.slice_tested,
+            "packed_leaves_a": s.packed_leaves_a, "packed_leaves_b": s.packed_leaves_b,
         }
 
     def per_product_flops(self, count: int) -> list:

@@ -53,7 +53,8 @@ class spamm_stats_t(ctypes.Structure):
                 ("ms_symbolic", ctypes.c_float), ("ms_numeric", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("ms_pack", ctypes.c_float),
                 ("slice", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("slice_kept", ctypes.c_int64), ("slice_tested", ctypes.c_int64)]
+                ("slice_kept", ctypes.c_int64), ("slice_tested", ctypes.c_int64),
+                ("packed_leaves_a", ctypes.c_int64), ("packed_leaves_b", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p

@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                                                    void* __restrict__ pa0, void* __restrict__ pa1,
                                                    void* __restrict__ pb0, void* __restrict__ pb1,
                                                    BandView bv, const double* __restrict__ gmax_a,
-                                                   const double* __restrict__ gmax_b) {
+                                                   const double* __restrict__ gmax_b,
+                                                   unsigned long long* __restrict__ packed) {
     constexpr int TL = 128 / LEAF;
     constexpr int CH = LEAF / 16;
     constexpr int ES = PK >= 3 ? 2 : 4;                  // element bytes
@@ -352,6 +353,13 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
         needA[t] = (rowmaxB && Q < nl && spamm_keep(nq, rowmaxB[Q], th, &tie)) ? 1 : 0;
         needB[t] = (colmaxA && Q < nl && spamm_keep(colmaxA[I], nq, th, &tie)) ? 1 : 0;
         if (needA[t] | needB[t]) atomicOr(&any, 1);
+    }
+    if (warp == 0) {
+        // the leaves this block packs, per role (one atomic per role and block)
+        const unsigned ba = __ballot_sync(0xffffffffu, t < TL && needA[t]);
+        const unsigned bb = __ballot_sync(0xffffffffu, t < TL && needB[t]);
+        if (lane == 0 && ba) atomicAdd(packed, (unsigned long long)__popc(ba));
+        if (lane == 0 && bb) atomicAdd(packed + 1, (unsigned long long)__popc(bb));
     }
     __syncthreads();
     if (!any) return;
@@ -685,8 +693,8 @@ cudaError_t launch_slab_copy(spamm_tree* t, const float* A, int64_t lda, cudaStr
 // Packs for one multiply: the per-K maxima of the two leaf tiers, then the
 // needed A-role pieces of A and B-role pieces of B (one pass when A and B are
 // the same tree).  `scratch` holds 2 nb doubles.
-cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, double rel,
-                         double* scratch, int sm_count, cudaStream_t s) {
+cudaError_t launch_packs(DevCtl* ctl, const spamm_tree* A, const spamm_tree* B, double tau,
+                         double rel, double* scratch, int sm_count, cudaStream_t s) {
     const int64_t off_leaf = (((int64_t)1 << (2 * A->d)) - 1) / 3;
     const double* la = A->pyr + off_leaf;
     const double* lb = B->pyr + off_leaf;
@@ -733,7 +741,7 @@ cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, d
         k_leaf_pack<PKV, LV, BV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,   \
                                                          t->nlp, leaf, rmB, cmA, th, pa0,    \
                                                          pa1, pb0, pb1, band_view(t), gmax,  \
-                                                         gmax + 1);                          \
+                                                         gmax + 1, &ctl->packed_a);          \
     } while (0)
 #define SPAMM_LP(PKV, LV)                                                                    \
     do {                                                                                     \

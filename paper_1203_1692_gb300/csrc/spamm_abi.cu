@@ -524,7 +524,7 @@ static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
     if (e == cudaSuccess) e = launch_group(ctx, A, B, tau, tt);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
     if (e == cudaSuccess && precision_uses_tc(ctx->cfg.precision))
-        e = launch_packs(A, B, tau, ctx->cfg.tie_rel, ctx->need, ctx->sm_count, s);
+        e = launch_packs(ctx->ctl, A, B, tau, ctx->cfg.tie_rel, ctx->need, ctx->sm_count, s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
     if (e == cudaSuccess) {
         if (ctx->cfg.precision == SPAMM_PREC_FP32)
@@ -628,6 +628,8 @@ spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     out->slice = ctx->cfg.slice;
     out->slice_kept = (int64_t)c.slice_kept;
     out->slice_tested = (int64_t)c.slice_tested;
+    out->packed_leaves_a = (int64_t)c.packed_a;
+    out->packed_leaves_b = (int64_t)c.packed_b;
     if (ctx->cfg.slice) out->kept_flops = 2.0 * b * b * ctx->cfg.slice * (double)c.slice_kept;
     out->dense_flops = 2.0 * (double)ctx->last_n * (double)ctx->last_n * (double)ctx->last_n;
     out->pool_bytes = ctx->pool_words * 8;
@@ -914,7 +916,8 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
         if (e == cudaSuccess && tc) {
             e = fork_aux(ctx);
             for (int p = 0; p < count && e == cudaSuccess; ++p)
-                e = launch_packs(A[p], B[p], tau[p], ctx->cfg.tie_rel, ctx->subs[p]->need,
+                e = launch_packs(ctx->subs[p]->ctl, A[p], B[p], tau[p], ctx->cfg.tie_rel,
+                                 ctx->subs[p]->need,
                                  ctx->sm_count, ctx->subs[p]->stream);
         }
         // stages 2-3 of all products: one launch per tier and grouping step
@@ -1001,6 +1004,8 @@ spamm_status spamm_stats_item(spamm_ctx* ctx, int32_t index, spamm_stats_t* out)
     out->slice = sub->cfg.slice;
     out->slice_kept = (int64_t)c.slice_kept;
     out->slice_tested = (int64_t)c.slice_tested;
+    out->packed_leaves_a = (int64_t)c.packed_a;
+    out->packed_leaves_b = (int64_t)c.packed_b;
     if (sub->cfg.slice) out->kept_flops = 2.0 * b * b * sub->cfg.slice * (double)c.slice_kept;
     out->dense_flops = 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
     out->pool_bytes = sub->pool_words * 8;
@@ -1033,6 +1038,8 @@ static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
         out->slice = sub->cfg.slice;
         out->slice_kept += (int64_t)c.slice_kept;
         out->slice_tested += (int64_t)c.slice_tested;
+        out->packed_leaves_a += (int64_t)c.packed_a;
+        out->packed_leaves_b += (int64_t)c.packed_b;
         out->dense_flops += 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
         out->pool_bytes += sub->pool_words * 8;
         out->pool_needed_bytes += words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)) * 8;

@@ -51,6 +51,8 @@ struct DevCtl {
     unsigned long long need_words;  // words the whole multiply needs
     unsigned long long slice_kept;  // kept k-slice products (sub-leaf cull)
     unsigned long long slice_tested;
+    unsigned long long packed_a;    // leaves packed in the A role (needed by a kept product)
+    unsigned long long packed_b;    // leaves packed in the B role
     unsigned int status;
     unsigned int pad;
 };
@@ -295,8 +297,8 @@ cudaError_t launch_ctl_batch(spamm_ctx* const* subs, int count, DevCtl* out, cud
 
 // Tensor-core packs of the leaves that can take part in a kept product of
 // A x B at tau (norms.cu); scratch holds 2 x (leaves per side) doubles.
-cudaError_t launch_packs(const spamm_tree* A, const spamm_tree* B, double tau, double rel,
-                         double* scratch, int sm_count, cudaStream_t s);
+cudaError_t launch_packs(DevCtl* ctl, const spamm_tree* A, const spamm_tree* B, double tau,
+                         double rel, double* scratch, int sm_count, cudaStream_t s);
 
 // Sparsification (norms.cu): drop the leaves whose product with norm2_max
 // fails the SpAMM test at tau (norms and panels zeroed), then the row and

@@ -310,3 +310,40 @@ def test_host_entry_bands_equal_device_multiply(prec, b, n, pinned):
     Ch2 = C0.copy()
     ctx.multiply_host(A, B, tau, alpha, beta, C=Ch2)
     assert np.array_equal(Ch2, Cd)
+
+
+@pytest.mark.parametrize("prec,b", [("f16x3", 32), ("tf32x3", 64)])
+def test_packed_leaf_counts(prec, b):
+    """stats() counts the leaves the packs hold: leaf (I, K) in the A role
+    iff ||A_IK||^2 max_J ||B_KJ||^2 passes the SpAMM test, leaf (K, J) in the
+    B role iff max_I ||A_IK||^2 ||B_KJ||^2 does (the monotone bound that
+    decides which pieces a kept product can read); recounted here from the
+    oracle's leaf norms."""
+    n, tau = 1200, 1e-3
+    A = gen.exp_decay(n, 0.8, seed=1)
+    B = gen.exp_decay(n, 0.85, seed=2)
+    ctx, _ = _run(A, B, b, tau, prec)
+    st = ctx.stats()
+    d = O.depth(n, b)
+    la = O.tier(O.pyramid(A, b), d)
+    lb = O.tier(O.pyramid(B, b), d)
+    nl = -(-n // b)
+    la, lb = la[:nl, :nl], lb[:nl, :nl]
+    rowmaxB = lb.max(axis=1)            # per K: max_J ||B_KJ||^2
+    colmaxA = la.max(axis=0)            # per K: max_I ||A_IK||^2
+    pa = la * rowmaxB[None, :]
+    pb = colmaxA[:, None] * lb
+    t2 = tau * tau
+    # no product near the threshold, so the exact test and this one agree
+    for p in (pa, pb):
+        assert np.all(np.abs(p[p > 0] - t2) > 1e-6 * t2)
+    want_a = int(np.count_nonzero((pa >= t2) & (la > 0) & (rowmaxB[None, :] > 0)))
+    want_b = int(np.count_nonzero((pb >= t2) & (lb > 0) & (colmaxA[:, None] > 0)))
+    assert 0 < want_a < nl * nl and 0 < want_b < nl * nl
+    assert st["packed_leaves_a"] == want_a
+    assert st["packed_leaves_b"] == want_b
+    # a dense product packs every leaf in both roles
+    D = gen.uniform_dense(n, seed=3, symmetric=False)
+    ctx2, _ = _run(D, D, b, 0.0, prec)
+    st2 = ctx2.stats()
+    assert st2["packed_leaves_a"] == nl * nl and st2["packed_leaves_b"] == nl * nl
