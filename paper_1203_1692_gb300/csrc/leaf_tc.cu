@@ -61,7 +61,7 @@ namespace {
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kChunkIters = 16;  // K-chunks of 16 per TMEM accumulation chunk
-constexpr int kGroupRows = 8;   // tile rows walked together (L2 reuse)
+constexpr int kGroupRows = 12;  // tile rows walked together (L2 reuse)
 constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 

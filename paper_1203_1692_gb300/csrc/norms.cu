@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ lea
 // leaves are needed as A-role pieces (rowmaxB given) and as B-role pieces
 // (colmaxA given) with the SpAMM condition above, returns at once if none
 // is, else stages the strip in shared memory (16-byte loads) and produces
-// the needed pieces in output order: thread t writes the t-th, (t+128)-th, ...
-// 16-byte unit of each piece, reading the elements that unit holds from the
+// the needed pieces in output order: with T threads, thread t writes the
+// t-th, (t+T)-th, ... 16-byte unit of each piece, reading the elements that unit holds from the
 // staged strip (a row quad for the A role, a column quad for the B role),
 // splitting them into hi/lo parts and storing both parts.  Every piece is
 // a contiguous run of at least 512 bytes and consecutive threads write its
@@ -314,8 +314,13 @@ __global__ void __launch_bounds__(256) k_leaf_max(const double* __restrict__ lea
 // hi, 2 tf32 hi+lo, 3 bf16 hi+lo, 4 scaled fp16 hi+lo.
 // BAND: a sparsified tree; the strip comes from the leaf row's slab and the
 // pieces go to their place inside the column (A role) or row (B role) band.
+// Threads per pack block: 256 for b >= 32, 128 for b = 16 (each the
+// faster measured form at n = 7500).
+template <int LEAF>
+constexpr int pack_threads() { return LEAF >= 32 ? 256 : 128; }
+
 template <int PK, int LEAF, bool BAND>
-__global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, int64_t n,
+__global__ void __launch_bounds__(pack_threads<LEAF>()) k_leaf_pack(const float* __restrict__ A, int64_t n,
                                                    int64_t lda, int64_t nb, int64_t nl, int64_t nlp,
                                                    const double* __restrict__ leaf,
                                                    const double* __restrict__ rowmaxB,
@@ -325,6 +330,8 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
                                                    BandView bv, const double* __restrict__ gmax_a,
                                                    const double* __restrict__ gmax_b,
                                                    unsigned long long* __restrict__ packed) {
+    constexpr int kPackThreads = pack_threads<LEAF>();
+    constexpr int kPackWarps = kPackThreads / 32;
     constexpr int TL = 128 / LEAF;
     constexpr int CH = LEAF / 16;
     constexpr int ES = PK >= 3 ? 2 : 4;                  // element bytes
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
         const int64_t w = (int64_t)(kmax - kmin + 1) * LEAF;
         const float* srow = bv.slab + bv.roff[I];
 #pragma unroll 4
-        for (int r = warp; r < LEAF; r += 4) {
+        for (int r = warp; r < LEAF; r += kPackWarps) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             const int64_t sc = c0 + cq - (int64_t)kmin * LEAF;    // slab column
             if (kmin <= kmax && sc >= 0 && sc + 3 < w)
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     } else {
         const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
 #pragma unroll 4
-        for (int r = warp; r < LEAF; r += 4) {
+        for (int r = warp; r < LEAF; r += kPackWarps) {
             const int64_t row = r0 + r, col = c0 + cq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (row < n) {
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(128) k_leaf_pack(const float* __restrict__ A, 
     __syncthreads();
     // pieces, in output order
     constexpr int UNITS = TL * CH * UPP;                 // per role and part
-    for (int u = t; u < UNITS; u += 128) {
+    for (int u = t; u < UNITS; u += kPackThreads) {
         const int pc = u / UPP, w = u % UPP;
         // unit w of a piece: row group w / (8 CPC), core (w / 8) % CPC, row w % 8
         const int rg = w / (8 * CPC), core = (w / 8) % CPC, rr = w % 8;
@@ -738,7 +745,7 @@ cudaError_t launch_packs(DevCtl* ctl, const spamm_tree* A, const spamm_tree* B, 
         if (smem > 48 * 1024)                                                                \
             cudaFuncSetAttribute(k_leaf_pack<PKV, LV, BV>,                                   \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-        k_leaf_pack<PKV, LV, BV><<<grid, 128, smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,   \
+        k_leaf_pack<PKV, LV, BV><<<grid, pack_threads<LV>(), smem, s>>>(t->A, t->n, t->lda, t->nb, t->nl,   \
                                                          t->nlp, leaf, rmB, cmA, th, pa0,    \
                                                          pa1, pb0, pb1, band_view(t), gmax,  \
                                                          gmax + 1, &ctl->packed_a);          \
