@@ -774,6 +774,33 @@ def run_nsweep(args, P, dev, rank, world, dist):
             ts.append(e0.elapsed_time(e1))
         return sorted(ts)[len(ts) // 2]
 
+    def med_graph(fn, s):
+        """The same, for fn captured once in a CUDA graph on stream s and
+        replayed (no host launch cost: what a serving loop pays)."""
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(max(2, args.warmup)):
+                fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fn()
+        ts = []
+        with torch.cuda.stream(s):
+            for _ in range(max(2, args.warmup)):
+                g.replay()
+            for _ in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                g.replay()
+                e1.record(s)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        del g
+        return sorted(ts)[len(ts) // 2]
+
     rows, launches = [], 0
     clocks = Clocks(dev.index or 0)
     clocks.start()
@@ -781,7 +808,9 @@ def run_nsweep(args, P, dev, rank, world, dist):
         A = D.exp_decay(n, 0.9, seed=0, device=dev)
         Cs = torch.empty_like(A)
         ms_sgemm = med(lambda: torch.mm(A, A, out=Cs))
-        row = {"n": n, "sgemm_ms": ms_sgemm,
+        gs = torch.cuda.Stream(device=dev)
+        ms_sgemm_graph = med_graph(lambda: torch.mm(A, A, out=Cs), gs)
+        row = {"n": n, "sgemm_ms": ms_sgemm, "sgemm_graph_ms": ms_sgemm_graph,
                "sgemm_effective_tflops": 2.0 * n ** 3 / (ms_sgemm * 1e-3) / 1e12}
         for prec in ("fp32", args.precision):
             ctx = P.Context(leaf=b, precision=prec, checked=True)
@@ -796,6 +825,9 @@ def run_nsweep(args, P, dev, rank, world, dist):
 
             ms = med(step)
             st = ctx.stats()
+            P._abi.spamm_set_stream(ctx.handle, gs.cuda_stream)
+            ms_graph = med_graph(step, gs)
+            ctx.stats()                      # raises if a replayed step failed
             launches += kernels_per_step(st["depth"], b, prec) * reps
             scale = float(Cs.abs().max())
             row[prec] = {"ms": ms, "ms_numeric": st["ms_numeric"],
@@ -804,6 +836,8 @@ def run_nsweep(args, P, dev, rank, world, dist):
                          "kept_tflops": st["kept_flops"] / (ms * 1e-3) / 1e12,
                          "effective_tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
                          "speedup_vs_sgemm": ms_sgemm / ms,
+                         "graph_ms": ms_graph,
+                         "graph_speedup_vs_sgemm_graph": ms_sgemm_graph / ms_graph,
                          "max_rel_diff_vs_sgemm": float((C - Cs).abs().max()) / scale,
                          "alg_bytes": leaf_alg_bytes(st, float(n) * n, b, prec)}
             tree.close()
@@ -817,6 +851,7 @@ def run_nsweep(args, P, dev, rank, world, dist):
     tc = args.precision
     cross = next((r["n"] for r in rows if r[tc]["speedup_vs_sgemm"] > 1.0), None)
     cross32 = next((r["n"] for r in rows if r["fp32"]["speedup_vs_sgemm"] > 1.0), None)
+    cross_g = next((r["n"] for r in rows if r[tc]["graph_speedup_vs_sgemm_graph"] > 1.0), None)
     big = [r for r in rows if r["n"] >= 2048]
     slope = {p: float(np.polyfit(np.log([r["n"] for r in big]),
                                  np.log([r[p]["ms"] for r in big]), 1)[0]) for p in ("fp32", tc)}
@@ -842,7 +877,7 @@ def run_nsweep(args, P, dev, rank, world, dist):
         "config": {"workload": WORKLOADS["nsweep"], "leaf": b, "tau": tau,
                    "l2": "L2 flushed (256 MB write) before every timed run",
                    "parallelism": f"replicas x{world}"},
-        "sweep": rows, "crossover_n": {tc: cross, "fp32": cross32},
+        "sweep": rows, "crossover_n": {tc: cross, "fp32": cross32, tc + "_graphs": cross_g},
         "time_vs_n_exponent_n_ge_2048": slope,
         "roofline": roof, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches,
         "clocks": clk,
