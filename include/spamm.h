@@ -113,7 +113,9 @@ typedef struct {
     float ms_symbolic;                 /* cull + grouping, CUDA events */
     float ms_numeric;                  /* leaf products + C epilogue */
     float ms_total;
-    float ms_pack;                     /* tensor-core packs of the needed leaves */
+    float ms_pack;                     /* tensor-core packs of the needed leaves: the
+                                          part not hidden behind the cull, beside
+                                          which they run on a side stream */
     int32_t slice;                     /* the config's slice (0: off) */
     int32_t pad;
     int64_t slice_kept;                /* kept k-slice products (slice != 0) */

@@ -226,6 +226,9 @@ spamm_status spamm_destroy(spamm_ctx* ctx) {
             cudaEventDestroy(ctx->aux_ev[i]);
         }
         cudaEventDestroy(ctx->fork_ev);
+        cudaStreamSynchronize(ctx->hi);
+        cudaStreamDestroy(ctx->hi);
+        cudaEventDestroy(ctx->hi_ev);
     }
     cudaGetLastError();
     delete ctx;
@@ -513,18 +516,39 @@ static cudaError_t copy_rows_out(void* user, int64_t r0, int64_t r1) {
     return e;
 }
 
+static spamm_status ensure_aux(spamm_ctx* ctx);
+
+// One multiply on the context stream.  The tensor-core packs depend on the
+// leaf norms and tau only, not on the cull, so the cull and grouping run on
+// the high-priority side stream beside them: the small latency-bound cull
+// launches go ahead of the HBM-bound pack kernel's blocks, and the leaf
+// products wait for both.
 static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
                                          const spamm_tree* B, double tau, float alpha,
                                          float beta, float* C, int64_t ldc) {
     cudaStream_t s = ctx->stream;
+    const bool tc = precision_uses_tc(ctx->cfg.precision);
     cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
     const int tt = tile_tier(A);
-    if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau, tt);
-    if (e == cudaSuccess) e = launch_group(ctx, A, B, tau, tt);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
-    if (e == cudaSuccess && precision_uses_tc(ctx->cfg.precision))
-        e = launch_packs(ctx->ctl, A, B, tau, ctx->cfg.tie_rel, ctx->need, ctx->sm_count, s);
+    if (tc) {
+        // fork: cull + grouping on ctx->hi, packs on the context stream, join
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hi, ctx->fork_ev, 0);
+        ctx->stream = ctx->hi;
+        if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau, tt);
+        if (e == cudaSuccess) e = launch_group(ctx, A, B, tau, tt);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], ctx->hi);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->hi_ev, ctx->hi);
+        ctx->stream = s;
+        if (e == cudaSuccess)
+            e = launch_packs(ctx->ctl, A, B, tau, ctx->cfg.tie_rel, ctx->need, ctx->sm_count, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->hi_ev, 0);
+    } else {
+        if (e == cudaSuccess) e = launch_cull(ctx, A, B, tau, tt);
+        if (e == cudaSuccess) e = launch_group(ctx, A, B, tau, tt);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
     if (e == cudaSuccess) {
         if (ctx->cfg.precision == SPAMM_PREC_FP32)
@@ -569,6 +593,7 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
     const int64_t tiles = (int64_t)tile_rows(A) * tile_cols(A);
     spamm_status st = ensure_tiles(ctx, tiles);
     if (st == SPAMM_OK) st = ensure_need(ctx, A->nb);
+    if (st == SPAMM_OK && precision_uses_tc(ctx->cfg.precision)) st = ensure_aux(ctx);
     if (st != SPAMM_OK) return st;
     ctx->last_batch = 0;
     ctx->last_d = A->d;
@@ -780,11 +805,20 @@ static spamm_status ensure_aux(spamm_ctx* ctx) {
             e = cudaEventCreateWithFlags(&ctx->aux_ev[made], cudaEventDisableTiming);
         if (e != cudaSuccess) break;
     }
+    int lo_prio = 0, hi_prio = 0;
+    bool hi_made = false;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->hi, cudaStreamNonBlocking, hi_prio);
+    if (e == cudaSuccess) {
+        hi_made = true;
+        e = cudaEventCreateWithFlags(&ctx->hi_ev, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         for (int i = 0; i < made; ++i) {
             cudaStreamDestroy(ctx->aux[i]);
             cudaEventDestroy(ctx->aux_ev[i]);
         }
+        if (hi_made) cudaStreamDestroy(ctx->hi);
         cudaEventDestroy(ctx->fork_ev);
         return cuda_err(ctx, e, "side streams");
     }

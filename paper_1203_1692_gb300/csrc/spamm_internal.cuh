@@ -254,6 +254,10 @@ struct spamm_ctx {
     cudaStream_t aux[kAux];
     cudaEvent_t aux_ev[kAux];
     cudaEvent_t fork_ev;
+    // high-priority side stream: a multiply's cull and grouping, whose small
+    // latency-bound launches then go ahead of the concurrent pack kernel
+    cudaStream_t hi;
+    cudaEvent_t hi_ev;
     bool aux_ready;
     std::string err;
 };
