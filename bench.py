@@ -66,7 +66,8 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from an ncu capture (GB), keyed by (kernel, workload, precision,
 # leaf); refreshed whenever that kernel changes.
-TRAFFIC = {("k_leaf_tc", "water7500", "f16x3", 64): 2.448009 + 0.224606}
+TRAFFIC = {("k_leaf_tc", "water7500", "f16x3", 64): 2.448009 + 0.224606,
+           ("k_leaf_tc", "water7500", "f16x3", 128): 2.085818 + 0.223873}
 
 
 def parse():

@@ -953,11 +953,18 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
                 e = launch_packs(ctx->subs[p]->ctl, A[p], B[p], tau[p], ctx->cfg.tie_rel,
                                  ctx->subs[p]->need,
                                  ctx->sm_count, ctx->subs[p]->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hi, ctx->fork_ev, 0);
         }
-        // stages 2-3 of all products: one launch per tier and grouping step
+        // stages 2-3 of all products: one launch per tier and grouping step,
+        // on the high-priority side stream when packs run beside them
         if (e == cudaSuccess)
-            e = launch_symbolic_batched(ctx, ctx->subs.data(), A, B, tau, count, s);
-        if (e == cudaSuccess && tc) e = join_aux(ctx);
+            e = launch_symbolic_batched(ctx, ctx->subs.data(), A, B, tau, count,
+                                        tc ? ctx->hi : s);
+        if (e == cudaSuccess && tc) {
+            e = cudaEventRecord(ctx->hi_ev, ctx->hi);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->hi_ev, 0);
+            if (e == cudaSuccess) e = join_aux(ctx);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
         if (e == cudaSuccess) {
