@@ -161,6 +161,17 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the whole job ends with its slowest
+    rank); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def leaf_alg_bytes(st, n_sq, b, precision):
     """Algorithmic bytes of one leaf-product launch: C written once (4 n^2)
     plus every operand leaf a kept product needs read once at 4 B per element
@@ -247,7 +258,7 @@ def run_reference(args, rank, world):
     b0, tau0 = SETTLED.get(args.workload, (16, 1e-6))
     b = b0 if args.leaf == "auto" else int(args.leaf)
     tau = tau0 if args.tau == "auto" else float(args.tau)
-    budget = min(10.0, 150.0 / max(1, args.steps + args.warmup))
+    budget = min(10.0, args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
     vals = []
     desc = ""
     threads = 1
@@ -449,10 +460,7 @@ def run_batched(args, P, dev, rank, world, dist):
     clk = clocks.stop()
     ms_step = e0.elapsed_time(e1) / args.steps
     lat = sorted(a.elapsed_time(c) for a, c in per)
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist, dev)
     value = kept_flops * world / (ms_step * 1e-3) / 1e12
     # the leaf launch alone (its own events inside the library), not in a graph
     with torch.cuda.stream(s):
@@ -551,8 +559,15 @@ def run_batched(args, P, dev, rank, world, dist):
         cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                "sample": f"product of n={ns[perm[q]]} (median n of the batch): " + desc}
     # per product: norm leaves, upper tiers, cull, grouping; one leaf launch
-    launches = (sum(kernels_per_step(t.depth, b, args.precision) - 1 for t in trees)
-                + -(-count // 64))
+    # per step: each tree's norm leaves and upper tiers; per product its norm
+    # maxima and packs; the table-driven cull (root, tiers, finish) and
+    # grouping (4 + tile cull) of all products; one leaf launch per 64
+    # products; two control-block kernels (zero, gather)
+    tl = int(math.log2(128 // b))
+    max_tt = max(max(0, t.depth - tl) for t in trees)
+    packs = 0 if args.precision == "fp32" else 2 * count
+    launches = (sum(1 + math.ceil(t.depth / 5) for t in trees) + packs + (max_tt + 2) + 5
+                + -(-count // 64) + 2)
     line = {
         "metric": "SpAMM leaf TFLOP/s (kept 2b^3 flops / step time), batch of 64 products",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -889,10 +904,11 @@ def run_nsweep(args, P, dev, rank, world, dist):
 def kernels_per_step(d, leaf, precision="tf32x3", same_tree=True):
     tl = 128 // leaf
     tt = max(0, d - int(math.log2(tl)))
-    # norm leaves + upper tiers | cull root, tiers < tt, finish | group x3,
-    # tile cull | norm maxima + packs (tensor cores) | leaf products
+    # norm leaves + upper tiers (5 per pass) | cull root, tiers < tt, finish |
+    # grouping zero, count, scan, scatter + tile cull | norm maxima + packs
+    # (tensor cores) | leaf products
     packs = 0 if precision == "fp32" else 1 + (1 if same_tree else 2)
-    return (1 + math.ceil(d / 5)) + (tt + 2) + 4 + packs + 1
+    return (1 + math.ceil(d / 5)) + (tt + 2) + 5 + packs + 1
 
 
 def main():
@@ -1055,10 +1071,7 @@ def main():
     leaf_ms = statistics.mean(numeric_ms)
     kept_flops = st["kept_flops"]
     ms_step = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist, dev)
     value = kept_flops * world / (ms_step * 1e-3) / 1e12
 
     # --- end to end through the host entry point --------------------------
