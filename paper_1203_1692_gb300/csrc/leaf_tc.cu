@@ -22,12 +22,16 @@
 // y0..y0+len-1 that share the same set of kept row leaves uses the MMA's
 // disable-output-lane mask to leave the accumulator rows (TMEM lanes) of the
 // culled row leaves untouched, so the tensor core adds exactly the kept
-// products.  N = len * b (16..256), M = 128.
+// products.  N = len * b (16..256), M = 128.  A step whose products are
+// all kept (the common case on dense blocks) skips the run analysis and
+// issues unmasked 128 x 256 MMAs.
 //
 // Precisions: TF32X3 splits each operand into a TF32 high part and a TF32
 // low part (a - hi) and adds lo*hi + hi*lo + hi*hi; TF32 uses hi*hi only;
-// BF16X3 does the same with bfloat16 parts on kind::f16.  All accumulate in
-// FP32.
+// BF16X3 does the same with bfloat16 parts on kind::f16; F16X3 with fp16
+// parts of each operand scaled by a power of two (its largest leaf norm
+// just below 2^15), the product scaled back exactly in the epilogue.  All
+// accumulate in FP32.
 //
 // Two-level accumulation: the tensor core's FP32 accumulation rounds less
 // carefully than an IEEE add, and a C tile can chain thousands of MMAs.  So
@@ -42,13 +46,17 @@
 // share A slices (same rows) and B slices (same columns) in L2.
 //
 // Roles (320 threads): warp 0 lane 0 issues the bulk copies into a ring of
-// shared-memory stages; warp 1 owns the TMEM allocation (all 512 columns)
-// and its lane 0 issues the MMAs and commits; warps 2-9 move the
-// double-buffered 128 x 256 chunk accumulators out of TMEM (two warps per
-// TMEM lane quarter, 128 columns each), sum them, apply alpha/beta and store
-// C.  Every wait on an
-// mbarrier gives up after one second, raises the timeout status and lets
+// shared-memory stages (two of 96 KB for 16-bit parts and single TF32, four
+// of 48 KB for TF32 hi and lo); warp 1 owns the TMEM allocation (all 512
+// columns) and its lane 0 issues the MMAs and commits, a stage's masks read
+// at once and its slots unrolled; warps 2-9 move the double-buffered
+// 128 x 256 chunk accumulators out of TMEM (two warps per TMEM lane quarter,
+// 128 columns each), sum them, apply alpha/beta and store C.  Every wait on
+// an mbarrier gives up after one second, raises the timeout status and lets
 // the block drain its copies and MMAs, free TMEM and exit.
+//
+// A launch covers the work items [first, total) of its table: one launch
+// for a multiply, or (host entry point) one per band of tile-row groups.
 #include <cuda_bf16.h>
 
 #include <algorithm>
