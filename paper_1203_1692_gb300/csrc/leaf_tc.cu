@@ -1032,9 +1032,12 @@ cudaError_t launch_leaf_tc_banded(spamm_ctx* ctx, const spamm_tree* A, const spa
     const int groups = (tr + kGroupRows - 1) / kGroupRows;
     if (bands > groups) bands = groups;
     if (bands < 1) bands = 1;
+    // band i ends at group ceil(groups (i+1) / bands): the remainder goes to
+    // the front, so the last band, whose copy-out nothing hides, is the
+    // smallest
     int g0 = 0;
     for (int i = 0; i < bands; ++i) {
-        const int g1 = (int)((int64_t)groups * (i + 1) / bands);
+        const int g1 = (int)(((int64_t)groups * (i + 1) + bands - 1) / bands);
         bt.first = g0 * kGroupRows * tc;
         bt.total = (g1 * kGroupRows < tr ? g1 * kGroupRows : tr) * tc;
         cudaError_t e = dispatch(ctx, bt, band);
