@@ -1,0 +1,31 @@
+"""Host logic of the autotuner: launch orders and the cache signature."""
+from paper_1203_1692_gb300 import autotune
+
+
+def test_order_of():
+    ns = [512, 8192, 1024, 8192, 600]
+    assert autotune.order_of("given", ns) == [0, 1, 2, 3, 4]
+    # largest first, ties in their given order
+    assert autotune.order_of("largest_first", ns) == [1, 3, 2, 4, 0]
+
+
+def test_signature_buckets_orders_and_taus():
+    s1 = autotune.signature([512, 1000, 8000], [1e-7, 1e-7, 1e-8], "f16x3")
+    # orders round to powers of two and sort; taus are a set
+    s2 = autotune.signature([8192, 1024, 500], [1e-8, 1e-7], "f16x3")
+    assert s1 == s2
+    assert s1 != autotune.signature([512, 1000, 8000], [1e-7], "f16x3")
+    assert s1 != autotune.signature([512, 1000, 8000], [1e-7, 1e-8], "tf32x3")
+
+
+def test_choice_permutation_and_cache_lookup():
+    c = autotune.Choice(leaf=32, order="largest_first", ms=1.0, slice=16)
+    assert c.permutation([100, 300, 200]) == [1, 2, 0]
+    key = autotune.signature([100], [1e-6], "bf16x3") + (
+        tuple(autotune.LEAVES), tuple(autotune.ORDERS), tuple(autotune.SLICES))
+    autotune._CACHE[key] = c
+    try:
+        assert autotune.cached([100], [1e-6], "bf16x3") is c
+        assert autotune.cached([100], [1e-6], "f16x3") is None
+    finally:
+        del autotune._CACHE[key]
