@@ -185,9 +185,10 @@ def leaf_alg_bytes(st, n_sq, b, precision):
 def leaf_roofline(precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_ms, kernel_traffic,
                   dev_sms):
     """Roofline of the leaf-product kernel.  Its algorithmic flops are the
-    kept leaf flops; its algorithmic bytes are the operands read once and C
-    written once (SURVEY-style 4n^2 per matrix).  The bound is the one the
-    arithmetic intensity selects against the ridge point of the two peaks."""
+    kept leaf flops; its algorithmic bytes come from leaf_alg_bytes (C
+    written once, the needed operand leaves read once).  The bound is the
+    one the arithmetic intensity selects against the ridge point of the two
+    peaks."""
     hbm = peaks["hbm_gbs"]
     if precision == "fp32":
         mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)

@@ -45,7 +45,7 @@ typedef enum {
     SPAMM_ERR_CAPACITY = 3,     /* the triple pool overflowed; C is not valid */
     SPAMM_ERR_OOM = 4,          /* device or pinned allocation failed */
     SPAMM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-    SPAMM_ERR_UNSUPPORTED = 6,  /* valid request outside this build's scope */
+    SPAMM_ERR_UNSUPPORTED = 6,  /* valid request the engine does not support (e.g. rectangular) */
     SPAMM_ERR_CUDA = 7          /* a CUDA runtime call failed */
 } spamm_status;
 
