@@ -98,3 +98,32 @@ def test_slice_cull_config_is_validated_before_the_gpu(libpath):
         c = _abi.spamm_config_default()
         c.leaf, c.precision, c.slice = leaf, prec, sl
         assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == want
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's spamm_config and spamm_stats_t have the C layout: every
+    field at the offset gcc gives it from include/spamm.h, and the same size
+    (a field added on one side only would shift the rest)."""
+    from paper_1203_1692_gb300 import _abi
+    structs = {"spamm_config": _abi.spamm_config, "spamm_stats_t": _abi.spamm_stats_t}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "spamm.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n"):
+        if line:
+            cname, field, val = line.split()
+            got[(cname, field)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
