@@ -91,3 +91,14 @@ def test_leaf_alg_bytes_and_launch_count():
     # grouping kernels, k_tile_cull, k_leaf_max, k_leaf_pack, k_leaf_tc
     assert bench.kernels_per_step(7, 64, "f16x3") == 19
     assert bench.kernels_per_step(7, 64, "fp32") == 17
+
+
+def test_cpu_baseline_reports_model_and_single_thread_rate():
+    import spamm_inputs as gen
+    from oracle import oracle as O
+    assert bench.cpu_model().strip() and "logical CPUs" in bench.cpu_model()
+    A = gen.exp_decay(512, 0.9, seed=0)
+    threads = O.threads()
+    v1, desc = bench.cpu_sample_single_thread(A, 16, 1e-6, 0.2)
+    assert v1 > 0 and "kept leaf products" in desc
+    assert O.threads() == threads          # restored
