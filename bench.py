@@ -268,7 +268,9 @@ def cpu_model() -> str:
             imp = [x.split(":", 1)[1].strip() for x in info if x.startswith("CPU implementer")]
             part = [x.split(":", 1)[1].strip() for x in info if x.startswith("CPU part")]
             if imp and part:
-                name = f"implementer {imp[0]} part {part[0]}"
+                arm = {"0xd0c": "Neoverse N1", "0xd40": "Neoverse V1", "0xd49": "Neoverse N2",
+                       "0xd4f": "Neoverse V2"}
+                name = arm.get(part[0].lower(), f"implementer {imp[0]} part {part[0]}")
     except OSError:
         pass
     return f"{name or platform.processor() or 'unknown'} ({platform.machine()}, "\
