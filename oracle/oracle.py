@@ -69,6 +69,12 @@ def lib():
         L.oracle_multiply_sliced.restype = _c_i64
         L.oracle_multiply_sliced.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _c_i64,
                                              _c_dbl, _c_dbl, _c_dbl, _p, _c_i64, _p]
+        L.oracle_round_sig.restype = _c_dbl
+        L.oracle_round_sig.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int]
+        L.oracle_multiply_tiered.restype = _c_i64
+        L.oracle_multiply_tiered.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _c_dbl,
+                                             _c_dbl, ctypes.c_int, ctypes.c_int, _c_dbl, _c_dbl,
+                                             _p, _c_i64, _p]
         L.oracle_sparsify.restype = _c_i64
         L.oracle_sparsify.argtypes = [_p, _c_i64, _c_i64, _c_i64, _c_dbl, _c_dbl, _p]
         L.oracle_block.restype = _c_i64
@@ -225,6 +231,39 @@ def multiply_sliced(A, B, b: int, g: int, tau: float, alpha: float = 1.0, beta: 
                                      _ptr(Cd), n, _ptr(stats))
     if m < 0:
         raise RuntimeError(f"oracle_multiply_sliced failed ({m})")
+    return Cd, int(m), int(stats[0]), int(stats[1])
+
+
+# significant bits of the high part of each split precision, and whether
+# its rounding breaks ties away from zero (TF32 conversion) or to even
+HIGH_PART = {"f16x3": (11, False), "tf32x3": (11, True), "bf16x3": (8, False)}
+
+
+def round_sig(x: float, p: int, ties_away: bool = False) -> float:
+    """x rounded to p significant bits (unbounded exponent range)."""
+    return float(lib().oracle_round_sig(float(x), int(p), 1 if ties_away else 0))
+
+
+def multiply_tiered(A, B, b: int, tau: float, tau_h: float, p: int, ties_away: bool = False,
+                    alpha: float = 1.0, beta: float = 0.0, C=None):
+    """SpAMM at tau with the precision of each kept product chosen by its
+    norm (reading R16): products with ||A_IK|| ||B_KJ|| >= tau_h exact,
+    the others from operands rounded to p significant bits.  Returns (C in
+    FP64, kept leaf triples, products formed exactly, products formed
+    rounded)."""
+    A = _f32(A)
+    B = _f32(B)
+    n = A.shape[0]
+    if B.shape != A.shape:
+        raise ValueError("shape mismatch")
+    Cd = np.zeros((n, n), dtype=np.float64) if C is None else \
+        np.ascontiguousarray(C, dtype=np.float64).copy()
+    stats = np.zeros(2, dtype=np.int64)
+    m = lib().oracle_multiply_tiered(_ptr(A), n, _ptr(B), n, n, b, tau, tau_h, int(p),
+                                     1 if ties_away else 0, alpha, beta, _ptr(Cd), n,
+                                     _ptr(stats))
+    if m < 0:
+        raise RuntimeError(f"oracle_multiply_tiered failed ({m})")
     return Cd, int(m), int(stats[0]), int(stats[1])
 
 

@@ -32,7 +32,15 @@
  *       the norms of its two panels pass the same condition;
  *   R15 sparsification (oracle_sparsify) drops a leaf iff its product with
  *       the largest operand norm fails the condition (epsilon = tau / max
- *       Frobenius norm, tested in squared form).
+ *       Frobenius norm, tested in squared form);
+ *   R16 precision chosen by norm (oracle_multiply_tiered): the SpAMM
+ *       condition applied a second time, at tau_h >= tau, to the kept
+ *       products.  A kept product with ||A_ik|| ||B_kj|| >= tau_h is formed
+ *       exactly; one below tau_h is formed from its operands rounded to p
+ *       significant bits (the high part of a split precision alone).  The
+ *       dropped terms are bounded by (2 u + u^2) ||A_ik|| ||B_kj|| with
+ *       u = 2^-p, so such a product errs by about tau_h 2^(1-p), the same
+ *       order as a culled product when tau_h = tau 2^(p-1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -368,6 +376,116 @@ int64_t oracle_multiply(const float *A, int64_t lda, const float *B, int64_t ldb
     }
     free(rowstart);
     return err ? OR_ENOMEM : cnt;
+}
+
+/* ------------------------------------------ precision by norm (R16) */
+
+/* x rounded to p significant bits (1 <= p <= 53), to nearest; ties to even,
+ * or away from zero when ties_away is set.  The exponent range is
+ * unbounded (no overflow, no subnormals): x = m 2^e with 1/2 <= |m| < 1,
+ * so m 2^p is exact and rounding it to an integer keeps p bits. */
+double oracle_round_sig(double x, int p, int ties_away)
+{
+    if (x == 0.0 || !isfinite(x) || p >= 53) return x;
+    int e;
+    double m = frexp(x, &e);
+    double s = ldexp(m, p);
+    double r = ties_away ? round(s) : nearbyint(s); /* default mode: ties to even */
+    return ldexp(r, e - p);
+}
+
+/* acc (b x b, FP64) += round(A_IK) round(B_KJ): the leaf product of the
+ * operands rounded to p significant bits, naive triple loop, zero padding. */
+static void leaf_product_rounded(const float *A, int64_t lda, const float *B, int64_t ldb,
+                                 int64_t n, int64_t b, int64_t I, int64_t K, int64_t J,
+                                 int p, int ties_away, double *acc)
+{
+    for (int64_t r = 0; r < b; r++) {
+        int64_t gr = I * b + r;
+        if (gr >= n) break;
+        for (int64_t c = 0; c < b; c++) {
+            int64_t gc = J * b + c;
+            if (gc >= n) break;
+            double s = 0.0;
+            for (int64_t q = 0; q < b; q++) {
+                int64_t gk = K * b + q;
+                if (gk >= n) break;
+                s += oracle_round_sig((double)A[gr * lda + gk], p, ties_away) *
+                     oracle_round_sig((double)B[gk * ldb + gc], p, ties_away);
+            }
+            acc[r * b + c] += s;
+        }
+    }
+}
+
+/* SpAMM with the precision of each kept product chosen by its norm (R16):
+ * the cull of oracle_multiply at tau, then every kept product with
+ * nA2 * nB2 >= tau_h^2 (FP64, squared as in R2) formed exactly, every other
+ * kept product formed from its operands rounded to p significant bits (ties
+ * to even, or away from zero).  C blocks accumulate in ascending K as in
+ * oracle_multiply; with tau_h <= tau (or p >= 53) the result is
+ * oracle_multiply's bit for bit.  stats[0] = kept products formed exactly,
+ * stats[1] = kept products formed rounded; cull_stats (2 (d + 1), may be
+ * NULL) gets the per-tier counts.  Returns the number of kept leaf triples
+ * or an error code. */
+int64_t oracle_multiply_tiered(const float *A, int64_t lda, const float *B, int64_t ldb,
+                               int64_t n, int64_t b, double tau, double tau_h, int p,
+                               int ties_away, double alpha, double beta, double *C,
+                               int64_t ldc, int64_t *stats)
+{
+    int d = oracle_depth(n, b);
+    if (d < 0 || lda < n || ldb < n || ldc < n || !(tau >= 0.0) || !(tau_h >= 0.0) ||
+        p < 1) return OR_EARG;
+    int64_t ps = oracle_pyramid_size(d);
+    double *pa = (double *)malloc(sizeof(double) * (size_t)ps);
+    double *pb = (double *)malloc(sizeof(double) * (size_t)ps);
+    int64_t *cs = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(d + 1));
+    if (!pa || !pb || !cs) { free(pa); free(pb); free(cs); return OR_ENOMEM; }
+    oracle_build_pyramid(A, n, lda, b, pa);
+    oracle_build_pyramid(B, n, ldb, b, pb);
+    int64_t cnt = oracle_cull_recursive(pa, pb, d, tau, NULL, 0, cs, cs + d + 1);
+    int32_t *tri = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(cnt > 0 ? cnt : 1));
+    if (!tri) { free(pa); free(pb); free(cs); return OR_ENOMEM; }
+    oracle_cull_recursive(pa, pb, d, tau, tri, cnt, cs, cs + d + 1);
+    free(cs);
+    qsort(tri, (size_t)cnt, 3 * sizeof(int32_t), cmp_ijk);
+    int64_t nb = (int64_t)1 << d;
+    const double *la = pa + oracle_tier_offset(d);
+    const double *lb = pb + oracle_tier_offset(d);
+    int64_t nbr = (n + b - 1) / b;
+    int64_t exact = 0, rounded = 0;
+    double *acc = (double *)malloc(sizeof(double) * (size_t)(b * b * nbr));
+    if (!acc) { free(pa); free(pb); free(tri); return OR_ENOMEM; }
+    int64_t t = 0;
+    for (int64_t I = 0; I < nbr; I++) {
+        memset(acc, 0, sizeof(double) * (size_t)(b * b * nbr));
+        for (; t < cnt && tri[3 * t] == I; t++) {
+            int64_t K = tri[3 * t + 1], J = tri[3 * t + 2];
+            if (keep(la[I * nb + K], lb[K * nb + J], tau_h * tau_h)) {
+                leaf_product(A, lda, B, ldb, n, b, I, K, J, acc + J * b * b);
+                exact++;
+            } else {
+                leaf_product_rounded(A, lda, B, ldb, n, b, I, K, J, p, ties_away,
+                                     acc + J * b * b);
+                rounded++;
+            }
+        }
+        for (int64_t r = I * b; r < I * b + b && r < n; r++)
+            for (int64_t c = 0; c < n; c++) {
+                int64_t J = c / b;
+                double v = alpha * acc[J * b * b + (r - I * b) * b + (c - J * b)];
+                C[r * ldc + c] = beta == 0.0 ? v : v + beta * C[r * ldc + c];
+            }
+    }
+    free(acc);
+    free(tri);
+    free(pa);
+    free(pb);
+    if (stats) {
+        stats[0] = exact;
+        stats[1] = rounded;
+    }
+    return cnt;
 }
 
 /* Sub-leaf cull along k (the paper's SpAMM(4x4) of Sec. III.B, cull finer

@@ -420,3 +420,103 @@ def test_sparsify_error_bound():
     dropped = (200 // b) ** 2 - m
     err2 = _norm2(A - As)
     assert dropped > 0 and err2 < dropped * tau * tau / m2
+
+
+# ------------------------------------- precision chosen by norm (R16)
+
+def test_round_sig_hand_values():
+    """Rounding to p significant bits: halfway cases go to even (or away
+    from zero), values already on the p-bit grid are fixed points."""
+    u = 2.0 ** -11
+    assert O.round_sig(1 + u, 11) == 1.0                      # tie, to even
+    assert O.round_sig(1 + u, 11, ties_away=True) == 1 + 2 * u
+    assert O.round_sig(1 + 3 * u, 11) == 1 + 4 * u            # tie, to even
+    assert O.round_sig(1 + 1.5 * u, 11) == 1 + 2 * u          # above the tie
+    assert O.round_sig(-(1 + u), 11, ties_away=True) == -(1 + 2 * u)
+    assert O.round_sig(2047.0, 11) == 2047.0                  # 11 bits exactly
+    assert O.round_sig(4095.0, 11) == 4096.0                  # carries into the exponent
+    assert O.round_sig(0.0, 8) == 0.0
+    assert O.round_sig(3.0 * 2.0 ** -200, 2) == 3.0 * 2.0 ** -200
+    assert O.round_sig(math.pi, 53) == math.pi
+
+
+def test_round_sig_matches_ieee_half_and_bfloat16():
+    """p = 11 is IEEE half precision's significand and p = 8 bfloat16's:
+    inside their normal ranges the oracle's rounding equals numpy's float16
+    conversion and torch's bfloat16 conversion (both round to nearest
+    even), computed independently of the oracle."""
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal(4000) * 10.0 ** rng.uniform(-4, 4, 4000)).astype(np.float32)
+    x = np.concatenate([x, np.float32(1.0) + np.float32(2.0 ** -11) * np.arange(-40, 40,
+                                                                               dtype=np.float32)])
+    x = x[(np.abs(x) >= 2.0 ** -14) & (np.abs(x) <= 60000.0)]    # float16's normal range
+    h = x.astype(np.float16).astype(np.float64)
+    got = np.array([O.round_sig(float(v), 11) for v in x])
+    assert np.array_equal(got, h)
+    torch = pytest.importorskip("torch")
+    bf = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    got8 = np.array([O.round_sig(float(v), 8) for v in x])
+    assert np.array_equal(got8, bf)
+
+
+@pytest.mark.parametrize("p,away", [(11, False), (11, True), (8, False)])
+def test_tiered_reduces_to_plain_spamm(p, away):
+    """tau_h <= tau (every kept product formed exactly) and p = 53 (no
+    rounding) both give oracle_multiply's C bit for bit."""
+    n, b, tau = 150, 16, 1e-3
+    A = gen.exp_decay_nonsym(n, 0.8, seed=4)
+    B = gen.exp_decay_nonsym(n, 0.85, seed=5)
+    ref = O.multiply(A, B, b, tau)
+    C, m, exact, rounded = O.multiply_tiered(A, B, b, tau, tau, p, away)
+    assert np.array_equal(C, ref.C) and m == len(ref.triples) == exact and rounded == 0
+    C, m, exact, rounded = O.multiply_tiered(A, B, b, tau, 1e9, 53, away)
+    assert np.array_equal(C, ref.C) and rounded == m
+
+
+def test_tiered_all_rounded_is_the_product_of_rounded_operands():
+    """tau = 0 and tau_h above every norm product: every non-NULL leaf
+    product is formed from operands rounded to 11 bits, so C is numpy's
+    FP64 product of the float16-rounded matrices (within FP64 summation
+    order)."""
+    n, b = 200, 16
+    A = gen.uniform_dense(n, seed=6, symmetric=False)
+    B = gen.uniform_dense(n, seed=7, symmetric=False)
+    # float16's subnormals keep fewer than 11 bits: stay in its normal range
+    A[np.abs(A) < 2.0 ** -14] = 0.0
+    B[np.abs(B) < 2.0 ** -14] = 0.0
+    C, m, exact, rounded = O.multiply_tiered(A, B, b, 0.0, 1e30, 11)
+    nl = -(-n // b)
+    assert exact == 0 and rounded == m == nl ** 3
+    ref = A.astype(np.float16).astype(np.float64) @ B.astype(np.float16).astype(np.float64)
+    assert np.abs(C - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(C - A.astype(np.float64) @ B.astype(np.float64)).max() > 1e-5
+
+
+@pytest.mark.parametrize("p,tau,shift", [(11, 1e-4, 10), (8, 1e-3, 7), (11, 1e-6, 14)])
+def test_tiered_error_bound_and_counts(p, tau, shift):
+    """||AB - C||_F <= sum over culled products of ||A_IK|| ||B_KJ|| plus
+    (2u + u^2) times the same sum over the rounded ones (u = 2^-p); the
+    exact and rounded counts are the kept products on either side of
+    tau_h, recounted from numpy leaf norms."""
+    n, b = 256, 16
+    A = gen.exp_decay_nonsym(n, 0.85, seed=8)
+    B = gen.exp_decay_nonsym(n, 0.8, seed=9)
+    tau_h = tau * 2.0 ** shift
+    C, m, exact, rounded = O.multiply_tiered(A, B, b, tau, tau_h, p)
+    la, lb = _leaf_norm2(A, b), _leaf_norm2(B, b)
+    P = la[:, :, None] * lb[None, :, :]
+    pos = P > 0
+    kept = pos & (P >= tau * tau)
+    hi = kept & (P >= tau_h * tau_h)
+    assert m == int(kept.sum()) and exact == int(hi.sum()) and rounded == m - exact
+    assert 0 < exact < m
+    u = 2.0 ** -p
+    culled = np.sqrt(P[pos & ~kept]).sum()
+    low = np.sqrt(P[kept & ~hi]).sum()
+    err = np.linalg.norm(A.astype(np.float64) @ B.astype(np.float64) - C)
+    assert err <= (culled + (2 * u + u * u) * low) * (1 + 1e-12)
+    # the rounded tier alone, against plain SpAMM at the same tau: nonzero
+    # and within (2u + u^2) times the rounded products' norm sum
+    plain = O.multiply(A, B, b, tau).C
+    diff = np.linalg.norm(C - plain)
+    assert 0 < diff <= (2 * u + u * u) * low * (1 + 1e-12)
