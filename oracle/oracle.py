@@ -68,7 +68,8 @@ def lib():
                                       _c_dbl, _p, _c_i64, _p, _c_i64, _p]
         L.oracle_multiply_sliced.restype = _c_i64
         L.oracle_multiply_sliced.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _c_i64,
-                                             _c_dbl, _c_dbl, _c_dbl, _p, _c_i64, _p]
+                                             _c_dbl, _c_dbl, ctypes.c_int, ctypes.c_int,
+                                             _c_dbl, _c_dbl, _p, _c_i64, _p]
         L.oracle_round_sig.restype = _c_dbl
         L.oracle_round_sig.argtypes = [_c_dbl, ctypes.c_int, ctypes.c_int]
         L.oracle_multiply_tiered.restype = _c_i64
@@ -215,10 +216,11 @@ def multiply(A, B, b: int, tau: float, alpha: float = 1.0, beta: float = 0.0,
 
 
 def multiply_sliced(A, B, b: int, g: int, tau: float, alpha: float = 1.0, beta: float = 0.0,
-                    C=None):
+                    C=None, tau_h: float = 0.0, p: int = 53, ties_away: bool = False):
     """C = alpha * SpAMM(A, B; b, tau) with the sub-leaf cull along k in
-    slices of g (reading R14) + beta * C, in FP64.  Returns (C, kept leaf
-    triples, kept slice products, tested slice products)."""
+    slices of g (reading R14) + beta * C, in FP64; with tau_h > tau the
+    precision of each kept leaf product chosen by its norm (R16).  Returns
+    (C, kept leaf triples, kept slice products, tested slice products)."""
     A = _f32(A)
     B = _f32(B)
     n = A.shape[0]
@@ -227,8 +229,9 @@ def multiply_sliced(A, B, b: int, g: int, tau: float, alpha: float = 1.0, beta: 
     Cd = np.zeros((n, n), dtype=np.float64) if C is None else \
         np.ascontiguousarray(C, dtype=np.float64).copy()
     stats = np.zeros(2, dtype=np.int64)
-    m = lib().oracle_multiply_sliced(_ptr(A), n, _ptr(B), n, n, b, g, tau, alpha, beta,
-                                     _ptr(Cd), n, _ptr(stats))
+    m = lib().oracle_multiply_sliced(_ptr(A), n, _ptr(B), n, n, b, g, tau, tau_h, int(p),
+                                     1 if ties_away else 0, alpha, beta, _ptr(Cd), n,
+                                     _ptr(stats))
     if m < 0:
         raise RuntimeError(f"oracle_multiply_sliced failed ({m})")
     return Cd, int(m), int(stats[0]), int(stats[1])

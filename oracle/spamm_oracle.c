@@ -495,7 +495,11 @@ int64_t oracle_multiply_tiered(const float *A, int64_t lda, const float *B, int6
  * same rows of B); the b x g panel of A_IK and the g x b panel of B_KJ are
  * multiplied only if their Frobenius norms pass the SpAMM condition (R1-R3,
  * squared in FP64, panel norms summed row-major from exact squares).  Each C
- * block accumulates its kept slice products in ascending (K, s).
+ * block accumulates its kept slice products in ascending (K, s).  With
+ * tau_h > tau, the precision of every kept leaf product is chosen by its leaf
+ * norms as in oracle_multiply_tiered (R16): its slice products are formed
+ * exactly if nA2 * nB2 >= tau_h^2, else from operands rounded to p
+ * significant bits; tau_h = 0 forms every slice product exactly.
  * stats[0] = kept slice products, stats[1] = tested slice products.
  * Returns the number of kept leaf triples or an error code. */
 static double panel_norm2(const float *M, int64_t ld, int64_t n, int64_t r0, int64_t nr,
@@ -511,8 +515,9 @@ static double panel_norm2(const float *M, int64_t ld, int64_t n, int64_t r0, int
 }
 
 int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int64_t ldb,
-                               int64_t n, int64_t b, int64_t g, double tau, double alpha,
-                               double beta, double *C, int64_t ldc, int64_t *stats)
+                               int64_t n, int64_t b, int64_t g, double tau, double tau_h,
+                               int p, int ties_away, double alpha, double beta, double *C,
+                               int64_t ldc, int64_t *stats)
 {
     int d = oracle_depth(n, b);
     if (d < 0 || lda < n || ldb < n || ldc < n || !(tau >= 0.0) || g <= 0 || b % g) return OR_EARG;
@@ -528,10 +533,11 @@ int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int6
     int32_t *tri = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(cnt > 0 ? cnt : 1));
     if (!tri) { free(pa); free(pb); free(cand); return OR_ENOMEM; }
     oracle_cull_recursive(pa, pb, d, tau, tri, cnt, cand, cand + d + 1);
-    free(pa);
-    free(pb);
     free(cand);
     qsort(tri, (size_t)cnt, 3 * sizeof(int32_t), cmp_ijk);
+    int64_t nb = (int64_t)1 << d;
+    const double *la = pa + oracle_tier_offset(d);
+    const double *lb = pb + oracle_tier_offset(d);
     int64_t nbr = (n + b - 1) / b;
     int64_t kept = 0, tested = 0;
     double *acc = (double *)malloc(sizeof(double) * (size_t)(b * b * nbr));
@@ -541,6 +547,7 @@ int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int6
         memset(acc, 0, sizeof(double) * (size_t)(b * b * nbr));
         for (; t < cnt && tri[3 * t] == I; t++) {
             int64_t K = tri[3 * t + 1], J = tri[3 * t + 2];
+            int exact = tau_h <= tau || keep(la[I * nb + K], lb[K * nb + J], tau_h * tau_h);
             for (int64_t s0 = 0; s0 < b; s0 += g) {
                 int64_t k0 = K * b + s0;
                 double na = panel_norm2(A, lda, n, I * b, b, k0, g);
@@ -552,8 +559,15 @@ int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int6
                 for (int64_t r = 0; r < b && I * b + r < n; r++)
                     for (int64_t c = 0; c < b && J * b + c < n; c++) {
                         double sum = 0.0;
-                        for (int64_t q = k0; q < k0 + g && q < n; q++)
-                            sum += (double)A[(I * b + r) * lda + q] * (double)B[q * ldb + J * b + c];
+                        for (int64_t q = k0; q < k0 + g && q < n; q++) {
+                            double x = (double)A[(I * b + r) * lda + q];
+                            double y = (double)B[q * ldb + J * b + c];
+                            if (!exact) {
+                                x = oracle_round_sig(x, p, ties_away);
+                                y = oracle_round_sig(y, p, ties_away);
+                            }
+                            sum += x * y;
+                        }
                         blk[r * b + c] += sum;
                     }
             }
@@ -567,6 +581,8 @@ int64_t oracle_multiply_sliced(const float *A, int64_t lda, const float *B, int6
     }
     free(acc);
     free(tri);
+    free(pa);
+    free(pb);
     if (stats) {
         stats[0] = kept;
         stats[1] = tested;

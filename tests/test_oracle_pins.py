@@ -520,3 +520,16 @@ def test_tiered_error_bound_and_counts(p, tau, shift):
     plain = O.multiply(A, B, b, tau).C
     diff = np.linalg.norm(C - plain)
     assert 0 < diff <= (2 * u + u * u) * low * (1 + 1e-12)
+
+
+def test_sliced_tiered_with_one_slice_per_leaf_is_the_tiered_product():
+    """The sub-leaf cull with one slice per leaf is plain SpAMM (R14), so
+    with the precision tier it equals oracle_multiply_tiered bit for bit."""
+    n, b, tau = 300, 32, 1e-4
+    A = gen.exp_decay_nonsym(n, 0.85, seed=14)
+    B = gen.exp_decay(n, 0.9, seed=15)
+    tau_h = tau * 2.0 ** 10
+    Ct, m, exact, rounded = O.multiply_tiered(A, B, b, tau, tau_h, 11)
+    Cs, ms, kept, tested = O.multiply_sliced(A, B, b, b, tau, tau_h=tau_h, p=11)
+    assert exact > 0 and rounded > 0
+    assert np.array_equal(Cs, Ct) and ms == m and kept == tested == m
