@@ -80,10 +80,10 @@ def lib():
         L.oracle_sparsify.argtypes = [_p, _c_i64, _c_i64, _c_i64, _c_dbl, _c_dbl, _p]
         L.oracle_block.restype = _c_i64
         L.oracle_block.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _p, _p, _c_dbl,
-                                   _c_i64, _c_i64, _p]
+                                   _c_dbl, ctypes.c_int, ctypes.c_int, _c_i64, _c_i64, _p]
         L.oracle_blocks.restype = _c_i64
         L.oracle_blocks.argtypes = [_p, _c_i64, _p, _c_i64, _c_i64, _c_i64, _p, _p, _c_dbl,
-                                    _p, _c_i64, _p]
+                                    _c_dbl, ctypes.c_int, ctypes.c_int, _p, _c_i64, _p]
         L.oracle_threads.restype = ctypes.c_int
         L.oracle_set_threads.restype = None
         L.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -282,9 +282,11 @@ def sparsify(A, b: int, tau: float, norm2_max: float):
     return out, int(m)
 
 
-def blocks(A, B, b: int, tau: float, ij, pyrA=None, pyrB=None):
+def blocks(A, B, b: int, tau: float, ij, pyrA=None, pyrB=None, tau_h: float = 0.0,
+           p: int = 53, ties_away: bool = False):
     """Selected C blocks (no epilogue): array [len(ij), b, b] of FP64 and the
-    total number of kept products over them."""
+    total number of kept products over them; with tau_h > tau the precision
+    of each kept product chosen by its norm (R16)."""
     A = _f32(A)
     B = _f32(B)
     n = A.shape[0]
@@ -292,8 +294,8 @@ def blocks(A, B, b: int, tau: float, ij, pyrA=None, pyrB=None):
     pb = pyramid(B, b) if pyrB is None else pyrB
     ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int64).reshape(-1, 2))
     acc = np.zeros((len(ij), b, b), dtype=np.float64)
-    tot = lib().oracle_blocks(_ptr(A), n, _ptr(B), n, n, b, _ptr(pa), _ptr(pb), tau,
-                              _ptr(ij), len(ij), _ptr(acc))
+    tot = lib().oracle_blocks(_ptr(A), n, _ptr(B), n, n, b, _ptr(pa), _ptr(pb), tau, tau_h,
+                              int(p), 1 if ties_away else 0, _ptr(ij), len(ij), _ptr(acc))
     return acc, int(tot)
 
 

@@ -618,11 +618,14 @@ int64_t oracle_sparsify(const float *A, int64_t lda, int64_t n, int64_t b, doubl
  * oracle is too slow: acc = sum over ascending K with the leaf pair kept by
  * the SpAMM condition of A_IK B_KJ.  Testing the leaf pair directly gives
  * the recursive product's set because a parent's norm is never below its
- * children's (checked by the tests against oracle_cull_recursive).  Returns
- * the number of kept K. */
+ * children's (checked by the tests against oracle_cull_recursive).  With
+ * tau_h > tau each kept product's precision is chosen by its norm as in
+ * oracle_multiply_tiered (R16); tau_h = 0 forms every product exactly.
+ * Returns the number of kept K. */
 int64_t oracle_block(const float *A, int64_t lda, const float *B, int64_t ldb,
                      int64_t n, int64_t b, const double *pyrA, const double *pyrB,
-                     double tau, int64_t I, int64_t J, double *acc)
+                     double tau, double tau_h, int p, int ties_away, int64_t I, int64_t J,
+                     double *acc)
 {
     int d = oracle_depth(n, b);
     int64_t nb = (int64_t)1 << d;
@@ -632,7 +635,10 @@ int64_t oracle_block(const float *A, int64_t lda, const float *B, int64_t ldb,
     int64_t kept = 0;
     for (int64_t K = 0; K < nb; K++)
         if (keep(la[I * nb + K], lb[K * nb + J], tau * tau)) {
-            leaf_product(A, lda, B, ldb, n, b, I, K, J, acc);
+            if (tau_h <= tau || keep(la[I * nb + K], lb[K * nb + J], tau_h * tau_h))
+                leaf_product(A, lda, B, ldb, n, b, I, K, J, acc);
+            else
+                leaf_product_rounded(A, lda, B, ldb, n, b, I, K, J, p, ties_away, acc);
             kept++;
         }
     return kept;
@@ -642,13 +648,14 @@ int64_t oracle_block(const float *A, int64_t lda, const float *B, int64_t ldb,
  * blocks[2*q], blocks[2*q+1] = (I, J); acc gets b*b doubles per block. */
 int64_t oracle_blocks(const float *A, int64_t lda, const float *B, int64_t ldb,
                       int64_t n, int64_t b, const double *pyrA, const double *pyrB,
-                      double tau, const int64_t *blocks, int64_t nblocks, double *acc)
+                      double tau, double tau_h, int p, int ties_away, const int64_t *blocks,
+                      int64_t nblocks, double *acc)
 {
     int64_t total = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
     for (int64_t q = 0; q < nblocks; q++)
-        total += oracle_block(A, lda, B, ldb, n, b, pyrA, pyrB, tau, blocks[2 * q],
-                              blocks[2 * q + 1], acc + q * b * b);
+        total += oracle_block(A, lda, B, ldb, n, b, pyrA, pyrB, tau, tau_h, p, ties_away,
+                              blocks[2 * q], blocks[2 * q + 1], acc + q * b * b);
     return total;
 }
 

@@ -533,3 +533,19 @@ def test_sliced_tiered_with_one_slice_per_leaf_is_the_tiered_product():
     Cs, ms, kept, tested = O.multiply_sliced(A, B, b, b, tau, tau_h=tau_h, p=11)
     assert exact > 0 and rounded > 0
     assert np.array_equal(Cs, Ct) and ms == m and kept == tested == m
+
+
+def test_tiered_blocks_match_the_tiered_product():
+    """The sampled-block oracle with the precision tier equals the full
+    tiered product block for block (same ascending-K order, same rounding)."""
+    n, b, tau = 230, 16, 1e-4
+    A = gen.exp_decay_nonsym(n, 0.85, seed=16)
+    tau_h = tau * 2.0 ** 10
+    for p, away in ((11, False), (11, True), (8, False)):
+        C, _, exact, rounded = O.multiply_tiered(A, A, b, tau, tau_h, p, away)
+        assert exact > 0 and rounded > 0
+        ij = [(0, 0), (3, 7), (14, 14), (14, 0), (5, 9), (9, 5)]
+        acc, _ = O.blocks(A, A, b, tau, ij, tau_h=tau_h, p=p, ties_away=away)
+        for q, (I, J) in enumerate(ij):
+            blk = C[I * b:min(n, (I + 1) * b), J * b:min(n, (J + 1) * b)]
+            assert np.array_equal(acc[q][:blk.shape[0], :blk.shape[1]], blk)
