@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--alt", default="tf32x3",
                    help="also time this leaf precision on the same workload ('' = off)")
     p.add_argument("--slice", type=int, default=0, help="sub-leaf cull along k (16) or off (0)")
+    p.add_argument("--tier-bits", type=int, default=0,
+                   help="quick mode: precision chosen by norm, tau_h = 2^bits tau (0 = off)")
     p.add_argument("--flat", action="store_true",
                    help="quick mode: also time the flat, norm-sorted enumeration (Algorithm 1)")
     p.add_argument("--quick", action="store_true",
@@ -374,7 +376,8 @@ def run_quick(args, P, A, n, b, stream):
     """Time the SpAMM step alone at a fixed tau (no reference products)."""
     import torch
     tau = 1e-4 if args.tau == "auto" else float(args.tau)
-    ctx = P.Context(leaf=b, precision=args.precision, checked=True, slice=args.slice)
+    ctx = P.Context(leaf=b, precision=args.precision, checked=True, slice=args.slice,
+                    tier_bits=args.tier_bits)
     tree = ctx.build_norms(A)
     C = torch.empty_like(A)
     ctx.multiply(tree, tree, tau, C=C)
@@ -396,7 +399,14 @@ def run_quick(args, P, A, n, b, stream):
     if args.flat and tree.handle is not None:
         _, cnt, fms = ctx.cull_flat(tree, tree, tau, triples=False)
         flat = {"triples": cnt, "ms": fms}
+    leaf_ms = []
+    for _ in range(5):
+        ctx.multiply(tree, tree, tau, C=C)
+        leaf_ms.append(ctx.stats()["ms_numeric"])
     print(json.dumps({"mode": "quick", "n": n, "leaf": b, "tau": tau, "slice": args.slice,
+                      "tier_bits": args.tier_bits, "hi_products": st["hi_products"],
+                      "leaf_ms": statistics.median(leaf_ms),
+                      "leaf_tflops": st["kept_flops_clipped"] / statistics.median(leaf_ms) / 1e9,
                       "flat_enumeration": flat,
                       "slice_kept": st["slice_kept"], "slice_tested": st["slice_tested"],
                       "precision": args.precision, "ms_per_step": ms,

@@ -79,7 +79,22 @@ typedef struct {
                               of B_KJ over each group of 16 k is kept only if
                               their norms pass the SpAMM condition.
                               Tensor-core precisions and leaf >= 32 only. */
-    int32_t reserved[6];   /* must be zero */
+    int32_t tier_bits;     /* precision chosen by norm (the SpAMM condition of
+                              Eq. (norm_condition) applied a second time, at
+                              tau_h = 2^tier_bits tau): 0 = off; 1..40 = a kept
+                              leaf product with ||A_IK|| ||B_KJ|| < tau_h
+                              (squared, FP64, as the cull) runs one pass on
+                              the high parts of the split (hi * hi) instead
+                              of three, and the step's low parts are not
+                              loaded when none of its products needs them.
+                              The dropped cross terms are bounded by
+                              (2u + u^2) ||A_IK|| ||B_KJ|| with u = 2^-p, p
+                              the high part's significant bits (11 for
+                              SPAMM_PREC_F16X3 and SPAMM_PREC_TF32X3, 8 for
+                              SPAMM_PREC_BF16X3), so tier_bits = p - 1 keeps
+                              each such product's error near tau, like a
+                              culled one.  Split precisions only. */
+    int32_t reserved[5];   /* must be zero */
 } spamm_config;
 
 /* Fill *cfg with the defaults: leaf 16, SPAMM_PREC_FP32, tie_rel 1e-6,
@@ -123,6 +138,16 @@ typedef struct {
     int64_t packed_leaves_a;           /* leaves packed as A-role tensor-core operands
                                           (those a kept product can read) */
     int64_t packed_leaves_b;           /* leaves packed as B-role operands */
+    int64_t hi_products;               /* with tier_bits: kept leaf products run with
+                                          the full split (norm product >= tau_h); the
+                                          other leaf_triples - hi_products ran one
+                                          pass.  Without tier_bits: leaf_triples */
+    int64_t tie_band_hi;               /* kept leaf products with | ||A|| ||B|| - tau_h |
+                                          <= tie_rel * tau_h (0 without tier_bits) */
+    double kept_flops_clipped;         /* kept_flops counted over each leaf's extent
+                                          inside the n x n matrices (rows x columns x k
+                                          of the ragged last leaves clipped), i.e.
+                                          without the zero padding */
 } spamm_stats_t;
 
 /* Create a context bound to the current CUDA device and to `stream` (a
@@ -284,6 +309,11 @@ spamm_status spamm_stats_item(spamm_ctx *ctx, int32_t index, spamm_stats_t *out)
 spamm_status spamm_multiply_host(spamm_ctx *ctx, const float *A, const float *B, int64_t n,
                                  double tau, float alpha, float beta, float *C);
 
+/* spamm_triples restricted to the leaf triples that ran with the full split
+ * precision under tier_bits (norm product >= tau_h); all kept triples
+ * without tier_bits.  Synchronises. */
+spamm_status spamm_triples_hi(spamm_ctx *ctx, int32_t *host_out, int64_t cap, int64_t *count);
+
 /* Statistics of the last multiply on ctx.  Synchronises the stream.  Returns
  * the multiply's own status (e.g. CAPACITY) as well as writing *out. */
 spamm_status spamm_stats(spamm_ctx *ctx, spamm_stats_t *out);
@@ -306,6 +336,9 @@ spamm_status spamm_triples(spamm_ctx *ctx, int32_t *host_out, int64_t cap, int64
  * exit, sized for the worst case at n <= 4096.  The first call on each
  * device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is cached for the life of the process: do not call this entry
+ * point on a device after cudaDeviceReset (or any teardown of its primary
+ * context), since the cached address would then be stale.
  * All calls share the array and it keeps the last call's contents (each
  * call clears what must start at zero); calls that overlap on the GPU race
  * on it, so order them on one stream.  Asynchronous; when status_dev (a

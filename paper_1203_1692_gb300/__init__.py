@@ -46,6 +46,27 @@ def _check_matrix(A):
     return A.shape[0], A.stride(0)
 
 
+def _stats_dict(s) -> dict:
+    """spamm_stats_t as a dict."""
+    d = s.depth
+    return {
+        "status": s.status, "depth": d, "n": s.n, "leaf": s.leaf,
+        "precision": s.precision, "tau": s.tau,
+        "tier_candidates": list(s.tier_candidates[:d + 1]),
+        "tier_kept": list(s.tier_kept[:d + 1]),
+        "leaf_triples": s.leaf_triples, "tie_band": s.tie_band,
+        "active_steps": s.active_steps, "tiles": s.tiles,
+        "kept_flops": s.kept_flops, "dense_flops": s.dense_flops,
+        "pool_bytes": s.pool_bytes, "pool_needed_bytes": s.pool_needed_bytes,
+        "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
+        "ms_pack": s.ms_pack, "slice": s.slice, "slice_kept": s.slice_kept,
+        "slice_tested": s.slice_tested,
+        "packed_leaves_a": s.packed_leaves_a, "packed_leaves_b": s.packed_leaves_b,
+        "hi_products": s.hi_products, "tie_band_hi": s.tie_band_hi,
+        "kept_flops_clipped": s.kept_flops_clipped,
+    }
+
+
 class Tree:
     """Norm quadtree of a matrix (holds a reference to the matrix, unless it
     is a sparsified tree, which holds its own copy of the kept leaves)."""
@@ -102,11 +123,13 @@ class Context:
     """A SpAMM context on the current CUDA device and stream."""
 
     def __init__(self, leaf: int = 16, precision: str = "fp32", tie_rel: float = 1e-6,
-                 pool_bytes: int = 0, checked: bool = True, stream=None, slice: int = 0):
+                 pool_bytes: int = 0, checked: bool = True, stream=None, slice: int = 0,
+                 tier_bits: int = 0):
         torch = _torch()
         cfg = spamm_config_default()
         cfg.leaf = leaf
         cfg.slice = slice
+        cfg.tier_bits = tier_bits
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.tie_rel = tie_rel
         cfg.pool_bytes = pool_bytes
@@ -115,6 +138,7 @@ class Context:
         self.handle = spamm_create(self.stream.cuda_stream, cfg)
         self.leaf = leaf
         self.slice = slice
+        self.tier_bits = tier_bits
         self.precision = precision
 
     def build_norms(self, A) -> Tree:
@@ -203,22 +227,11 @@ class Context:
         spamm_reserve(self.handle, pool_bytes)
 
     def stats(self, raise_on_error: bool = True) -> dict:
-        s = spamm_stats(self.handle, raise_on_error)
-        d = s.depth
-        return {
-            "status": s.status, "depth": d, "n": s.n, "leaf": s.leaf,
-            "precision": s.precision, "tau": s.tau,
-            "tier_candidates": list(s.tier_candidates[:d + 1]),
-            "tier_kept": list(s.tier_kept[:d + 1]),
-            "leaf_triples": s.leaf_triples, "tie_band": s.tie_band,
-            "active_steps": s.active_steps, "tiles": s.tiles,
-            "kept_flops": s.kept_flops, "dense_flops": s.dense_flops,
-            "pool_bytes": s.pool_bytes, "pool_needed_bytes": s.pool_needed_bytes,
-            "ms_symbolic": s.ms_symbolic, "ms_numeric": s.ms_numeric, "ms_total": s.ms_total,
-            "ms_pack": s.ms_pack, "slice": s.slice, "slice_kept": s.slice_kept,
-            "slice_tested": s.slice_tested,
-            "packed_leaves_a": s.packed_leaves_a, "packed_leaves_b": s.packed_leaves_b,
-        }
+        return _stats_dict(spamm_stats(self.handle, raise_on_error))
+
+    def stats_item(self, index: int, raise_on_error: bool = True) -> dict:
+        """Statistics of product ``index`` of the last batched multiply."""
+        return _stats_dict(spamm_stats_item(self.handle, index, raise_on_error))
 
     def per_product_flops(self, count: int) -> list:
         """Kept flops of each product of the last batched multiply."""
@@ -236,11 +249,15 @@ class Context:
                                        cnt)
         return out[:cnt], cnt, ms
 
-    def triples(self) -> np.ndarray:
+    def triples(self, hi: bool = False) -> np.ndarray:
+        """Surviving leaf triples (I, K, J) of the last multiply; with hi,
+        only those that ran with the full split precision (tier_bits)."""
+        f = _abi.spamm_triples_hi if hi else spamm_triples
         count = ctypes.c_int64()
-        _abi.lib().spamm_triples(self.handle, None, 0, ctypes.byref(count))
+        getattr(_abi.lib(), "spamm_triples_hi" if hi else "spamm_triples")(
+            self.handle, None, 0, ctypes.byref(count))
         out = np.empty((max(count.value, 1), 3), dtype=np.int32)
-        m = spamm_triples(self.handle, out.ctypes.data, count.value)
+        m = f(self.handle, out.ctypes.data, count.value)
         return out[:m]
 
     def close(self):

@@ -37,7 +37,7 @@ class spamm_config(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tie_rel", ctypes.c_double), ("pool_bytes", ctypes.c_int64),
                 ("checked", ctypes.c_int32), ("slice", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("tier_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class spamm_stats_t(ctypes.Structure):
@@ -54,7 +54,9 @@ class spamm_stats_t(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("ms_pack", ctypes.c_float),
                 ("slice", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("slice_kept", ctypes.c_int64), ("slice_tested", ctypes.c_int64),
-                ("packed_leaves_a", ctypes.c_int64), ("packed_leaves_b", ctypes.c_int64)]
+                ("packed_leaves_a", ctypes.c_int64), ("packed_leaves_b", ctypes.c_int64),
+                ("hi_products", ctypes.c_int64), ("tie_band_hi", ctypes.c_int64),
+                ("kept_flops_clipped", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -91,6 +93,7 @@ SIGNATURES = {
     "spamm_stats": (_i32, [_vp, ctypes.POINTER(spamm_stats_t)]),
     "spamm_stats_item": (_i32, [_vp, _i32, ctypes.POINTER(spamm_stats_t)]),
     "spamm_triples": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "spamm_triples_hi": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "spamm_cull_flat": (_i32, [_vp, _vp, _vp, _dbl, _vp, _i64, ctypes.POINTER(_i64),
                                ctypes.POINTER(_flt)]),
     "spamm_multiply_static": (_i32, [_vp, _i64, _vp, _i64, _i64, _dbl, _flt, _flt, _vp, _i64,
@@ -262,6 +265,12 @@ def spamm_stats_item(ctx, index: int, raise_on_error: bool = True) -> spamm_stat
 def spamm_triples(ctx, out_ptr: int, cap: int) -> int:
     cnt = _i64()
     check(lib().spamm_triples(ctx, _vp(out_ptr), cap, ctypes.byref(cnt)), ctx)
+    return cnt.value
+
+
+def spamm_triples_hi(ctx, out_ptr: int, cap: int) -> int:
+    cnt = _i64()
+    check(lib().spamm_triples_hi(ctx, _vp(out_ptr), cap, ctypes.byref(cnt)), ctx)
     return cnt.value
 
 

@@ -33,6 +33,7 @@
 // all its products in one launch each, with the blocks of a product sized
 // to its share of the work.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "spamm_internal.cuh"
@@ -58,6 +59,10 @@ struct CullProd {
     int SL;                    // mask pairs per step: 1, or the 16-wide slices of a leaf
     int chunks;                // 16-wide K-chunks per leaf (b / 16)
     int nl;                    // leaves per side holding data
+    int tier;                  // precision chosen by norm: also emit the full-split masks
+    Thresh thh;                // its threshold tau_h
+    int64_t n;                 // matrix order (the clipped extent of the ragged leaves)
+    int b;                     // leaf size
 };
 
 constexpr int kCullBatch = 64;
@@ -256,7 +261,8 @@ __global__ void __launch_bounds__(1024) k_group_scan(CullBatch<NB> cb) {
         ctl->ent_off = end;
         ctl->pk_off = end + (m + 1) / 2;
         ctl->pm_off = ctl->pk_off + (ms + 1) / 2;
-        ctl->need_words = ctl->pm_off + 2 * ms * (unsigned long long)q.SL;
+        ctl->ph_off = ctl->pm_off + 2 * ms * (unsigned long long)q.SL;
+        ctl->need_words = ctl->ph_off + (q.tier ? 2 * ms : 0ull);
         if (ctl->need_words > q.cap || m >= 0xffffffffull / (unsigned long long)q.S)
             ctl->status |= ST_OVERFLOW;
     }
@@ -330,7 +336,9 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
     constexpr int KPW = WIN / S;             // K' per window
     extern __shared__ uint32_t dyn[];        // K' bitmaps of both halves, then the K' list
     __shared__ unsigned long long masks[WIN][SL][2];
-    __shared__ unsigned long long st_slk, st_slt;
+    // products of each step that keep the full split precision (q.tier)
+    __shared__ unsigned long long hmasks[WIN][2];
+    __shared__ unsigned long long st_slk, st_slt, st_vol, st_nhi, st_tiehi;
     __shared__ uint32_t st_iters;
     // per-warp staged norms of one sub-cube: levels 1..DS, A side [x][k], B side [k][y]
     __shared__ double nA[kCullWarps][84], nB[kCullWarps][84];
@@ -360,6 +368,7 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
     const uint32_t* ent = reinterpret_cast<const uint32_t*>(pool + ctl->ent_off);
     uint32_t* pk = reinterpret_cast<uint32_t*>(pool + ctl->pk_off);
     unsigned long long* pm = reinterpret_cast<unsigned long long*>(pool + ctl->pm_off);
+    unsigned long long* ph = reinterpret_cast<unsigned long long*>(pool + ctl->ph_off);
     const int words = ((1 << tt) + 31) >> 5;
     uint32_t* bm0 = dyn;
     uint32_t* bm1 = dyn + words;
@@ -369,9 +378,18 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
     if (tid == 0) {
         st_tie = 0ull;
         st_slk = st_slt = 0ull;
+        st_vol = st_nhi = st_tiehi = 0ull;
         st_iters = 0u;
     }
     unsigned long long slk = 0, slt = 0;     // kept / tested slice products
+    // clipped volume (rows x k x columns inside the matrix) of the kept
+    // products, and the precision tier's counts
+    unsigned long long vol = 0, nhi = 0, tie_hi = 0;
+    const int64_t nn = q.n, lb = q.b;
+    auto ext = [&](int64_t L) -> unsigned long long {   // rows of leaf L inside the matrix
+        const int64_t r = nn - L * lb;
+        return (unsigned long long)(r < lb ? (r > 0 ? r : 0) : lb);
+    };
     __syncthreads();
     for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
         const uint32_t v = ent[e], k = v >> 1;
@@ -453,6 +471,45 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                         tie += tb ? 1 : 0;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    if (l == DS) {
+                        // leaf level: the clipped extent of every kept leaf
+                        // triple and, with the precision tier, whether its
+                        // norm product reaches tau_h (the same FP64 test)
+                        const int64_t I = ((int64_t)I0 << DS) + xi;
+                        const int64_t K = ((int64_t)Kp << DS) + ki;
+                        const int64_t J = ((int64_t)J0 << DS) + yi;
+                        bool hi = false;
+                        if (ok) {
+                            if (SL == 1) vol += ext(I) * ext(K) * ext(J);
+                            if (q.tier) {
+                                bool tb;
+                                hi = spamm_keep(nA[warp][so + xi * side + ki],
+                                                nB[warp][so + ki * side + yi], q.thh, &tb);
+                                tie_hi += tb ? 1 : 0;
+                                nhi += hi ? 1 : 0;
+                            }
+                        }
+                        if (q.tier) {
+                            if (DS == 3) {
+                                const unsigned hb = __ballot_sync(0xffffffffu, hi);
+                                const int kk = r >> 1;
+                                if (lane == 0) {
+                                    if ((r & 1) == 0) hmasks[g * S + kk][half] = hb;
+                                    else hmasks[g * S + kk][half] |= (unsigned long long)hb << 32;
+                                }
+                            } else {
+                                const unsigned long long bit = hi ? 1ull << (yi * 8 + xi) : 0ull;
+#pragma unroll
+                                for (int kq = 0; kq < S; ++kq) {
+                                    const unsigned long long mine = (idx < per && ki == kq) ? bit : 0ull;
+                                    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)mine);
+                                    const uint32_t hh = __reduce_or_sync(0xffffffffu, (uint32_t)(mine >> 32));
+                                    if (r == 0 && lane == 0) hmasks[g * S + kq][half] = 0ull;
+                                    if (lane == 0) hmasks[g * S + kq][half] |= ((unsigned long long)hh << 32) | lo;
+                                }
+                            }
+                        }
+                    }
                     if (l == DS && SL > 1) {
                         // leaf level with the sub-leaf cull: per slice, the
                         // kept leaf triples whose panels pass, remapped to the
@@ -470,6 +527,11 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                                 tie += tb ? 1 : 0;
                                 slt += 1;
                                 slk += oks ? 1 : 0;
+                                if (oks) {
+                                    const int64_t kr = nn - K * lb - 16 * sl;
+                                    vol += ext(I) * ext(J) *
+                                           (unsigned long long)(kr < 16 ? (kr > 0 ? kr : 0) : 16);
+                                }
                             }
                             const unsigned long long bit = oks ? 1ull << (yi * 8 + xi) : 0ull;
 #pragma unroll
@@ -512,8 +574,24 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                 if (l == 2) lv2[1] = 0ull;
             }
             if (DS == 0) {
+                // the tile node is the leaf (I0, Kp, J0), kept iff it has an
+                // entry; its precision tier from the leaf norms
+                const unsigned long long rc = has ? ext(I0) * ext(J0) : 0ull;
+                if (q.tier && lane == 0) {
+                    bool hi = false;
+                    if (has) {
+                        const int64_t w = (int64_t)1 << tt;
+                        const int64_t off_t = (((int64_t)1 << (2 * tt)) - 1) / 3;
+                        bool tb;
+                        hi = spamm_keep(pyrA[off_t + (int64_t)I0 * w + Kp],
+                                        pyrB[off_t + (int64_t)Kp * w + J0], q.thh, &tb);
+                        tie_hi += tb ? 1 : 0;
+                        nhi += hi ? 1 : 0;
+                    }
+                    hmasks[g][half] = hi ? 1ull : 0ull;
+                }
                 if (SL > 1) {
-                    // the tile node is the leaf: lane sl tests slice sl
+                    // lane sl tests slice sl
                     bool oks = false;
                     if (lane < SL && has) {
                         bool tb;
@@ -522,12 +600,17 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                         tie += tb ? 1 : 0;
                         slt += 1;
                         slk += oks ? 1 : 0;
+                        if (oks) {
+                            const int64_t kr = nn - (int64_t)Kp * lb - 16 * lane;
+                            vol += rc * (unsigned long long)(kr < 16 ? (kr > 0 ? kr : 0) : 16);
+                        }
                     }
                     const unsigned bs = __ballot_sync(0xffffffffu, oks);
                     if (lane == 0)
                         for (int sl = 0; sl < SL; ++sl) masks[g][sl][half] = (bs >> sl) & 1u;
                 } else if (lane == 0) {
                     masks[g][0][half] = has ? 1ull : 0ull;
+                    vol += rc * ext(Kp);
                 }
             }
             __syncwarp();  // staged norms are reused by the next sub-cube
@@ -552,6 +635,10 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
                     pm[2 * ((size_t)pos * SL + sl)] = masks[i][sl][0];
                     pm[2 * ((size_t)pos * SL + sl) + 1] = masks[i][sl][1];
                 }
+                if (q.tier) {
+                    ph[2 * (size_t)pos] = hmasks[i][0];
+                    ph[2 * (size_t)pos + 1] = hmasks[i][1];
+                }
                 it_mine += SL > 1 ? (uint32_t)__popc(live) : (uint32_t)q.chunks;
             }
             written += total_s;
@@ -573,12 +660,18 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
         tie += __shfl_xor_sync(0xffffffffu, tie, o);
         slk += __shfl_xor_sync(0xffffffffu, slk, o);
         slt += __shfl_xor_sync(0xffffffffu, slt, o);
+        vol += __shfl_xor_sync(0xffffffffu, vol, o);
+        nhi += __shfl_xor_sync(0xffffffffu, nhi, o);
+        tie_hi += __shfl_xor_sync(0xffffffffu, tie_hi, o);
     }
     if (lane == 0 && tie) atomicAdd(&st_tie, tie);
     if (lane == 0 && slt) {
         atomicAdd(&st_slk, slk);
         atomicAdd(&st_slt, slt);
     }
+    if (lane == 0 && vol) atomicAdd(&st_vol, vol);
+    if (lane == 0 && nhi) atomicAdd(&st_nhi, nhi);
+    if (lane == 0 && tie_hi) atomicAdd(&st_tiehi, tie_hi);
     __syncthreads();
     if (tid == 0) {
         steps[u] = written;
@@ -588,6 +681,9 @@ __global__ void __launch_bounds__(kCullWarps * 32, 3) k_tile_cull(CullBatch<NB> 
             atomicAdd(&ctl->slice_tested, st_slt);
         }
         atomicAdd(&ctl->active_steps, (unsigned long long)written);
+        if (st_vol) atomicAdd(&ctl->clip_vol, st_vol);
+        if (st_nhi) atomicAdd(&ctl->hi_products, st_nhi);
+        if (st_tiehi) atomicAdd(&ctl->tie_hi, st_tiehi);
         for (int l = 0; l < DS; ++l) {
             atomicAdd(&ctl->tier_cand[tt + 1 + l], st_cand[l]);
             atomicAdd(&ctl->tier_count[tt + 1 + l], st_kept[l]);
@@ -768,6 +864,12 @@ static CullProd make_prod(spamm_ctx* c, const spamm_tree* A, const spamm_tree* B
     q.SL = (A->slices && B->slices) ? A->slices : 1;
     q.chunks = A->b / 16;
     q.nl = (int)A->nl;
+    q.tier = c->cfg.tier_bits > 0 ? 1 : 0;
+    // tau_h = 2^tier_bits tau, exact (a power-of-two scale), so tau_h^2 is
+    // formed as the oracle forms it
+    q.thh = make_thresh(q.tier ? ldexp(tau, c->cfg.tier_bits) : tau, rel);
+    q.n = A->n;
+    q.b = A->b;
     return q;
 }
 

@@ -60,6 +60,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "spamm_internal.cuh"
 
@@ -272,6 +273,9 @@ struct TcProd {
     const int64_t* b_off;
     // FP16 split: largest squared leaf norms of A and B (their scales)
     const double* gmax;
+    // precision chosen by norm: the step list carries a second mask pair per
+    // step, the products that keep the full split; the others run hi * hi
+    int tier;
 };
 
 constexpr int kMaxBatch = 64;
@@ -302,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         bar_drain;
     __shared__ uint32_t tmem_slot;
     __shared__ unsigned long long st_mask[ST][T::kSPS][2];  // masks of each stage slot
+    __shared__ unsigned long long st_hmask[ST][T::kSPS][2]; // of those, the full-split products
     __shared__ uint32_t st_count[ST];                        // filled slots of each stage
     __shared__ volatile int abort_flag;
     __shared__ unsigned long long issued_s, consumed_s;
@@ -309,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     // items.  Everything else is read from the parameter space: pointers that
     // come from there are known to be global, which keeps the MMA issue loop
     // as tight as with a single product.
-    __shared__ unsigned long long sp_pk[kMaxBatch], sp_pm[kMaxBatch];
+    __shared__ unsigned long long sp_pk[kMaxBatch], sp_pm[kMaxBatch], sp_ph[kMaxBatch];
     __shared__ int sp_skip[kMaxBatch], sp_end[kMaxBatch];
     __shared__ float2 sp_uns[PREC == SPAMM_PREC_F16X3 ? kMaxBatch : 1];  // 2^-(kA + kB)
 
@@ -323,6 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         const TcProd& g = bt.prods[i];
         sp_pk[i] = g.ctl->pk_off;
         sp_pm[i] = g.ctl->pm_off;
+        sp_ph[i] = g.ctl->ph_off;
         // a product whose cull failed is left untouched (its status says why)
         sp_skip[i] = (g.ctl->status & (ST_OVERFLOW | ST_NONFINITE)) ? 1 : 0;
         sp_end[i] = g.base + g.tr * g.tc;
@@ -386,6 +392,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(q.pool + sp_pk[pi]);
             const unsigned long long* pm =
                 reinterpret_cast<const unsigned long long*>(q.pool + sp_pm[pi]);
+            const unsigned long long* ph =
+                reinterpret_cast<const unsigned long long*>(q.pool + sp_ph[pi]);
+            const bool tier = q.tier != 0;
             const int u = tile_at(k - q.base, q.tr, q.tc);
             const int64_t srow = (int64_t)(u / q.tc) * TL;
             const int64_t scol = (int64_t)(u % q.tc) * TLC;
@@ -399,8 +408,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const int64_t ga = srow / TL, gb = scol / TLC;          // tile's pack groups
             int64_t bandK = -1;
             int64_t a_lo = 0, a_hi = -1, a_off = 0, b_lo = 0, b_hi = -1, b_off = 0;
+            // lean: no product of the step keeps the full split (precision
+            // chosen by norm), so only the high parts are loaded
             auto issue = [&](int64_t K, int kc0, int m, unsigned long long m0,
-                             unsigned long long m1) {
+                             unsigned long long m1, unsigned long long h0,
+                             unsigned long long h1, bool lean) {
                 if (fill == 0) {
                     s = (int)(stage_it % ST);
                     const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
@@ -439,9 +451,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         na = hi >= lo ? hi - lo + 1 : 0;
                         sa = a_off + kc0 * (a_hi - a_lo + 1) + (lo - a_lo);
                         da = lo - srow;
-                        bytes += (uint32_t)(T::kParts * na * piece);
+                        bytes += (uint32_t)((lean ? 1 : T::kParts) * na * piece);
                     } else {
-                        bytes += (uint32_t)T::kASlot;
+                        bytes += (uint32_t)(lean ? T::kSlice : T::kASlot);
                     }
                     int64_t sb2 = 0, nb2 = TLC, db = 0;
                     if (q.b_lo) {
@@ -450,17 +462,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         nb2 = hi >= lo ? hi - lo + 1 : 0;
                         sb2 = b_off + kc0 * (b_hi - b_lo + 1) + (lo - b_lo);
                         db = lo - scol;
-                        bytes += (uint32_t)(T::kParts * nb2 * piece);
+                        bytes += (uint32_t)((lean ? 1 : T::kParts) * nb2 * piece);
                     } else {
-                        bytes += (uint32_t)T::kBSlot;
+                        bytes += (uint32_t)(lean ? 2 * T::kSlice : T::kBSlot);
                     }
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
                                  "r"(bytes)
                                  : "memory");
+                    const int parts = lean ? 1 : T::kParts;
                     if (q.a_lo) {
 #pragma unroll
                         for (int part = 0; part < T::kParts; ++part)
-                            if (na)
+                            if (na && part < parts)
                                 bulk_g2s(smem_u32(sa_dst + part * T::kSlice + da * piece),
                                          static_cast<const unsigned char*>(q.pa[part]) +
                                              (size_t)sa * piece,
@@ -468,12 +481,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     } else {
                         bulk_g2s(smem_u32(sa_dst),
                                  static_cast<const unsigned char*>(q.pa[0]) + a_src,
-                                 (uint32_t)T::kASlot, full);
+                                 (uint32_t)(lean ? T::kSlice : T::kASlot), full);
                     }
                     if (q.b_lo) {
 #pragma unroll
                         for (int part = 0; part < T::kParts; ++part)
-                            if (nb2)
+                            if (nb2 && part < parts)
                                 bulk_g2s(smem_u32(sb_dst + 2 * part * T::kSlice + db * piece),
                                          static_cast<const unsigned char*>(q.pb[part]) +
                                              (size_t)sb2 * piece,
@@ -481,7 +494,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     } else {
                         bulk_g2s(smem_u32(sb_dst),
                                  static_cast<const unsigned char*>(q.pb[0]) + b_src,
-                                 (uint32_t)T::kBSlot, full);
+                                 (uint32_t)(lean ? 2 * T::kSlice : T::kBSlot), full);
+                    }
+                } else if (lean) {
+                    // the high part of each chunk: the first kSlice (A) and
+                    // 2 kSlice (B) bytes of its slot, one copy each
+                    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
+                                 "r"((uint32_t)(m * 3 * T::kSlice))
+                                 : "memory");
+                    for (int j = 0; j < m; ++j) {
+                        bulk_g2s(smem_u32(sa_dst + (size_t)j * T::kASlot),
+                                 static_cast<const unsigned char*>(q.pa[0]) + a_src +
+                                     (size_t)j * T::kASlot,
+                                 (uint32_t)T::kSlice, full);
+                        bulk_g2s(smem_u32(sb_dst + (size_t)j * T::kBSlot),
+                                 static_cast<const unsigned char*>(q.pb[0]) + b_src +
+                                     (size_t)j * T::kBSlot,
+                                 (uint32_t)(2 * T::kSlice), full);
                     }
                 } else {
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
@@ -495,6 +524,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 for (int j = 0; j < m; ++j) {
                     st_mask[s][fill + j][0] = m0;
                     st_mask[s][fill + j][1] = m1;
+                    st_hmask[s][fill + j][0] = h0;
+                    st_hmask[s][fill + j][1] = h1;
                 }
                 fill += m;
                 if (fill == T::kSPS) {
@@ -509,23 +540,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 uint32_t ck = lane < (int)ns ? pk[sb + lane] : 0u;
                 unsigned long long cm0 = lane < (int)ns ? pm[2 * (sb + lane)] : 0ull;
                 unsigned long long cm1 = lane < (int)ns ? pm[2 * (sb + lane) + 1] : 0ull;
+                unsigned long long ch0 = cm0, ch1 = cm1;
+                if (tier) {
+                    ch0 = lane < (int)ns ? ph[2 * (sb + lane)] : 0ull;
+                    ch1 = lane < (int)ns ? ph[2 * (sb + lane) + 1] : 0ull;
+                }
                 for (uint32_t base = 0; base < ns && ok; base += 32) {
                     const bool more = base + 32 + lane < ns;
                     const uint32_t nk = more ? pk[sb + base + 32 + lane] : 0u;
                     const unsigned long long nm0 = more ? pm[2 * (sb + base + 32 + lane)] : 0ull;
                     const unsigned long long nm1 = more ? pm[2 * (sb + base + 32 + lane) + 1] : 0ull;
+                    unsigned long long nh0 = nm0, nh1 = nm1;
+                    if (tier) {
+                        nh0 = more ? ph[2 * (sb + base + 32 + lane)] : 0ull;
+                        nh1 = more ? ph[2 * (sb + base + 32 + lane) + 1] : 0ull;
+                    }
                     const uint32_t cnt = ns - base < 32 ? ns - base : 32;
                     for (uint32_t j = 0; j < cnt && ok; ++j) {
                         const int64_t K = __shfl_sync(0xffffffffu, ck, j);
                         const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
                         const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
+                        const unsigned long long h0 = __shfl_sync(0xffffffffu, ch0, j);
+                        const unsigned long long h1 = __shfl_sync(0xffffffffu, ch1, j);
+                        const bool lean = tier && (h0 | h1) == 0ull;
                         // the step's chunks in runs that end at stage boundaries
                         // (one chunk per run when an operand is sparsified)
                         for (int kc = 0; kc < CHUNKS && ok;) {
                             int m = 1;
                             if (lane == 0) {
                                 if (!BAND) m = min(CHUNKS - kc, T::kSPS - fill);
-                                issue(K, kc, m, m0, m1);
+                                issue(K, kc, m, m0, m1, h0, h1, lean);
                             }
                             m = __shfl_sync(0xffffffffu, m, 0);
                             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -535,42 +579,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     ck = nk;
                     cm0 = nm0;
                     cm1 = nm1;
+                    ch0 = nh0;
+                    ch1 = nh1;
                 }
             } else {
                 // sub-leaf cull: a mask pair per (step, K-chunk); chunks whose
                 // slice products were all culled are not loaded at all
+                // (the full-split masks are per step, shared by its slices)
                 const uint32_t nit = ns * CHUNKS;
                 auto ld = [&](uint32_t it, uint32_t& kk, unsigned long long& a,
-                              unsigned long long& b) {
+                              unsigned long long& b, unsigned long long& ha,
+                              unsigned long long& hb) {
                     if (it < nit) {
                         const uint64_t st = sb + it / CHUNKS;
                         kk = pk[st];
                         a = pm[2 * (st * CHUNKS + it % CHUNKS)];
                         b = pm[2 * (st * CHUNKS + it % CHUNKS) + 1];
+                        ha = tier ? ph[2 * st] & a : a;
+                        hb = tier ? ph[2 * st + 1] & b : b;
                     } else {
                         kk = 0u;
-                        a = b = 0ull;
+                        a = b = ha = hb = 0ull;
                     }
                 };
                 uint32_t ck;
-                unsigned long long cm0, cm1;
-                ld(lane, ck, cm0, cm1);
+                unsigned long long cm0, cm1, ch0, ch1;
+                ld(lane, ck, cm0, cm1, ch0, ch1);
                 for (uint32_t base = 0; base < nit && ok; base += 32) {
                     uint32_t nk;
-                    unsigned long long nm0, nm1;
-                    ld(base + 32 + lane, nk, nm0, nm1);
+                    unsigned long long nm0, nm1, nh0, nh1;
+                    ld(base + 32 + lane, nk, nm0, nm1, nh0, nh1);
                     const uint32_t cnt = nit - base < 32 ? nit - base : 32;
                     for (uint32_t j = 0; j < cnt && ok; ++j) {
                         const int64_t K = __shfl_sync(0xffffffffu, ck, j);
                         const unsigned long long m0 = __shfl_sync(0xffffffffu, cm0, j);
                         const unsigned long long m1 = __shfl_sync(0xffffffffu, cm1, j);
+                        const unsigned long long h0 = __shfl_sync(0xffffffffu, ch0, j);
+                        const unsigned long long h1 = __shfl_sync(0xffffffffu, ch1, j);
                         if ((m0 | m1) == 0ull) continue;
-                        if (lane == 0) issue(K, (int)((base + j) % CHUNKS), 1, m0, m1);
+                        const bool lean = tier && (h0 | h1) == 0ull;
+                        if (lane == 0) issue(K, (int)((base + j) % CHUNKS), 1, m0, m1, h0, h1, lean);
                         ok = __shfl_sync(0xffffffffu, ok, 0);
                     }
                     ck = nk;
                     cm0 = nm0;
                     cm1 = nm1;
+                    ch0 = nh0;
+                    ch1 = nh1;
                 }
             }
             // a stage never spans two tiles
@@ -614,11 +669,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     consumed_s = stage_it + 1;
                     // the stage's masks in one go, then its slots unrolled (slot
                     // offsets become constants); this loop is the MMA issue path
-                    unsigned long long mk0[T::kSPS], mk1[T::kSPS];
+                    unsigned long long mk0[T::kSPS], mk1[T::kSPS], hk0[T::kSPS], hk1[T::kSPS];
 #pragma unroll
                     for (int jj = 0; jj < T::kSPS; ++jj) {
                         mk0[jj] = st_mask[s][jj][0];
                         mk1[jj] = st_mask[s][jj][1];
+                        hk0[jj] = st_hmask[s][jj][0];
+                        hk1[jj] = st_hmask[s][jj][1];
                     }
                     const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
 #pragma unroll
@@ -642,10 +699,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         const uint32_t b_hi =
                             sbuf + (uint32_t)(T::kSPS * T::kASlot) + jj * (uint32_t)T::kBSlot;
                         const uint32_t b_lo = b_hi + 2 * T::kSlice;
-                        // Runs of column leaves with the same kept row leaves:
-                        // a column y starts a run when its row mask is non-zero
-                        // and differs from column y-1's.  Uniform halves (the
-                        // common case on dense blocks) give one run directly.
                         constexpr unsigned long long kRep =
                             TL == 8   ? 0x0101010101010101ull
                             : TL == 4 ? 0x0000000001010101ull
@@ -659,26 +712,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                             ah[kk] = make_desc(a_hi + (uint32_t)kk * 256u, 128, T::kSBO);
                             al[kk] = make_desc(a_lo + (uint32_t)kk * 256u, 128, T::kSBO);
                         }
-                        if (mask0 == kFull && mask1 == kFull) {
-                            // every product of the step kept (the common case on
-                            // dense blocks): one 128 x 256 MMA per pass, no masks
-                            constexpr uint32_t idesc_full = make_idesc(T::kAB, 128, 256);
+                        // The MMAs of one pass set over the products of masks
+                        // (r0, r1): MODE 3 = all three of the split (lo*hi,
+                        // hi*lo, hi*hi; hi*hi alone for single TF32), 1 = hi*hi,
+                        // 2 = the cross terms.  Runs of column leaves with the
+                        // same kept row leaves: a column y starts a run when its
+                        // row mask is non-zero and differs from column y-1's.
+                        // Uniform halves (the common case on dense blocks) give
+                        // one run directly.
+                        auto passes = [&](unsigned long long r0, unsigned long long r1,
+                                          auto mode_c) {
+                            constexpr int MODE = decltype(mode_c)::value;
+                            constexpr bool kCross = PREC != SPAMM_PREC_TF32 && MODE != 1;
+                            constexpr bool kHiHi = MODE != 2;
+                            if (r0 == kFull && r1 == kFull) {
+                                // every product of the step: one 128 x 256 MMA per
+                                // pass, no masks
+                                constexpr uint32_t idesc_full = make_idesc(T::kAB, 128, 256);
 #pragma unroll
-                            for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                const uint32_t koff = (uint32_t)kk * 256u;
-                                const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
-                                if (PREC != SPAMM_PREC_TF32) {
-                                    const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
-                                    mma_all<PREC>(dacc, al[kk], bh, idesc_full, 1u);
-                                    mma_all<PREC>(dacc, ah[kk], bl, idesc_full, 1u);
+                                for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                    const uint32_t koff = (uint32_t)kk * 256u;
+                                    const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
+                                    if (kCross) {
+                                        const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
+                                        mma_all<PREC>(dacc, al[kk], bh, idesc_full, 1u);
+                                        mma_all<PREC>(dacc, ah[kk], bl, idesc_full, 1u);
+                                    }
+                                    if (kHiHi) mma_all<PREC>(dacc, ah[kk], bh, idesc_full, 1u);
                                 }
-                                mma_all<PREC>(dacc, ah[kk], bh, idesc_full, 1u);
+                                return;
                             }
-                        } else {
-                            const uint32_t x0 = (uint32_t)mask0 & 0xFFu;
-                            const uint32_t x1 = (uint32_t)mask1 & 0xFFu;
-                            const bool u0 = mask0 == (unsigned long long)x0 * kRep;
-                            const bool u1 = mask1 == (unsigned long long)x1 * kRep;
+                            const uint32_t x0 = (uint32_t)r0 & 0xFFu;
+                            const uint32_t x1 = (uint32_t)r1 & 0xFFu;
+                            const bool u0 = r0 == (unsigned long long)x0 * kRep;
+                            const bool u1 = r1 == (unsigned long long)x1 * kRep;
                             uint32_t starts, nz;
                             if (u0 && u1) {
                                 starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
@@ -691,8 +758,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
 #pragma unroll
                                 for (int yy = 0; yy < TLC; ++yy) {
                                     const uint32_t xm =
-                                        yy < TL ? (uint32_t)(mask0 >> (8 * yy)) & 0xFFu
-                                                : (uint32_t)(mask1 >> (8 * (yy - TL))) & 0xFFu;
+                                        yy < TL ? (uint32_t)(r0 >> (8 * yy)) & 0xFFu
+                                                : (uint32_t)(r1 >> (8 * (yy - TL))) & 0xFFu;
                                     if (xm) nz |= 1u << yy;
                                     if (xm && xm != prev) starts |= 1u << yy;
                                     prev = xm;
@@ -705,8 +772,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                                 const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
                                 const int len = yend - y;
                                 const uint32_t xm =
-                                    y < TL ? (uint32_t)(mask0 >> (8 * y)) & 0xFFu
-                                           : (uint32_t)(mask1 >> (8 * (y - TL))) & 0xFFu;
+                                    y < TL ? (uint32_t)(r0 >> (8 * y)) & 0xFFu
+                                           : (uint32_t)(r1 >> (8 * (y - TL))) & 0xFFu;
                                 // disable-output-lane bits: row r of the tile is
                                 // lane r, and a dropped row leaf x masks its b rows
                                 uint32_t dis[4];
@@ -735,15 +802,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                                     const uint32_t koff = (uint32_t)kk * 256u;
                                     const uint64_t bh =
                                         make_desc(b_hi + boff + koff, 128, T::kSBO);
-                                    if (PREC != SPAMM_PREC_TF32) {
+                                    if (kCross) {
                                         const uint64_t bl =
                                             make_desc(b_lo + boff + koff, 128, T::kSBO);
                                         mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
                                         mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
                                     }
-                                    mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
+                                    if (kHiHi) mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
                                 }
                             }
+                        };
+                        const unsigned long long hmask0 = hk0[jj];
+                        const unsigned long long hmask1 = hk1[jj];
+                        if (hmask0 == mask0 && hmask1 == mask1) {
+                            passes(mask0, mask1, std::integral_constant<int, 3>{});
+                        } else {
+                            // precision chosen by norm: hi * hi for every kept
+                            // product, the cross terms for the full-split ones
+                            passes(mask0, mask1, std::integral_constant<int, 1>{});
+                            if ((hmask0 | hmask1) != 0ull)
+                                passes(hmask0, hmask1, std::integral_constant<int, 2>{});
                         }
                         if (i % kChunkIters == kChunkIters - 1 || i == iters - 1) {
                             tc_commit(smem_u32(&bar_accf[ccount & 1]));
@@ -948,6 +1026,7 @@ static bool fill_batch(spamm_ctx* ctx, const LeafJob* jobs, int count, TcBatch& 
         q.steps = jb.sub->tile_steps;
         q.iters = jb.sub->tile_iters;
         q.gmax = jb.sub->need + 2 * jb.A->nb;
+        q.tier = ctx->cfg.tier_bits > 0 ? 1 : 0;
         if (jb.A->sparse) {
             const BandView v = band_view(jb.A);
             q.a_lo = v.imin;

@@ -128,7 +128,8 @@ spamm_status check_matrix(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda
 }
 
 // Pool words a multiply needs: the frontiers of tiers 0..tt, then one u32
-// entry per tier-tt triple and S steps (u32 K + two u64 masks) per entry.
+// entry per tier-tt triple and S steps (u32 K + SL pairs of u64 masks) per
+// entry.
 int64_t words_needed(const DevCtl& c, int tt, int S, int SL) {
     unsigned long long s = 0;
     for (int t = 0; t <= tt; ++t) s += c.tier_count[t];
@@ -139,6 +140,24 @@ int64_t words_needed(const DevCtl& c, int tt, int S, int SL) {
 
 // Mask pairs per step: one, or one per 16-wide k-slice with the sub-leaf cull.
 int slices_of(const spamm_ctx* ctx, int b) { return ctx->cfg.slice ? b / 16 : 1; }
+
+// Pool mask pairs per step: the kept masks, and with the precision tier the
+// full-split masks.
+int mask_pairs_of(const spamm_ctx* ctx, int b) {
+    return slices_of(ctx, b) + (ctx->cfg.tier_bits > 0 ? 1 : 0);
+}
+
+bool split_precision(int p) {
+    return p == SPAMM_PREC_TF32X3 || p == SPAMM_PREC_BF16X3 || p == SPAMM_PREC_F16X3;
+}
+
+// Stats fields of one product from its control block.
+void fill_tier_stats(const spamm_ctx* ctx, const DevCtl& c, int64_t leaf_triples,
+                     spamm_stats_t* out) {
+    out->hi_products = ctx->cfg.tier_bits > 0 ? (int64_t)c.hi_products : leaf_triples;
+    out->tie_band_hi = (int64_t)c.tie_hi;
+    out->kept_flops_clipped = 2.0 * (double)c.clip_vol;
+}
 
 }  // namespace
 
@@ -162,8 +181,10 @@ spamm_status spamm_create(spamm_ctx** out, void* stream, const spamm_config* cfg
     if (!valid_leaf(c.leaf)) return SPAMM_ERR_INVALID_ARG;
     if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_F16X3) return SPAMM_ERR_INVALID_ARG;
     if (!(c.tie_rel >= 0.0 && c.tie_rel < 0.5) || c.pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (c.reserved[i]) return SPAMM_ERR_INVALID_ARG;
+    if (c.tier_bits < 0 || c.tier_bits > 40) return SPAMM_ERR_INVALID_ARG;
+    if (c.tier_bits && !split_precision(c.precision)) return SPAMM_ERR_INVALID_ARG;
     if (c.slice != 0 && c.slice != 16) return SPAMM_ERR_INVALID_ARG;
     if (c.slice && (!precision_uses_tc(c.precision) || c.leaf < 32)) return SPAMM_ERR_UNSUPPORTED;
     spamm_ctx* ctx = new (std::nothrow) spamm_ctx();
@@ -615,7 +636,7 @@ spamm_status spamm_multiply(spamm_ctx* ctx, const spamm_tree* A, const spamm_tre
         if (e != cudaSuccess) return (spamm_status)(ctx->last_status = cuda_err(ctx, e, "multiply"));
         const DevCtl& c = *ctx->ctl_host;
         if ((c.status & ST_OVERFLOW) && !(c.status & (ST_NONFINITE | ST_TIMEOUT)) && attempt < 8) {
-            const int64_t need = std::max<int64_t>(words_needed(c, ctx->last_tt, ctx->last_S, slices_of(ctx, ctx->last_b)),
+            const int64_t need = std::max<int64_t>(words_needed(c, ctx->last_tt, ctx->last_S, mask_pairs_of(ctx, ctx->last_b)),
                                                    2 * ctx->pool_words);
             st = alloc_pool(ctx, need * 8 + need * 2);  // 25% headroom
             if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
@@ -656,9 +677,10 @@ spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     out->packed_leaves_a = (int64_t)c.packed_a;
     out->packed_leaves_b = (int64_t)c.packed_b;
     if (ctx->cfg.slice) out->kept_flops = 2.0 * b * b * ctx->cfg.slice * (double)c.slice_kept;
+    fill_tier_stats(ctx, c, out->leaf_triples, out);
     out->dense_flops = 2.0 * (double)ctx->last_n * (double)ctx->last_n * (double)ctx->last_n;
     out->pool_bytes = ctx->pool_words * 8;
-    out->pool_needed_bytes = words_needed(c, ctx->last_tt, ctx->last_S, slices_of(ctx, ctx->last_b)) * 8;
+    out->pool_needed_bytes = words_needed(c, ctx->last_tt, ctx->last_S, mask_pairs_of(ctx, ctx->last_b)) * 8;
     if (ctx->timed) {
         cudaEventElapsedTime(&out->ms_symbolic, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&out->ms_pack, ctx->ev[1], ctx->ev[3]);
@@ -671,7 +693,11 @@ spamm_status spamm_stats(spamm_ctx* ctx, spamm_stats_t* out) {
     return st;
 }
 
-spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64_t* count) {
+// spamm_triples and spamm_triples_hi: the tile-compressed steps expanded
+// into (I, K, J) rows, all kept triples or (hi, with the precision tier) the
+// full-split ones.
+static spamm_status expand_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap,
+                                   int64_t* count, bool hi) {
     if (!ctx || !count || cap < 0 || (cap > 0 && !host_out)) return SPAMM_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "triples");
@@ -681,12 +707,13 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     const int d = ctx->last_d;
     const int64_t m = (int64_t)c.tier_count[d];
     const int SL = slices_of(ctx, ctx->last_b);
-    *count = m;
+    const bool tier = hi && ctx->cfg.tier_bits > 0;
+    *count = tier ? (int64_t)c.hi_products : m;
     if (c.status & (ST_OVERFLOW | ST_NONFINITE)) {
         *count = 0;
         return status_from_ctl_pub(ctx, c);
     }
-    if ((cap <= 0 && SL == 1) || m == 0) return SPAMM_OK;
+    if ((cap <= 0 && SL == 1) || *count == 0) return SPAMM_OK;
     // expand the tile-compressed steps (K, mask) into (I, K, J) rows; with the
     // sub-leaf cull, a leaf triple is listed if any of its k-slices is kept
     // (the count is then exact only after the expansion)
@@ -705,6 +732,10 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     if (e == cudaSuccess && msteps)
         e = cudaMemcpy(pm.data(), ctx->pool + c.pm_off, sizeof(uint64_t) * 2 * msteps * SL,
                        cudaMemcpyDeviceToHost);
+    std::vector<uint64_t> ph(tier ? (size_t)(2 * msteps) : 0);
+    if (e == cudaSuccess && msteps && tier)
+        e = cudaMemcpy(ph.data(), ctx->pool + c.ph_off, sizeof(uint64_t) * 2 * msteps,
+                       cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(ctx, e, "triples copy");
     int64_t k = 0;
     for (int64_t u = 0; u < tiles; ++u) {
@@ -713,6 +744,7 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
             for (int h = 0; h < kTileHalves; ++h) {
                 uint64_t mk = 0;
                 for (int sl = 0; sl < SL; ++sl) mk |= pm[2 * ((base + q) * SL + sl) + h];
+                if (tier) mk &= ph[2 * (base + q) + h];
                 while (mk) {
                     const int bit = __builtin_ctzll(mk);
                     mk &= mk - 1;
@@ -729,6 +761,14 @@ spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64
     }
     *count = k;
     return SPAMM_OK;
+}
+
+spamm_status spamm_triples(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64_t* count) {
+    return expand_triples(ctx, host_out, cap, count, false);
+}
+
+spamm_status spamm_triples_hi(spamm_ctx* ctx, int32_t* host_out, int64_t cap, int64_t* count) {
+    return expand_triples(ctx, host_out, cap, count, true);
 }
 
 spamm_status spamm_cull_flat(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
@@ -1002,7 +1042,7 @@ spamm_status spamm_multiply_batched(spamm_ctx* ctx, int32_t count, const spamm_t
             if (c.status & (ST_NONFINITE | ST_TIMEOUT))
                 return (spamm_status)(ctx->last_status = status_of(ctx, c));
             if (c.status & ST_OVERFLOW) {
-                const int64_t need = std::max<int64_t>(words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)),
+                const int64_t need = std::max<int64_t>(words_needed(c, sub->last_tt, sub->last_S, mask_pairs_of(sub, sub->last_b)),
                                                        2 * sub->pool_words);
                 const spamm_status st = alloc_pool(sub, need * 8 + need * 2);
                 if (st != SPAMM_OK) return (spamm_status)(ctx->last_status = st);
@@ -1048,9 +1088,10 @@ spamm_status spamm_stats_item(spamm_ctx* ctx, int32_t index, spamm_stats_t* out)
     out->packed_leaves_a = (int64_t)c.packed_a;
     out->packed_leaves_b = (int64_t)c.packed_b;
     if (sub->cfg.slice) out->kept_flops = 2.0 * b * b * sub->cfg.slice * (double)c.slice_kept;
+    fill_tier_stats(sub, c, out->leaf_triples, out);
     out->dense_flops = 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
     out->pool_bytes = sub->pool_words * 8;
-    out->pool_needed_bytes = words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)) * 8;
+    out->pool_needed_bytes = words_needed(c, sub->last_tt, sub->last_S, mask_pairs_of(sub, sub->last_b)) * 8;
     out->status = status_of(ctx, c);
     return (spamm_status)out->status;
 }
@@ -1081,9 +1122,14 @@ static spamm_status batch_stats(spamm_ctx* ctx, spamm_stats_t* out) {
         out->slice_tested += (int64_t)c.slice_tested;
         out->packed_leaves_a += (int64_t)c.packed_a;
         out->packed_leaves_b += (int64_t)c.packed_b;
+        spamm_stats_t one{};
+        fill_tier_stats(sub, c, m, &one);
+        out->hi_products += one.hi_products;
+        out->tie_band_hi += one.tie_band_hi;
+        out->kept_flops_clipped += one.kept_flops_clipped;
         out->dense_flops += 2.0 * (double)sub->last_n * (double)sub->last_n * (double)sub->last_n;
         out->pool_bytes += sub->pool_words * 8;
-        out->pool_needed_bytes += words_needed(c, sub->last_tt, sub->last_S, slices_of(sub, sub->last_b)) * 8;
+        out->pool_needed_bytes += words_needed(c, sub->last_tt, sub->last_S, mask_pairs_of(sub, sub->last_b)) * 8;
         const spamm_status st = status_of(ctx, c);
         if (worst == SPAMM_OK) worst = st;
     }

@@ -53,6 +53,12 @@ struct DevCtl {
     unsigned long long slice_tested;
     unsigned long long packed_a;    // leaves packed in the A role (needed by a kept product)
     unsigned long long packed_b;    // leaves packed in the B role
+    unsigned long long ph_off;      // two u64 masks of each step: products that keep the
+                                    // full split precision (precision chosen by norm)
+    unsigned long long hi_products; // kept leaf products at or above tau_h
+    unsigned long long tie_hi;      // kept leaf products in the tie band around tau_h
+    unsigned long long clip_vol;    // sum over kept products of rows x k x columns inside
+                                    // the n x n matrices
     unsigned int status;
     unsigned int pad;
 };

@@ -70,3 +70,27 @@ def blocks_from(C, ij, b, n):
         blk = np.asarray(C[I * b:min(n, (I + 1) * b), J * b:min(n, (J + 1) * b)], dtype=np.float64)
         out[q, :blk.shape[0], :blk.shape[1]] = blk
     return out
+
+
+def _keys(tr) -> np.ndarray:
+    t = np.asarray(tr, dtype=np.int64).reshape(-1, 3)
+    return np.unique((t[:, 0] << 42) | (t[:, 1] << 21) | t[:, 2])
+
+
+def compare_triples_large(gpu, orc, pyrA, pyrB, d, tau, rel=1e-6):
+    """compare_triples for millions of triples: the two sets as sorted
+    integer keys, their symmetric difference checked against the tie band
+    with the oracle's leaf norms.  Returns the number of disagreeing
+    triples (all inside the band)."""
+    g, o = _keys(gpu), _keys(orc)
+    assert len(g) == len(np.asarray(gpu).reshape(-1, 3)), "duplicate GPU triples"
+    diff = np.setxor1d(g, o, assume_unique=True)
+    if diff.size == 0:
+        return 0
+    la = O.tier(pyrA, d)
+    lb = O.tier(pyrB, d)
+    I, K, J = diff >> 42, (diff >> 21) & ((1 << 21) - 1), diff & ((1 << 21) - 1)
+    p = la[I, K] * lb[K, J]
+    inside = (p > 0) & (np.abs(np.sqrt(p) - tau) <= rel * tau)
+    assert inside.all(), f"{int((~inside).sum())} triples differ outside the tie band"
+    return int(diff.size)

@@ -100,6 +100,21 @@ def test_slice_cull_config_is_validated_before_the_gpu(libpath):
         assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == want
 
 
+def test_tier_config_is_validated_before_the_gpu(libpath):
+    """Precision chosen by norm needs a split precision and 0 <= tier_bits
+    <= 40; invalid combinations are refused before any CUDA call."""
+    from paper_1203_1692_gb300 import _abi
+    L = _abi.lib()
+    h = ctypes.c_void_p()
+    for prec, bits in [(_abi.SPAMM_PREC_FP32, 10), (_abi.SPAMM_PREC_TF32, 10),
+                       (_abi.SPAMM_PREC_F16X3, -1), (_abi.SPAMM_PREC_F16X3, 41),
+                       (_abi.SPAMM_PREC_BF16X3, 1000)]:
+        c = _abi.spamm_config_default()
+        c.leaf, c.precision, c.tier_bits = 64, prec, bits
+        assert L.spamm_create(ctypes.byref(h), None, ctypes.byref(c)) == \
+            _abi.SPAMM_ERR_INVALID_ARG
+
+
 def test_ctypes_structs_match_the_header(tmp_path):
     """The binding's spamm_config and spamm_stats_t have the C layout: every
     field at the offset gcc gives it from include/spamm.h, and the same size

@@ -44,8 +44,8 @@ def _single(P, prec, case):
     return C.cpu().numpy(), ctx.stats()["leaf_triples"]
 
 
-def _batched(P, prec, cases, ctx=None):
-    ctx = ctx or P.Context(leaf=16, precision=prec)
+def _batched(P, prec, cases, ctx=None, leaf=16, slice=0):
+    ctx = ctx or P.Context(leaf=leaf, precision=prec, slice=slice)
     keep = []
     As, Bs, Cs = [], [], []
     for A, B, tau, alpha, beta, C0 in cases:
@@ -81,6 +81,26 @@ def test_batched_matches_oracle(prec):
     for (A, B, tau, alpha, beta, C0), C in zip(cases, got):
         ref = oracle.multiply(A, B, 16, tau, alpha=alpha, beta=beta, C=C0)
         assert rel_max_err(C, ref.C) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,leaf", [("f16x3", 64), ("f16x3", 128), ("tf32x3", 64),
+                                       ("bf16x3", 128)])
+def test_batched_slice_cull_matches_oracle(prec, leaf):
+    """The configuration the batch-of-64 workload runs (leaf 64 or 128, the
+    sub-leaf cull along k in slices of 16): every product of a mixed batch
+    against the oracle's sliced product (reading R14 of the SpAMM(4x4)
+    cull), with its kept slice count."""
+    import paper_1203_1692_gb300 as P
+    cases = _mix(seed=4)
+    got, ctx = _batched(P, prec, cases, leaf=leaf, slice=16)
+    for p, ((A, B, tau, alpha, beta, C0), C) in enumerate(zip(cases, got)):
+        refC, m, kept, _ = oracle.multiply_sliced(A, B, leaf, 16, tau, alpha=alpha, beta=beta,
+                                                  C=C0)
+        assert rel_max_err(C, refC) <= TOL[prec]
+        st = ctx.stats_item(p)
+        if st["tie_band"] == 0:
+            assert st["leaf_triples"] == m
+            assert st["slice_kept"] == kept
 
 
 def test_batched_more_than_one_launch_and_reuse():

@@ -15,6 +15,8 @@ import numpy as np
 import pytest
 
 import spamm_inputs as gen
+from oracle import oracle as O
+from tests.spamm_check import blocks_from, sample_blocks
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -108,3 +110,55 @@ def test_static_accepts_its_maximum_and_rejects_beyond():
     assert st == _abi.SPAMM_ERR_UNSUPPORTED
     st = L.spamm_multiply_static(p, 4, p, 4, 8, 1e-6, 1.0, 0.0, p, 8, None, None)
     assert st == _abi.SPAMM_ERR_INVALID_ARG
+
+
+def test_static_matches_oracle():
+    """The allocation-free product against the FP64 oracle directly (Eqs.
+    (product), (norm_condition), Algorithm 1), with alpha and beta."""
+    n, tau, alpha, beta = 900, 1e-5, 0.75, -1.5
+    A = gen.exp_decay_nonsym(n, 0.85, seed=11)
+    B = gen.exp_decay(n, 0.9, seed=12)
+    C0 = gen.uniform_dense(n, seed=13, symmetric=False)
+    ref = O.multiply(A, B, 16, tau, alpha=alpha, beta=beta, C=C0)
+    got, status = _static(A, B, tau, alpha, beta, C0)
+    assert status == 0
+    assert _rel(got, ref.C) <= TOL
+
+
+def test_static_worst_case_at_its_maximum():
+    """n = 4096 at tau = 0 on a dense matrix: every block product is kept,
+    which is the case the static scratch is sized for (full frontiers at
+    every tier, every tile with all its steps).  Sampled C blocks against
+    the oracle, the whole C against the regular entry point, and the
+    regular entry point's kept count against the oracle's (all (n/16)^3)."""
+    import paper_1203_1692_gb300 as P
+    n, b, tau = 4096, 16, 0.0
+    A = gen.uniform_dense(n, seed=21, symmetric=False)
+    B = gen.uniform_dense(n, seed=22, symmetric=False)
+    C0 = np.zeros((n, n), dtype=np.float32)
+    got, status = _static(A, B, tau, 1.0, 0.0, C0)
+    assert status == 0
+    ij = sample_blocks(n, b, 24)
+    ref, kept = O.blocks(A, B, b, tau, ij)
+    assert kept == len(ij) * (n // b)
+    blk = blocks_from(got, ij, b, n)
+    assert float(np.abs(blk - ref).max() / np.abs(ref).max()) <= TOL
+    ctx = P.Context(leaf=b, precision="fp32")
+    ta = ctx.build_norms(torch.from_numpy(A).cuda())
+    tb = ctx.build_norms(torch.from_numpy(B).cuda())
+    C = ctx.multiply(ta, tb, tau)
+    torch.cuda.synchronize()
+    assert ctx.stats()["leaf_triples"] == (n // b) ** 3
+    assert _rel(got, C.cpu().numpy()) <= TOL
+
+
+def test_static_non_finite_input_reports_status_and_leaves_C():
+    """A NaN in A: the device status word reads 2 (non-finite input) and C
+    is left as it was."""
+    n = 300
+    A = gen.exp_decay(n, 0.9, seed=31)
+    A[17, 123] = np.nan
+    C0 = gen.uniform_dense(n, seed=32, symmetric=False)
+    got, status = _static(A, A, 1e-6, 1.0, 0.5, C0)
+    assert status == 2
+    assert np.array_equal(got, C0)
