@@ -8,9 +8,11 @@
 // tile needs A's 128 x 16 slice (its row leaves at column leaf K) and B's
 // 16 x 256 slice, hi and lo parts; the packs hold them already in the
 // no-swizzle K-major layout of tcgen05 (8-row x 16-byte core matrices),
-// grouped so that all chunks and parts a tile reads from one operand at one
-// K are a single contiguous run.  One 1-D bulk copy per operand moves a run
-// of K-chunks into shared memory: at b = 64 one step is two copies.  The
+// grouped so that the chunks a tile reads from one operand at one K are
+// contiguous runs of pack groups (CG chunks: their high parts, then their
+// low parts).  One 1-D bulk copy per operand moves a group into shared
+// memory: at b = 64 one step is two copies, with both parts or with the
+// high parts alone.  The
 // copies, not their bytes, set the pace of the producer (each costs on the
 // order of fifty cycles to issue and complete), so fewer and larger copies
 // are what keeps the tensor pipe fed.  A 256-wide tile halves the MMA
@@ -31,7 +33,10 @@
 // BF16X3 does the same with bfloat16 parts on kind::f16; F16X3 with fp16
 // parts of each operand scaled by a power of two (its largest leaf norm
 // just below 2^15), the product scaled back exactly in the epilogue.  All
-// accumulate in FP32.
+// accumulate in FP32.  With precision chosen by norm, each step also carries
+// the masks of its products whose norm product reaches tau_h: those get all
+// three passes, the other kept products hi*hi alone, and a step without any
+// such product loads only the high parts of its operands.
 //
 // Two-level accumulation: the tensor core's FP32 accumulation rounds less
 // carefully than an IEEE add, and a C tile can chain thousands of MMAs.  So
@@ -301,6 +306,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     constexpr int TLC = 2 * TL;         // column leaves of the tile
     constexpr int CHUNKS = LEAF / 16;
     constexpr int ST = T::kStages;
+    // K-chunks per pack group (the packs store a group's high parts before
+    // its low parts); a stage holds whole groups
+    constexpr int CG = CHUNKS < T::kSPS ? CHUNKS : T::kSPS;
+    static_assert(CG == pack_group_chunks(LEAF, PREC), "pack group and stage disagree");
+    static_assert(T::kSPS % CG == 0, "a stage holds whole pack groups");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2],
         bar_drain;
@@ -402,9 +412,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const uint64_t sb = (uint64_t)q.off[u] * q.S;
             // lane 0: m consecutive K-chunks kc0.. of the step at K into slots
             // fill.. of the current stage (m <= kSPS - fill).  A stage keeps the
-            // A parts of its slots together, then the B parts, and the dense
-            // packs keep a tile's chunks of one K together in the same order,
-            // so the run is one bulk copy per operand.
+            // A parts of its slots together, then the B parts, each in groups
+            // of CG slots (high parts, then low parts), and the dense packs
+            // keep a tile's chunks of one K in the same groups, so a whole
+            // group is one bulk copy per operand, and so are its high parts
+            // alone.
             const int64_t ga = srow / TL, gb = scol / TLC;          // tile's pack groups
             int64_t bandK = -1;
             int64_t a_lo = 0, a_hi = -1, a_off = 0, b_lo = 0, b_hi = -1, b_off = 0;
@@ -421,12 +433,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 if (!ok) return;
                 const uint32_t full = smem_u32(&bar_full[s]);
                 unsigned char* const stg = stages + (size_t)s * T::kStage;
-                unsigned char* const sa_dst = stg + (size_t)fill * T::kASlot;
-                unsigned char* const sb_dst =
-                    stg + (size_t)T::kSPS * T::kASlot + (size_t)fill * T::kBSlot;
-                // dense operand: its run of m chunks, all parts
-                const size_t a_src = ((size_t)(K * (q.nlp / TL) + ga) * CHUNKS + kc0) * T::kASlot;
-                const size_t b_src = ((size_t)(K * (q.nlp / TLC) + gb) * CHUNKS + kc0) * T::kBSlot;
+                // shared memory of slot `slot`, part `part` (groups of CG
+                // slots: the high parts of the group, then its low parts)
+                auto a_dst = [&](int slot, int part) {
+                    return stg + (size_t)(slot / CG) * CG * T::kASlot +
+                           (size_t)part * CG * T::kSlice + (size_t)(slot % CG) * T::kSlice;
+                };
+                auto b_dst = [&](int slot, int part) {
+                    return stg + (size_t)T::kSPS * T::kASlot + (size_t)(slot / CG) * CG * T::kBSlot +
+                           (size_t)part * CG * 2 * T::kSlice + (size_t)(slot % CG) * 2 * T::kSlice;
+                };
+                // dense operand: the pack group holding chunk kc0, and chunk
+                // kc0 + j's part inside it
+                const int c0 = kc0 % CG;
+                const size_t a_grp =
+                    ((size_t)(K * (q.nlp / TL) + ga) * CHUNKS + (kc0 - c0)) * T::kASlot;
+                const size_t b_grp =
+                    ((size_t)(K * (q.nlp / TLC) + gb) * CHUNKS + (kc0 - c0)) * T::kBSlot;
+                const unsigned char* const pa0 = static_cast<const unsigned char*>(q.pa[0]);
+                const unsigned char* const pb0 = static_cast<const unsigned char*>(q.pb[0]);
+                auto a_src = [&](int j, int part) {
+                    return pa0 + a_grp + (size_t)part * CG * T::kSlice + (size_t)(c0 + j) * T::kSlice;
+                };
+                auto b_src = [&](int j, int part) {
+                    return pb0 + b_grp + (size_t)part * CG * 2 * T::kSlice +
+                           (size_t)(c0 + j) * 2 * T::kSlice;
+                };
+                const int parts = lean ? 1 : T::kParts;
                 if constexpr (BAND) {
                     // m == 1 here: a sparsified operand's chunk comes from
                     // inside its band, one copy per part
@@ -451,9 +484,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         na = hi >= lo ? hi - lo + 1 : 0;
                         sa = a_off + kc0 * (a_hi - a_lo + 1) + (lo - a_lo);
                         da = lo - srow;
-                        bytes += (uint32_t)((lean ? 1 : T::kParts) * na * piece);
+                        bytes += (uint32_t)(parts * na * piece);
                     } else {
-                        bytes += (uint32_t)(lean ? T::kSlice : T::kASlot);
+                        bytes += (uint32_t)(parts * T::kSlice);
                     }
                     int64_t sb2 = 0, nb2 = TLC, db = 0;
                     if (q.b_lo) {
@@ -462,64 +495,60 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         nb2 = hi >= lo ? hi - lo + 1 : 0;
                         sb2 = b_off + kc0 * (b_hi - b_lo + 1) + (lo - b_lo);
                         db = lo - scol;
-                        bytes += (uint32_t)((lean ? 1 : T::kParts) * nb2 * piece);
+                        bytes += (uint32_t)(parts * nb2 * piece);
                     } else {
-                        bytes += (uint32_t)(lean ? 2 * T::kSlice : T::kBSlot);
+                        bytes += (uint32_t)(parts * 2 * T::kSlice);
                     }
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
                                  "r"(bytes)
                                  : "memory");
-                    const int parts = lean ? 1 : T::kParts;
-                    if (q.a_lo) {
 #pragma unroll
-                        for (int part = 0; part < T::kParts; ++part)
-                            if (na && part < parts)
-                                bulk_g2s(smem_u32(sa_dst + part * T::kSlice + da * piece),
+                    for (int part = 0; part < T::kParts; ++part) {
+                        if (part >= parts) break;
+                        if (q.a_lo) {
+                            if (na)
+                                bulk_g2s(smem_u32(a_dst(fill, part) + da * piece),
                                          static_cast<const unsigned char*>(q.pa[part]) +
                                              (size_t)sa * piece,
                                          (uint32_t)(na * piece), full);
-                    } else {
-                        bulk_g2s(smem_u32(sa_dst),
-                                 static_cast<const unsigned char*>(q.pa[0]) + a_src,
-                                 (uint32_t)(lean ? T::kSlice : T::kASlot), full);
-                    }
-                    if (q.b_lo) {
-#pragma unroll
-                        for (int part = 0; part < T::kParts; ++part)
-                            if (nb2 && part < parts)
-                                bulk_g2s(smem_u32(sb_dst + 2 * part * T::kSlice + db * piece),
+                        } else {
+                            bulk_g2s(smem_u32(a_dst(fill, part)), a_src(0, part),
+                                     (uint32_t)T::kSlice, full);
+                        }
+                        if (q.b_lo) {
+                            if (nb2)
+                                bulk_g2s(smem_u32(b_dst(fill, part) + db * piece),
                                          static_cast<const unsigned char*>(q.pb[part]) +
                                              (size_t)sb2 * piece,
                                          (uint32_t)(nb2 * piece), full);
-                    } else {
-                        bulk_g2s(smem_u32(sb_dst),
-                                 static_cast<const unsigned char*>(q.pb[0]) + b_src,
-                                 (uint32_t)(lean ? 2 * T::kSlice : T::kBSlot), full);
+                        } else {
+                            bulk_g2s(smem_u32(b_dst(fill, part)), b_src(0, part),
+                                     (uint32_t)(2 * T::kSlice), full);
+                        }
                     }
-                } else if (lean) {
-                    // the high part of each chunk: the first kSlice (A) and
-                    // 2 kSlice (B) bytes of its slot, one copy each
+                } else if (m == CG && c0 == 0 && fill % CG == 0) {
+                    // a whole pack group: one copy per operand, all parts
+                    // (or the high parts alone)
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                 "r"((uint32_t)(m * 3 * T::kSlice))
+                                 "r"((uint32_t)(parts * m * 3 * T::kSlice))
                                  : "memory");
-                    for (int j = 0; j < m; ++j) {
-                        bulk_g2s(smem_u32(sa_dst + (size_t)j * T::kASlot),
-                                 static_cast<const unsigned char*>(q.pa[0]) + a_src +
-                                     (size_t)j * T::kASlot,
-                                 (uint32_t)T::kSlice, full);
-                        bulk_g2s(smem_u32(sb_dst + (size_t)j * T::kBSlot),
-                                 static_cast<const unsigned char*>(q.pb[0]) + b_src +
-                                     (size_t)j * T::kBSlot,
-                                 (uint32_t)(2 * T::kSlice), full);
-                    }
+                    bulk_g2s(smem_u32(a_dst(fill, 0)), a_src(0, 0),
+                             (uint32_t)(parts * m * T::kSlice), full);
+                    bulk_g2s(smem_u32(b_dst(fill, 0)), b_src(0, 0),
+                             (uint32_t)(parts * m * 2 * T::kSlice), full);
                 } else {
+                    // single chunks of a group (the sub-leaf cull): one copy
+                    // per operand and part
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                 "r"((uint32_t)(m * T::kIter))
+                                 "r"((uint32_t)(parts * m * 3 * T::kSlice))
                                  : "memory");
-                    bulk_g2s(smem_u32(sa_dst), static_cast<const unsigned char*>(q.pa[0]) + a_src,
-                             (uint32_t)(m * T::kASlot), full);
-                    bulk_g2s(smem_u32(sb_dst), static_cast<const unsigned char*>(q.pb[0]) + b_src,
-                             (uint32_t)(m * T::kBSlot), full);
+                    for (int j = 0; j < m; ++j)
+                        for (int part = 0; part < parts; ++part) {
+                            bulk_g2s(smem_u32(a_dst(fill + j, part)), a_src(j, part),
+                                     (uint32_t)T::kSlice, full);
+                            bulk_g2s(smem_u32(b_dst(fill + j, part)), b_src(j, part),
+                                     (uint32_t)(2 * T::kSlice), full);
+                        }
                 }
                 for (int j = 0; j < m; ++j) {
                     st_mask[s][fill + j][0] = m0;
@@ -678,156 +707,191 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         hk1[jj] = st_hmask[s][jj][1];
                     }
                     const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
+                    constexpr unsigned long long kRep =
+                        TL == 8   ? 0x0101010101010101ull
+                        : TL == 4 ? 0x0000000001010101ull
+                        : TL == 2 ? 0x0000000000000101ull
+                                  : 0x0000000000000001ull;
+                    constexpr unsigned long long kFull =
+                        (unsigned long long)((1u << TL) - 1u) * kRep;
+                    // The MMAs of one pass set over the products of masks (r0,
+                    // r1), for the slots [j0, j1) of the stage: MODE 3 = all
+                    // three of the split (lo*hi, hi*lo, hi*hi; hi*hi alone for
+                    // single TF32), 1 = hi*hi, 2 = the cross terms.  Runs of
+                    // column leaves with the same kept row leaves: a column y
+                    // starts a run when its row mask is non-zero and differs
+                    // from column y-1's.  Uniform halves (the common case on
+                    // dense blocks) give one run directly.  Slot jj sits in its
+                    // group of CG slots, high parts first, then low parts.
+                    auto passes = [&](unsigned long long r0, unsigned long long r1, auto mode_c,
+                                      int j0, int j1) {
+                        constexpr int MODE = decltype(mode_c)::value;
+                        constexpr bool kCross = PREC != SPAMM_PREC_TF32 && MODE != 1;
+                        constexpr bool kHiHi = MODE != 2;
+                        // the MMAs of slot jj over one run: N = nn, TMEM
+                        // columns from d, B rows from boff, lane mask dis
+                        auto slot_mmas = [&](int jj, uint32_t d, uint32_t boff, uint32_t idesc,
+                                             const uint32_t (&dis)[4], bool masked) {
+                            const uint32_t a_hi = sbuf + (uint32_t)((jj / CG) * CG * T::kASlot +
+                                                                    (jj % CG) * T::kSlice);
+                            const uint32_t a_lo = a_hi + (uint32_t)(CG * T::kSlice);
+                            const uint32_t b_hi =
+                                sbuf + (uint32_t)(T::kSPS * T::kASlot + (jj / CG) * CG * T::kBSlot +
+                                                  (jj % CG) * 2 * T::kSlice) + boff;
+                            const uint32_t b_lo = b_hi + (uint32_t)(CG * 2 * T::kSlice);
 #pragma unroll
-                    for (int jj = 0; jj < T::kSPS; ++jj) {
-                        if ((uint32_t)jj >= cnt || !ok) break;
-                        if (i % kChunkIters == 0) {
-                            const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
-                            if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status)) {
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                            dacc = tmem + ab * 256;
-                            // clear the chunk accumulator: 0 * 0, input accumulator off
-                            mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256), dis0, 0u);
-                        }
-                        const unsigned long long mask0 = mk0[jj];
-                        const unsigned long long mask1 = mk1[jj];
-                        const uint32_t a_hi = sbuf + jj * (uint32_t)T::kASlot;
-                        const uint32_t a_lo = a_hi + T::kSlice;
-                        const uint32_t b_hi =
-                            sbuf + (uint32_t)(T::kSPS * T::kASlot) + jj * (uint32_t)T::kBSlot;
-                        const uint32_t b_lo = b_hi + 2 * T::kSlice;
-                        constexpr unsigned long long kRep =
-                            TL == 8   ? 0x0101010101010101ull
-                            : TL == 4 ? 0x0000000001010101ull
-                            : TL == 2 ? 0x0000000000000101ull
-                                      : 0x0000000000000001ull;
-                        constexpr unsigned long long kFull =
-                            (unsigned long long)((1u << TL) - 1u) * kRep;
-                        uint64_t ah[2], al[2];
-#pragma unroll
-                        for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                            ah[kk] = make_desc(a_hi + (uint32_t)kk * 256u, 128, T::kSBO);
-                            al[kk] = make_desc(a_lo + (uint32_t)kk * 256u, 128, T::kSBO);
-                        }
-                        // The MMAs of one pass set over the products of masks
-                        // (r0, r1): MODE 3 = all three of the split (lo*hi,
-                        // hi*lo, hi*hi; hi*hi alone for single TF32), 1 = hi*hi,
-                        // 2 = the cross terms.  Runs of column leaves with the
-                        // same kept row leaves: a column y starts a run when its
-                        // row mask is non-zero and differs from column y-1's.
-                        // Uniform halves (the common case on dense blocks) give
-                        // one run directly.
-                        auto passes = [&](unsigned long long r0, unsigned long long r1,
-                                          auto mode_c) {
-                            constexpr int MODE = decltype(mode_c)::value;
-                            constexpr bool kCross = PREC != SPAMM_PREC_TF32 && MODE != 1;
-                            constexpr bool kHiHi = MODE != 2;
-                            if (r0 == kFull && r1 == kFull) {
-                                // every product of the step: one 128 x 256 MMA per
-                                // pass, no masks
-                                constexpr uint32_t idesc_full = make_idesc(T::kAB, 128, 256);
-#pragma unroll
-                                for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                    const uint32_t koff = (uint32_t)kk * 256u;
-                                    const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
-                                    if (kCross) {
-                                        const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
-                                        mma_all<PREC>(dacc, al[kk], bh, idesc_full, 1u);
-                                        mma_all<PREC>(dacc, ah[kk], bl, idesc_full, 1u);
-                                    }
-                                    if (kHiHi) mma_all<PREC>(dacc, ah[kk], bh, idesc_full, 1u);
-                                }
-                                return;
-                            }
-                            const uint32_t x0 = (uint32_t)r0 & 0xFFu;
-                            const uint32_t x1 = (uint32_t)r1 & 0xFFu;
-                            const bool u0 = r0 == (unsigned long long)x0 * kRep;
-                            const bool u1 = r1 == (unsigned long long)x1 * kRep;
-                            uint32_t starts, nz;
-                            if (u0 && u1) {
-                                starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
-                                nz = (x0 ? (1u << TL) - 1u : 0u) |
-                                     (x1 ? ((1u << TL) - 1u) << TL : 0u);
-                            } else {
-                                starts = 0u;
-                                nz = 0u;
-                                uint32_t prev = 0u;
-#pragma unroll
-                                for (int yy = 0; yy < TLC; ++yy) {
-                                    const uint32_t xm =
-                                        yy < TL ? (uint32_t)(r0 >> (8 * yy)) & 0xFFu
-                                                : (uint32_t)(r1 >> (8 * (yy - TL))) & 0xFFu;
-                                    if (xm) nz |= 1u << yy;
-                                    if (xm && xm != prev) starts |= 1u << yy;
-                                    prev = xm;
-                                }
-                            }
-                            while (starts) {
-                                const int y = __ffs(starts) - 1;
-                                starts &= starts - 1;
-                                const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
-                                const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
-                                const int len = yend - y;
-                                const uint32_t xm =
-                                    y < TL ? (uint32_t)(r0 >> (8 * y)) & 0xFFu
-                                           : (uint32_t)(r1 >> (8 * (y - TL))) & 0xFFu;
-                                // disable-output-lane bits: row r of the tile is
-                                // lane r, and a dropped row leaf x masks its b rows
-                                uint32_t dis[4];
-#pragma unroll
-                                for (int w = 0; w < 4; ++w) {
-                                    uint32_t v = 0;
-                                    if (LEAF <= 32) {
-#pragma unroll
-                                        for (int q = 0; q < 32 / LEAF; ++q) {
-                                            const int x = w * (32 / LEAF) + q;
-                                            if (!((xm >> x) & 1u))
-                                                v |= (LEAF == 32 ? 0xFFFFFFFFu
-                                                                 : (0xFFFFu << (16 * q)));
-                                        }
+                            for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                const uint32_t koff = (uint32_t)kk * 256u;
+                                const uint64_t ah = make_desc(a_hi + koff, 128, T::kSBO);
+                                const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
+                                if (kCross) {
+                                    const uint64_t al = make_desc(a_lo + koff, 128, T::kSBO);
+                                    const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
+                                    if (masked) {
+                                        mma<PREC>(d, al, bh, idesc, dis, 1u);
+                                        mma<PREC>(d, ah, bl, idesc, dis, 1u);
                                     } else {
-                                        const int x = (w * 32) / LEAF;
-                                        if (!((xm >> x) & 1u)) v = 0xFFFFFFFFu;
+                                        mma_all<PREC>(d, al, bh, idesc, 1u);
+                                        mma_all<PREC>(d, ah, bl, idesc, 1u);
                                     }
-                                    dis[w] = v;
                                 }
-                                const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
-                                const uint32_t d = dacc + (uint32_t)(y * LEAF);
-                                const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
-#pragma unroll
-                                for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                    const uint32_t koff = (uint32_t)kk * 256u;
-                                    const uint64_t bh =
-                                        make_desc(b_hi + boff + koff, 128, T::kSBO);
-                                    if (kCross) {
-                                        const uint64_t bl =
-                                            make_desc(b_lo + boff + koff, 128, T::kSBO);
-                                        mma<PREC>(d, al[kk], bh, idesc, dis, 1u);
-                                        mma<PREC>(d, ah[kk], bl, idesc, dis, 1u);
-                                    }
-                                    if (kHiHi) mma<PREC>(d, ah[kk], bh, idesc, dis, 1u);
+                                if (kHiHi) {
+                                    if (masked) mma<PREC>(d, ah, bh, idesc, dis, 1u);
+                                    else mma_all<PREC>(d, ah, bh, idesc, 1u);
                                 }
                             }
                         };
-                        const unsigned long long hmask0 = hk0[jj];
-                        const unsigned long long hmask1 = hk1[jj];
-                        if (hmask0 == mask0 && hmask1 == mask1) {
-                            passes(mask0, mask1, std::integral_constant<int, 3>{});
-                        } else {
-                            // precision chosen by norm: hi * hi for every kept
-                            // product, the cross terms for the full-split ones
-                            passes(mask0, mask1, std::integral_constant<int, 1>{});
-                            if ((hmask0 | hmask1) != 0ull)
-                                passes(hmask0, hmask1, std::integral_constant<int, 2>{});
+                        if (r0 == kFull && r1 == kFull) {
+                            // every product of the step: one 128 x 256 MMA per
+                            // pass, no masks
+                            constexpr uint32_t idesc_full = make_idesc(T::kAB, 128, 256);
+#pragma unroll
+                            for (int jj = 0; jj < T::kSPS; ++jj)
+                                if (jj >= j0 && jj < j1) slot_mmas(jj, dacc, 0u, idesc_full, dis0, false);
+                            return;
                         }
-                        if (i % kChunkIters == kChunkIters - 1 || i == iters - 1) {
+                        const uint32_t x0 = (uint32_t)r0 & 0xFFu;
+                        const uint32_t x1 = (uint32_t)r1 & 0xFFu;
+                        const bool u0 = r0 == (unsigned long long)x0 * kRep;
+                        const bool u1 = r1 == (unsigned long long)x1 * kRep;
+                        uint32_t starts, nz;
+                        if (u0 && u1) {
+                            starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
+                            nz = (x0 ? (1u << TL) - 1u : 0u) | (x1 ? ((1u << TL) - 1u) << TL : 0u);
+                        } else {
+                            starts = 0u;
+                            nz = 0u;
+                            uint32_t prev = 0u;
+#pragma unroll
+                            for (int yy = 0; yy < TLC; ++yy) {
+                                const uint32_t xm =
+                                    yy < TL ? (uint32_t)(r0 >> (8 * yy)) & 0xFFu
+                                            : (uint32_t)(r1 >> (8 * (yy - TL))) & 0xFFu;
+                                if (xm) nz |= 1u << yy;
+                                if (xm && xm != prev) starts |= 1u << yy;
+                                prev = xm;
+                            }
+                        }
+                        while (starts) {
+                            const int y = __ffs(starts) - 1;
+                            starts &= starts - 1;
+                            const uint32_t stop = (starts | ~nz) & ~((2u << y) - 1u);
+                            const int yend = stop ? min(__ffs(stop) - 1, TLC) : TLC;
+                            const int len = yend - y;
+                            const uint32_t xm = y < TL ? (uint32_t)(r0 >> (8 * y)) & 0xFFu
+                                                       : (uint32_t)(r1 >> (8 * (y - TL))) & 0xFFu;
+                            // disable-output-lane bits: row r of the tile is
+                            // lane r, and a dropped row leaf x masks its b rows
+                            uint32_t dis[4];
+#pragma unroll
+                            for (int w = 0; w < 4; ++w) {
+                                uint32_t v = 0;
+                                if (LEAF <= 32) {
+#pragma unroll
+                                    for (int q = 0; q < 32 / LEAF; ++q) {
+                                        const int x = w * (32 / LEAF) + q;
+                                        if (!((xm >> x) & 1u))
+                                            v |= (LEAF == 32 ? 0xFFFFFFFFu : (0xFFFFu << (16 * q)));
+                                    }
+                                } else {
+                                    const int x = (w * 32) / LEAF;
+                                    if (!((xm >> x) & 1u)) v = 0xFFFFFFFFu;
+                                }
+                                dis[w] = v;
+                            }
+                            const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
+                            const uint32_t d = dacc + (uint32_t)(y * LEAF);
+                            const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
+#pragma unroll
+                            for (int jj = 0; jj < T::kSPS; ++jj)
+                                if (jj >= j0 && jj < j1) slot_mmas(jj, d, boff, idesc, dis, true);
+                        }
+                    };
+                    // every pass set of slots [j0, j1) sharing the masks (m, h):
+                    // the full split where h == m; with precision chosen by
+                    // norm, hi * hi for every kept product and the cross terms
+                    // for the full-split ones
+                    auto pass_sets = [&](unsigned long long m0, unsigned long long m1,
+                                         unsigned long long h0, unsigned long long h1, int j0,
+                                         int j1) {
+                        if (h0 == m0 && h1 == m1) {
+                            passes(m0, m1, std::integral_constant<int, 3>{}, j0, j1);
+                        } else {
+                            passes(m0, m1, std::integral_constant<int, 1>{}, j0, j1);
+                            if ((h0 | h1) != 0ull)
+                                passes(h0, h1, std::integral_constant<int, 2>{}, j0, j1);
+                        }
+                    };
+                    // a new TMEM chunk at every kChunkIters-th K-chunk of a tile:
+                    // wait until the epilogue has drained the buffer, clear it
+                    auto open_chunk = [&]() -> bool {
+                        const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
+                        if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status))
+                            return false;
+                        tc_fence_after();
+                        dacc = tmem + ab * 256;
+                        // clear the chunk accumulator: 0 * 0, input accumulator off
+                        mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256), dis0, 0u);
+                        return true;
+                    };
+                    // the chunk's last K-chunk (or the tile's): hand it over
+                    auto close_chunk = [&](uint32_t last) {
+                        if (last % kChunkIters == kChunkIters - 1 || last == iters - 1) {
                             tc_commit(smem_u32(&bar_accf[ccount & 1]));
                             ++ccount;
                         }
-                        ++i;
+                    };
+                    // A stage starts at a multiple of kSPS K-chunks of its tile
+                    // and kSPS divides kChunkIters, so it never crosses a TMEM
+                    // chunk.  When all its slots carry the same masks (every
+                    // stage of a step with unculled chunks, and dense steps of
+                    // any leaf size), one run analysis serves them all.
+                    bool uni = true;
+#pragma unroll
+                    for (int jj = 1; jj < T::kSPS; ++jj)
+                        if ((uint32_t)jj < cnt)
+                            uni = uni && mk0[jj] == mk0[0] && mk1[jj] == mk1[0] &&
+                                  hk0[jj] == hk0[0] && hk1[jj] == hk1[0];
+                    if (uni) {
+                        if (i % kChunkIters == 0 && !open_chunk()) {
+                            ok = false;
+                        } else {
+                            pass_sets(mk0[0], mk1[0], hk0[0], hk1[0], 0, (int)cnt);
+                            i += cnt;
+                            close_chunk(i - 1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < T::kSPS; ++jj) {
+                            if ((uint32_t)jj >= cnt || !ok) break;
+                            if (i % kChunkIters == 0 && !open_chunk()) {
+                                ok = false;
+                                break;
+                            }
+                            pass_sets(mk0[jj], mk1[jj], hk0[jj], hk1[jj], jj, jj + 1);
+                            close_chunk(i);
+                            ++i;
+                        }
                     }
                     // the stage's MMAs have read its shared memory once they complete
                     tc_commit(smem_u32(&bar_empty[s]));

@@ -23,16 +23,20 @@
 // stored); the B role holds leaf (K, J) transposed, rows = j.  Pieces are
 // grouped the way one C tile reads them: a tile's rows are TL = 128 / b
 // consecutive leaves, its columns 2 TL, so with G the group size (TL for the
-// A role, 2 TL for the B role), P the parts (hi, lo) and CH = b / 16,
-//     piece(K, x, kc, part) at ((((K * nlp/G + x/G) * CH + kc) * P + part) * G
-//                               + x % G) * piece_bytes
+// A role, 2 TL for the B role), P the parts (hi, lo), CH = b / 16 and the
+// chunks of a leaf taken CG at a time (pack_group_chunks: the chunks one
+// stage of the leaf kernel holds), chunk kc = q CG + c,
+//     piece(K, x, kc, part) at (((((K * nlp/G + x/G) * CH/CG + q) * P + part)
+//                                 * CG + c) * G + x % G) * piece_bytes
 // (K = the shared index, x = the leaf's other index).  The G pieces of one
 // group, chunk and part form the 128 x 16 (A) or 256 x 16 (B) operand slice
-// of one MMA, the parts of a chunk follow each other, and the chunks of one
-// K follow each other: everything a tile needs from one operand at one K is
-// one contiguous run, which a single bulk copy moves into shared memory
-// already in the layout the MMA reads.  Sparsified trees keep their own
-// banded layout (one array per part, see k_leaf_pack).
+// of one MMA; the high parts of CG chunks come first, then their low parts,
+// and the groups of one K follow each other.  So everything a stage needs
+// from one operand is one contiguous run, and its high parts alone (a step
+// whose products all run one pass, precision chosen by norm) another, each
+// moved by a single bulk copy into shared memory already in the layout the
+// MMA reads.  Sparsified trees keep their own banded layout (one array per
+// part, see k_leaf_pack).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -341,6 +345,8 @@ __global__ void __launch_bounds__(pack_threads<LEAF>()) k_leaf_pack(const float*
     constexpr int CPC = 16 / EPU;                        // core matrices per 16-wide K chunk
     constexpr int LDS = 128 + 4;                         // padded staging row
     constexpr int NPART = PK == 1 ? 1 : 2;               // hi (and lo) parts
+    // chunks per pack group (high parts of the group, then low parts)
+    constexpr int CG = pack_group_chunks(LEAF, PK == 2 ? SPAMM_PREC_TF32X3 : SPAMM_PREC_F16X3);
     extern __shared__ __align__(16) float raw_dyn[];     // LEAF x LDS staged strip
     float (*raw)[LDS] = reinterpret_cast<float (*)[LDS]>(raw_dyn);
     __shared__ int needA[TL], needB[TL], any;
@@ -428,8 +434,9 @@ __global__ void __launch_bounds__(pack_threads<LEAF>()) k_leaf_pack(const float*
                 const int64_t len = bv.imax[K] - bv.imin[K] + 1;
                 g = (size_t)(bv.aoff[K] + kca * len + (I - bv.imin[K])) * PIECE + (size_t)w * 16;
             } else {
-                g = ((size_t)((((Q0 + xa) * (nlp / TL) + I / TL) * CH + kca) * NPART) * TL +
-                     I % TL) * PIECE + (size_t)w * 16;
+                const int64_t grp = ((Q0 + xa) * (nlp / TL) + I / TL) * (CH / CG) + kca / CG;
+                const int64_t slot = grp * NPART * CG + kca % CG;   // its high-part slice
+                g = (size_t)(slot * TL + I % TL) * PIECE + (size_t)w * 16;
             }
             if (PK <= 2) {
                 const float4 v = *reinterpret_cast<const float4*>(src);
@@ -464,8 +471,10 @@ __global__ void __launch_bounds__(pack_threads<LEAF>()) k_leaf_pack(const float*
                 g = (size_t)(bv.boff[I] + kcb * len + (Q0 + xb - bv.kmin[I])) * PIECE +
                     (size_t)w * 16;
             } else {
-                g = ((size_t)(((I * (nlp / (2 * TL)) + (Q0 + xb) / (2 * TL)) * CH + kcb) * NPART) *
-                         (2 * TL) + (Q0 + xb) % (2 * TL)) * PIECE + (size_t)w * 16;
+                const int64_t grp = (I * (nlp / (2 * TL)) + (Q0 + xb) / (2 * TL)) * (CH / CG) +
+                                    kcb / CG;                 // pack group of the chunk
+                const int64_t slot = grp * NPART * CG + kcb % CG;   // its high-part slice
+                g = (size_t)(slot * (2 * TL) + (Q0 + xb) % (2 * TL)) * PIECE + (size_t)w * 16;
             }
             if (PK <= 2) {
                 float f[4];
@@ -733,10 +742,12 @@ cudaError_t launch_packs(DevCtl* ctl, const spamm_tree* A, const spamm_tree* B, 
             pa1 = roleA ? t->packA[1] : nullptr;
             pb1 = roleB ? t->packB[1] : nullptr;
         } else if (pk != 1) {
-            // grouped layout: the lo part of a group follows its hi part
+            // grouped layout: the lo parts of a group of CG chunks follow its
+            // hi parts
             const size_t slice = (size_t)128 * 16 * (pk >= 3 ? 2 : 4);   // TL pieces
-            pa1 = pa0 ? static_cast<unsigned char*>(pa0) + slice : nullptr;
-            pb1 = pb0 ? static_cast<unsigned char*>(pb0) + 2 * slice : nullptr;
+            const size_t cg = (size_t)pack_group_chunks(t->b, t->precision);
+            pa1 = pa0 ? static_cast<unsigned char*>(pa0) + cg * slice : nullptr;
+            pb1 = pb0 ? static_cast<unsigned char*>(pb0) + 2 * cg * slice : nullptr;
         }
         const double* leaf = t->pyr + off_leaf;
         dim3 grid((unsigned)t->nl, (unsigned)(t->nlp / tl));

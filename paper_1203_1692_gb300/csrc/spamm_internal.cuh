@@ -32,6 +32,15 @@ constexpr int kTileRows = 128;
 constexpr int kTileHalves = 2;
 constexpr int kMaxLeavesPerSide = 1 << 14;
 
+// Chunks per pack group: the pieces of a leaf's 16-wide K-chunks are stored
+// in groups of this many chunks, the high parts of a group before its low
+// parts (norms.cu), so that the K-chunks one leaf-kernel stage holds (four
+// for 16-bit parts and single TF32, one for TF32 hi + lo) are one contiguous
+// run per part.  At most the chunks of a leaf (b / 16).
+__host__ __device__ constexpr int pack_group_chunks(int leaf, int precision) {
+    return precision == SPAMM_PREC_TF32X3 ? 1 : (leaf / 16 < 4 ? leaf / 16 : 4);
+}
+
 // Device status bits.
 constexpr uint32_t ST_OVERFLOW = 1u;
 constexpr uint32_t ST_NONFINITE = 2u;
