@@ -307,17 +307,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     constexpr int CHUNKS = LEAF / 16;
     constexpr int ST = T::kStages;
     // K-chunks per pack group (the packs store a group's high parts before
-    // its low parts); a stage holds whole groups
+    // its low parts).  A stage is cut into U units: the A region into U
+    // 128 x 16 slices, the B region into U 256 x 16 slices.  A group of c
+    // chunks takes 2c units with both parts (high c, then low c) or c with
+    // the high parts alone, so a stage holds kSPS chunks of full groups or up
+    // to U = kParts x kSPS chunks of lean ones.
     constexpr int CG = CHUNKS < T::kSPS ? CHUNKS : T::kSPS;
+    constexpr int U = T::kParts * T::kSPS;
     static_assert(CG == pack_group_chunks(LEAF, PREC), "pack group and stage disagree");
     static_assert(T::kSPS % CG == 0, "a stage holds whole pack groups");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2],
         bar_drain;
     __shared__ uint32_t tmem_slot;
-    __shared__ unsigned long long st_mask[ST][T::kSPS][2];  // masks of each stage slot
-    __shared__ unsigned long long st_hmask[ST][T::kSPS][2]; // of those, the full-split products
-    __shared__ uint32_t st_count[ST];                        // filled slots of each stage
+    // the groups of each stage: first unit, chunks (and lean flag) packed,
+    // the kept masks and, of those, the full-split products
+    __shared__ uint32_t st_grp[ST][U];
+    __shared__ unsigned long long st_mask[ST][U][2];
+    __shared__ unsigned long long st_hmask[ST][U][2];
+    __shared__ uint32_t st_count[ST];                        // groups of each stage
     __shared__ volatile int abort_flag;
     __shared__ unsigned long long issued_s, consumed_s;
     // per product: step-list offsets in its pool, skip flag, end of its work
@@ -383,14 +391,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         // ---------------------------------------------------------- producer
         // The whole warp walks the step list in batches of 32 (each lane
         // loads one step's K and masks; the next batch is prefetched while
-        // this one is issued) and lane 0 fills the stages: up to kSPS
-        // K-chunk slots per stage, never across tiles.  For every run of
-        // slots it adds the run's bytes to the stage's expected transaction
-        // count and issues the bulk copies; closing a stage records the
-        // slots' masks and count in shared memory and arrives on the full
-        // barrier.
+        // this one is issued) and lane 0 fills the stages with groups of
+        // K-chunks (up to U units per stage, never across tiles).  For every
+        // group it adds the group's bytes to the stage's expected transaction
+        // count, issues the bulk copies and records the group's first unit,
+        // chunk count and masks; closing a stage records its group count and
+        // arrives on the full barrier.
         unsigned long long stage_it = 0;
-        int fill = 0;
+        int fill = 0;   // units of the current stage in use
+        int ng = 0;     // groups in the current stage
         int s = 0;
         bool ok = true;
         const size_t piece = (size_t)LEAF * 16 * T::kEsize;
@@ -410,21 +419,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const int64_t scol = (int64_t)(u % q.tc) * TLC;
             const uint32_t ns = q.steps[u];
             const uint64_t sb = (uint64_t)q.off[u] * q.S;
-            // lane 0: m consecutive K-chunks kc0.. of the step at K into slots
-            // fill.. of the current stage (m <= kSPS - fill).  A stage keeps the
-            // A parts of its slots together, then the B parts, each in groups
-            // of CG slots (high parts, then low parts), and the dense packs
-            // keep a tile's chunks of one K in the same groups, so a whole
-            // group is one bulk copy per operand, and so are its high parts
-            // alone.
+            // lane 0: the group of m consecutive K-chunks kc0.. of the step at K
+            // (a whole pack group, or one chunk with the sub-leaf cull or a
+            // sparsified operand) into the units fill.. of the current stage.
+            // The dense packs keep a tile's chunks of one K in the same groups
+            // (high parts, then low parts) as the stage, so a whole group is
+            // one bulk copy per operand, and so are its high parts alone.
             const int64_t ga = srow / TL, gb = scol / TLC;          // tile's pack groups
             int64_t bandK = -1;
             int64_t a_lo = 0, a_hi = -1, a_off = 0, b_lo = 0, b_hi = -1, b_off = 0;
+            auto close_stage = [&]() {
+                st_count[s] = (uint32_t)ng;
+                mbar_arrive(smem_u32(&bar_full[s]));
+                issued_s = ++stage_it;
+                fill = 0;
+                ng = 0;
+            };
             // lean: no product of the step keeps the full split (precision
             // chosen by norm), so only the high parts are loaded
             auto issue = [&](int64_t K, int kc0, int m, unsigned long long m0,
                              unsigned long long m1, unsigned long long h0,
                              unsigned long long h1, bool lean) {
+                const int parts = lean ? 1 : T::kParts;
+                const int need = parts * m;                       // units
+                if (fill > 0 && fill + need > U) close_stage();
                 if (fill == 0) {
                     s = (int)(stage_it % ST);
                     const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
@@ -433,18 +451,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 if (!ok) return;
                 const uint32_t full = smem_u32(&bar_full[s]);
                 unsigned char* const stg = stages + (size_t)s * T::kStage;
-                // shared memory of slot `slot`, part `part` (groups of CG
-                // slots: the high parts of the group, then its low parts)
-                auto a_dst = [&](int slot, int part) {
-                    return stg + (size_t)(slot / CG) * CG * T::kASlot +
-                           (size_t)part * CG * T::kSlice + (size_t)(slot % CG) * T::kSlice;
-                };
-                auto b_dst = [&](int slot, int part) {
-                    return stg + (size_t)T::kSPS * T::kASlot + (size_t)(slot / CG) * CG * T::kBSlot +
-                           (size_t)part * CG * 2 * T::kSlice + (size_t)(slot % CG) * 2 * T::kSlice;
+                // shared memory of unit x of the A and B regions
+                auto a_dst = [&](int x) { return stg + (size_t)x * T::kSlice; };
+                auto b_dst = [&](int x) {
+                    return stg + (size_t)U * T::kSlice + (size_t)x * 2 * T::kSlice;
                 };
                 // dense operand: the pack group holding chunk kc0, and chunk
-                // kc0 + j's part inside it
+                // kc0's part inside it
                 const int c0 = kc0 % CG;
                 const size_t a_grp =
                     ((size_t)(K * (q.nlp / TL) + ga) * CHUNKS + (kc0 - c0)) * T::kASlot;
@@ -452,14 +465,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     ((size_t)(K * (q.nlp / TLC) + gb) * CHUNKS + (kc0 - c0)) * T::kBSlot;
                 const unsigned char* const pa0 = static_cast<const unsigned char*>(q.pa[0]);
                 const unsigned char* const pb0 = static_cast<const unsigned char*>(q.pb[0]);
-                auto a_src = [&](int j, int part) {
-                    return pa0 + a_grp + (size_t)part * CG * T::kSlice + (size_t)(c0 + j) * T::kSlice;
+                auto a_src = [&](int part) {
+                    return pa0 + a_grp + ((size_t)part * CG + c0) * T::kSlice;
                 };
-                auto b_src = [&](int j, int part) {
-                    return pb0 + b_grp + (size_t)part * CG * 2 * T::kSlice +
-                           (size_t)(c0 + j) * 2 * T::kSlice;
+                auto b_src = [&](int part) {
+                    return pb0 + b_grp + ((size_t)part * CG + c0) * 2 * T::kSlice;
                 };
-                const int parts = lean ? 1 : T::kParts;
                 if constexpr (BAND) {
                     // m == 1 here: a sparsified operand's chunk comes from
                     // inside its band, one copy per part
@@ -507,62 +518,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         if (part >= parts) break;
                         if (q.a_lo) {
                             if (na)
-                                bulk_g2s(smem_u32(a_dst(fill, part) + da * piece),
+                                bulk_g2s(smem_u32(a_dst(fill + part) + da * piece),
                                          static_cast<const unsigned char*>(q.pa[part]) +
                                              (size_t)sa * piece,
                                          (uint32_t)(na * piece), full);
                         } else {
-                            bulk_g2s(smem_u32(a_dst(fill, part)), a_src(0, part),
+                            bulk_g2s(smem_u32(a_dst(fill + part)), a_src(part),
                                      (uint32_t)T::kSlice, full);
                         }
                         if (q.b_lo) {
                             if (nb2)
-                                bulk_g2s(smem_u32(b_dst(fill, part) + db * piece),
+                                bulk_g2s(smem_u32(b_dst(fill + part) + db * piece),
                                          static_cast<const unsigned char*>(q.pb[part]) +
                                              (size_t)sb2 * piece,
                                          (uint32_t)(nb2 * piece), full);
                         } else {
-                            bulk_g2s(smem_u32(b_dst(fill, part)), b_src(0, part),
+                            bulk_g2s(smem_u32(b_dst(fill + part)), b_src(part),
                                      (uint32_t)(2 * T::kSlice), full);
                         }
                     }
-                } else if (m == CG && c0 == 0 && fill % CG == 0) {
-                    // a whole pack group: one copy per operand, all parts
-                    // (or the high parts alone)
+                } else if (m == CG) {
+                    // a whole pack group: one copy per operand, all parts (or
+                    // the high parts alone)
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                 "r"((uint32_t)(parts * m * 3 * T::kSlice))
+                                 "r"((uint32_t)(need * 3 * T::kSlice))
                                  : "memory");
-                    bulk_g2s(smem_u32(a_dst(fill, 0)), a_src(0, 0),
-                             (uint32_t)(parts * m * T::kSlice), full);
-                    bulk_g2s(smem_u32(b_dst(fill, 0)), b_src(0, 0),
-                             (uint32_t)(parts * m * 2 * T::kSlice), full);
+                    bulk_g2s(smem_u32(a_dst(fill)), a_src(0), (uint32_t)(need * T::kSlice), full);
+                    bulk_g2s(smem_u32(b_dst(fill)), b_src(0), (uint32_t)(need * 2 * T::kSlice),
+                             full);
                 } else {
-                    // single chunks of a group (the sub-leaf cull): one copy
-                    // per operand and part
+                    // one chunk of a group (the sub-leaf cull): one copy per
+                    // operand and part
                     asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full),
-                                 "r"((uint32_t)(parts * m * 3 * T::kSlice))
+                                 "r"((uint32_t)(need * 3 * T::kSlice))
                                  : "memory");
-                    for (int j = 0; j < m; ++j)
-                        for (int part = 0; part < parts; ++part) {
-                            bulk_g2s(smem_u32(a_dst(fill + j, part)), a_src(j, part),
-                                     (uint32_t)T::kSlice, full);
-                            bulk_g2s(smem_u32(b_dst(fill + j, part)), b_src(j, part),
-                                     (uint32_t)(2 * T::kSlice), full);
-                        }
+                    for (int part = 0; part < parts; ++part) {
+                        bulk_g2s(smem_u32(a_dst(fill + part)), a_src(part), (uint32_t)T::kSlice,
+                                 full);
+                        bulk_g2s(smem_u32(b_dst(fill + part)), b_src(part),
+                                 (uint32_t)(2 * T::kSlice), full);
+                    }
                 }
-                for (int j = 0; j < m; ++j) {
-                    st_mask[s][fill + j][0] = m0;
-                    st_mask[s][fill + j][1] = m1;
-                    st_hmask[s][fill + j][0] = h0;
-                    st_hmask[s][fill + j][1] = h1;
-                }
-                fill += m;
-                if (fill == T::kSPS) {
-                    st_count[s] = (uint32_t)fill;
-                    mbar_arrive(full);
-                    issued_s = ++stage_it;
-                    fill = 0;
-                }
+                st_grp[s][ng] = (uint32_t)fill | ((uint32_t)m << 8);
+                st_mask[s][ng][0] = m0;
+                st_mask[s][ng][1] = m1;
+                st_hmask[s][ng][0] = h0;
+                st_hmask[s][ng][1] = h1;
+                ++ng;
+                fill += need;
+                if (fill == U) close_stage();
             };
             if (q.sl == 1) {
                 // one mask pair per step, shared by its K-chunks
@@ -597,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         for (int kc = 0; kc < CHUNKS && ok;) {
                             int m = 1;
                             if (lane == 0) {
-                                if (!BAND) m = min(CHUNKS - kc, T::kSPS - fill);
+                                if (!BAND) m = CG;
                                 issue(K, kc, m, m0, m1, h0, h1, lean);
                             }
                             m = __shfl_sync(0xffffffffu, m, 0);
@@ -658,12 +662,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 }
             }
             // a stage never spans two tiles
-            if (lane == 0 && fill > 0) {
-                st_count[s] = (uint32_t)fill;
-                mbar_arrive(smem_u32(&bar_full[s]));
-                issued_s = ++stage_it;
-                fill = 0;
-            }
+            if (lane == 0 && fill > 0) close_stage();
         }
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA
@@ -694,18 +693,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         ok = false;
                         break;
                     }
-                    const uint32_t cnt = st_count[s];
+                    const int ngs = (int)st_count[s];
                     consumed_s = stage_it + 1;
-                    // the stage's masks in one go, then its slots unrolled (slot
-                    // offsets become constants); this loop is the MMA issue path
-                    unsigned long long mk0[T::kSPS], mk1[T::kSPS], hk0[T::kSPS], hk1[T::kSPS];
-#pragma unroll
-                    for (int jj = 0; jj < T::kSPS; ++jj) {
-                        mk0[jj] = st_mask[s][jj][0];
-                        mk1[jj] = st_mask[s][jj][1];
-                        hk0[jj] = st_hmask[s][jj][0];
-                        hk1[jj] = st_hmask[s][jj][1];
-                    }
                     const uint32_t sbuf = smem_u32(stages + (size_t)s * T::kStage);
                     constexpr unsigned long long kRep =
                         TL == 8   ? 0x0101010101010101ull
@@ -715,67 +704,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     constexpr unsigned long long kFull =
                         (unsigned long long)((1u << TL) - 1u) * kRep;
                     // The MMAs of one pass set over the products of masks (r0,
-                    // r1), for the slots [j0, j1) of the stage: MODE 3 = all
-                    // three of the split (lo*hi, hi*lo, hi*hi; hi*hi alone for
-                    // single TF32), 1 = hi*hi, 2 = the cross terms.  Runs of
-                    // column leaves with the same kept row leaves: a column y
-                    // starts a run when its row mask is non-zero and differs
-                    // from column y-1's.  Uniform halves (the common case on
-                    // dense blocks) give one run directly.  Slot jj sits in its
-                    // group of CG slots, high parts first, then low parts.
+                    // r1), for ngrp groups of c chunks each, the first at unit
+                    // u0 and the others every `stride` units: MODE 3 = all three
+                    // of the split (lo*hi, hi*lo, hi*hi; hi*hi alone for single
+                    // TF32), 1 = hi*hi, 2 = the cross terms.  Chunk j of a group
+                    // at unit x has its high parts at unit x + j and its low
+                    // parts at unit x + c + j.  Runs of column leaves with the
+                    // same kept row leaves: a column y starts a run when its row
+                    // mask is non-zero and differs from column y-1's.  Uniform
+                    // halves (the common case on dense blocks) give one run
+                    // directly.
                     auto passes = [&](unsigned long long r0, unsigned long long r1, auto mode_c,
-                                      int j0, int j1) {
+                                      int u0, int c, int ngrp, int stride) {
                         constexpr int MODE = decltype(mode_c)::value;
                         constexpr bool kCross = PREC != SPAMM_PREC_TF32 && MODE != 1;
                         constexpr bool kHiHi = MODE != 2;
-                        // the MMAs of slot jj over one run: N = nn, TMEM
-                        // columns from d, B rows from boff, lane mask dis
-                        auto slot_mmas = [&](int jj, uint32_t d, uint32_t boff, uint32_t idesc,
-                                             const uint32_t (&dis)[4], bool masked) {
-                            const uint32_t a_hi = sbuf + (uint32_t)((jj / CG) * CG * T::kASlot +
-                                                                    (jj % CG) * T::kSlice);
-                            const uint32_t a_lo = a_hi + (uint32_t)(CG * T::kSlice);
-                            const uint32_t b_hi =
-                                sbuf + (uint32_t)(T::kSPS * T::kASlot + (jj / CG) * CG * T::kBSlot +
-                                                  (jj % CG) * 2 * T::kSlice) + boff;
-                            const uint32_t b_lo = b_hi + (uint32_t)(CG * 2 * T::kSlice);
+                        // the MMAs of every chunk of the groups over one run: N
+                        // = the run's columns, TMEM columns from d, B rows from
+                        // boff, lane mask dis
+                        auto run_mmas = [&](uint32_t d, uint32_t boff, uint32_t idesc,
+                                            const uint32_t (&dis)[4], bool masked) {
+                            for (int gq = 0; gq < ngrp; ++gq) {
+                                const int x = u0 + gq * stride;
 #pragma unroll
-                            for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
-                                const uint32_t koff = (uint32_t)kk * 256u;
-                                const uint64_t ah = make_desc(a_hi + koff, 128, T::kSBO);
-                                const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
-                                if (kCross) {
-                                    const uint64_t al = make_desc(a_lo + koff, 128, T::kSBO);
-                                    const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
-                                    if (masked) {
-                                        mma<PREC>(d, al, bh, idesc, dis, 1u);
-                                        mma<PREC>(d, ah, bl, idesc, dis, 1u);
-                                    } else {
-                                        mma_all<PREC>(d, al, bh, idesc, 1u);
-                                        mma_all<PREC>(d, ah, bl, idesc, 1u);
+                                for (int j = 0; j < CG; ++j) {
+                                    if (j >= c) break;
+                                    const uint32_t a_hi = sbuf + (uint32_t)(x + j) * T::kSlice;
+                                    const uint32_t a_lo = a_hi + (uint32_t)c * T::kSlice;
+                                    const uint32_t b_hi = sbuf + (uint32_t)(U * T::kSlice) +
+                                                          (uint32_t)(x + j) * 2 * T::kSlice + boff;
+                                    const uint32_t b_lo = b_hi + (uint32_t)c * 2 * T::kSlice;
+#pragma unroll
+                                    for (int kk = 0; kk < 16 / T::kKInstr; ++kk) {
+                                        const uint32_t koff = (uint32_t)kk * 256u;
+                                        const uint64_t ah = make_desc(a_hi + koff, 128, T::kSBO);
+                                        const uint64_t bh = make_desc(b_hi + koff, 128, T::kSBO);
+                                        if (kCross) {
+                                            const uint64_t al = make_desc(a_lo + koff, 128, T::kSBO);
+                                            const uint64_t bl = make_desc(b_lo + koff, 128, T::kSBO);
+                                            if (masked) {
+                                                mma<PREC>(d, al, bh, idesc, dis, 1u);
+                                                mma<PREC>(d, ah, bl, idesc, dis, 1u);
+                                            } else {
+                                                mma_all<PREC>(d, al, bh, idesc, 1u);
+                                                mma_all<PREC>(d, ah, bl, idesc, 1u);
+                                            }
+                                        }
+                                        if (kHiHi) {
+                                            if (masked) mma<PREC>(d, ah, bh, idesc, dis, 1u);
+                                            else mma_all<PREC>(d, ah, bh, idesc, 1u);
+                                        }
                                     }
-                                }
-                                if (kHiHi) {
-                                    if (masked) mma<PREC>(d, ah, bh, idesc, dis, 1u);
-                                    else mma_all<PREC>(d, ah, bh, idesc, 1u);
                                 }
                             }
                         };
                         if (r0 == kFull && r1 == kFull) {
                             // every product of the step: one 128 x 256 MMA per
                             // pass, no masks
-                            constexpr uint32_t idesc_full = make_idesc(T::kAB, 128, 256);
-#pragma unroll
-                            for (int jj = 0; jj < T::kSPS; ++jj)
-                                if (jj >= j0 && jj < j1) slot_mmas(jj, dacc, 0u, idesc_full, dis0, false);
+                            run_mmas(dacc, 0u, make_idesc(T::kAB, 128, 256), dis0, false);
                             return;
                         }
                         const uint32_t x0 = (uint32_t)r0 & 0xFFu;
                         const uint32_t x1 = (uint32_t)r1 & 0xFFu;
-                        const bool u0 = r0 == (unsigned long long)x0 * kRep;
-                        const bool u1 = r1 == (unsigned long long)x1 * kRep;
+                        const bool u0m = r0 == (unsigned long long)x0 * kRep;
+                        const bool u1m = r1 == (unsigned long long)x1 * kRep;
                         uint32_t starts, nz;
-                        if (u0 && u1) {
+                        if (u0m && u1m) {
                             starts = (x0 ? 1u : 0u) | ((x1 && x1 != x0) ? (1u << TL) : 0u);
                             nz = (x0 ? (1u << TL) - 1u : 0u) | (x1 ? ((1u << TL) - 1u) << TL : 0u);
                         } else {
@@ -819,27 +813,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                                 }
                                 dis[w] = v;
                             }
-                            const uint32_t idesc = make_idesc(T::kAB, 128, len * LEAF);
-                            const uint32_t d = dacc + (uint32_t)(y * LEAF);
-                            const uint32_t boff = (uint32_t)(y * (LEAF / 8)) * T::kSBO;
-#pragma unroll
-                            for (int jj = 0; jj < T::kSPS; ++jj)
-                                if (jj >= j0 && jj < j1) slot_mmas(jj, d, boff, idesc, dis, true);
-                        }
-                    };
-                    // every pass set of slots [j0, j1) sharing the masks (m, h):
-                    // the full split where h == m; with precision chosen by
-                    // norm, hi * hi for every kept product and the cross terms
-                    // for the full-split ones
-                    auto pass_sets = [&](unsigned long long m0, unsigned long long m1,
-                                         unsigned long long h0, unsigned long long h1, int j0,
-                                         int j1) {
-                        if (h0 == m0 && h1 == m1) {
-                            passes(m0, m1, std::integral_constant<int, 3>{}, j0, j1);
-                        } else {
-                            passes(m0, m1, std::integral_constant<int, 1>{}, j0, j1);
-                            if ((h0 | h1) != 0ull)
-                                passes(h0, h1, std::integral_constant<int, 2>{}, j0, j1);
+                            run_mmas(dacc + (uint32_t)(y * LEAF), (uint32_t)(y * (LEAF / 8)) * T::kSBO,
+                                     make_idesc(T::kAB, 128, len * LEAF), dis, true);
                         }
                     };
                     // a new TMEM chunk at every kChunkIters-th K-chunk of a tile:
@@ -854,44 +829,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256), dis0, 0u);
                         return true;
                     };
-                    // the chunk's last K-chunk (or the tile's): hand it over
-                    auto close_chunk = [&](uint32_t last) {
+                    // Groups in stage order.  Consecutive groups with the same
+                    // masks inside one TMEM chunk share one run analysis: with
+                    // the same masks they are both lean or both full and, within
+                    // a tile, all groups have the same chunk count, so they sit
+                    // at a fixed stride of units.
+                    for (int g = 0; g < ngs && ok;) {
+                        const uint32_t rec = st_grp[s][g];
+                        const int u0 = (int)(rec & 0xFFu), c = (int)((rec >> 8) & 0xFFu);
+                        const unsigned long long m0 = st_mask[s][g][0], m1 = st_mask[s][g][1];
+                        const unsigned long long h0 = st_hmask[s][g][0], h1 = st_hmask[s][g][1];
+                        int g2 = g + 1;
+                        int stride = 0;
+                        const uint32_t room = kChunkIters - i % kChunkIters;   // chunks left in the TMEM chunk
+                        while (g2 < ngs && (uint32_t)((g2 - g + 1) * c) <= room &&
+                               st_mask[s][g2][0] == m0 && st_mask[s][g2][1] == m1 &&
+                               st_hmask[s][g2][0] == h0 && st_hmask[s][g2][1] == h1) {
+                            const int x = (int)(st_grp[s][g2] & 0xFFu);
+                            if (g2 == g + 1) stride = x - u0;
+                            else if (x - u0 != stride * (g2 - g)) break;
+                            ++g2;
+                        }
+                        if (i % kChunkIters == 0 && !open_chunk()) {
+                            ok = false;
+                            break;
+                        }
+                        const int ngrp = g2 - g;
+                        if (h0 == m0 && h1 == m1) {
+                            passes(m0, m1, std::integral_constant<int, 3>{}, u0, c, ngrp, stride);
+                        } else {
+                            // precision chosen by norm: hi * hi for every kept
+                            // product, the cross terms for the full-split ones
+                            passes(m0, m1, std::integral_constant<int, 1>{}, u0, c, ngrp, stride);
+                            if ((h0 | h1) != 0ull)
+                                passes(h0, h1, std::integral_constant<int, 2>{}, u0, c, ngrp, stride);
+                        }
+                        i += (uint32_t)(ngrp * c);
+                        const uint32_t last = i - 1;
                         if (last % kChunkIters == kChunkIters - 1 || last == iters - 1) {
                             tc_commit(smem_u32(&bar_accf[ccount & 1]));
                             ++ccount;
                         }
-                    };
-                    // A stage starts at a multiple of kSPS K-chunks of its tile
-                    // and kSPS divides kChunkIters, so it never crosses a TMEM
-                    // chunk.  When all its slots carry the same masks (every
-                    // stage of a step with unculled chunks, and dense steps of
-                    // any leaf size), one run analysis serves them all.
-                    bool uni = true;
-#pragma unroll
-                    for (int jj = 1; jj < T::kSPS; ++jj)
-                        if ((uint32_t)jj < cnt)
-                            uni = uni && mk0[jj] == mk0[0] && mk1[jj] == mk1[0] &&
-                                  hk0[jj] == hk0[0] && hk1[jj] == hk1[0];
-                    if (uni) {
-                        if (i % kChunkIters == 0 && !open_chunk()) {
-                            ok = false;
-                        } else {
-                            pass_sets(mk0[0], mk1[0], hk0[0], hk1[0], 0, (int)cnt);
-                            i += cnt;
-                            close_chunk(i - 1);
-                        }
-                    } else {
-#pragma unroll
-                        for (int jj = 0; jj < T::kSPS; ++jj) {
-                            if ((uint32_t)jj >= cnt || !ok) break;
-                            if (i % kChunkIters == 0 && !open_chunk()) {
-                                ok = false;
-                                break;
-                            }
-                            pass_sets(mk0[jj], mk1[jj], hk0[jj], hk1[jj], jj, jj + 1);
-                            close_chunk(i);
-                            ++i;
-                        }
+                        g = g2;
                     }
                     // the stage's MMAs have read its shared memory once they complete
                     tc_commit(smem_u32(&bar_empty[s]));
