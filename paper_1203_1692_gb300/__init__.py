@@ -234,8 +234,9 @@ class Context:
         return _stats_dict(spamm_stats_item(self.handle, index, raise_on_error))
 
     def per_product_flops(self, count: int) -> list:
-        """Kept flops of each product of the last batched multiply."""
-        return [spamm_stats_item(self.handle, p).kept_flops for p in range(count)]
+        """Kept flops of each product of the last batched multiply (over the
+        leaves' extents inside the matrices)."""
+        return [spamm_stats_item(self.handle, p).kept_flops_clipped for p in range(count)]
 
     def cull_flat(self, A: Tree, B: Tree, tau: float, triples: bool = True):
         """The flat, norm-sorted enumeration (Algorithm 1) on the GPU:

@@ -15,9 +15,12 @@ blocks in turn, so the products at the end of the list make up the tail of
 the launch; "largest_first" puts the big products first and leaves the small
 ones to fill the tail.
 
-Choices are cached in-process per signature (precision, tau, the products'
-orders rounded to powers of two), so a serving loop pays for a tuning run
-once per kind of batch.
+Choices are cached in-process per signature: precision, precision tier,
+tau, the products' orders rounded to powers of two, and a decay estimate
+of each product from its norm profile (the share of the operand's squared
+Frobenius norm held by its 64 x 64 diagonal blocks, as a power of two), so
+a serving loop pays for a tuning run once per kind of batch and batches of
+equal sizes but different decay are tuned apart.
 """
 from __future__ import annotations
 
@@ -51,26 +54,52 @@ def order_of(order: str, ns):
     return idx
 
 
-def signature(ns, taus, precision: str):
-    return (precision, tuple(sorted(round(math.log2(max(n, 1))) for n in ns)),
-            tuple(sorted(set(float(t) for t in taus))))
+def decay_estimate(A, blk: int = 64) -> float:
+    """Share of ||A||_F^2 held by the blk x blk diagonal blocks of the square
+    matrix A (1 for block-diagonal matrices, about blk / n without decay)."""
+    import torch
+    n = A.shape[0]
+    nb = -(-n // blk)
+    P = torch.zeros((nb * blk, nb * blk), dtype=torch.float32, device=A.device)
+    P[:n, :n] = A
+    Q = P.view(nb, blk, nb, blk)
+    diag = torch.diagonal(Q, dim1=0, dim2=2)          # blk x blk x nb
+    tot = float((P.double() ** 2).sum())
+    return float((diag.double() ** 2).sum()) / tot if tot > 0 else 1.0
 
 
-def cached(ns, taus, precision: str, leaves=LEAVES, orders=ORDERS, slices=SLICES):
-    return _CACHE.get(signature(ns, taus, precision) + (tuple(leaves), tuple(orders),
-                                                        tuple(slices)))
+def decay_bucket(A) -> int:
+    return int(round(math.log2(max(decay_estimate(A), 1e-30))))
+
+
+def signature(ns, taus, precision: str, decay=None, tier_bits: int = 0):
+    sig = (precision, int(tier_bits), tuple(sorted(round(math.log2(max(n, 1))) for n in ns)),
+           tuple(sorted(set(float(t) for t in taus))))
+    if decay is not None:
+        sig += (tuple(sorted(decay)),)
+    return sig
+
+
+def cached(ns, taus, precision: str, leaves=LEAVES, orders=ORDERS, slices=SLICES, decay=None,
+           tier_bits: int = 0):
+    return _CACHE.get(signature(ns, taus, precision, decay, tier_bits) +
+                      (tuple(leaves), tuple(orders), tuple(slices)))
 
 
 def tune_batch(pairs, taus, precision: str = "tf32x3", leaves=LEAVES, orders=ORDERS,
-               slices=SLICES, reps: int = 3, use_cache: bool = True) -> Choice:
+               slices=SLICES, reps: int = 3, use_cache: bool = True,
+               tier_bits: int = 0) -> Choice:
     """Pick (leaf, order, sub-leaf cull) for the batch of products ``pairs``
-    = [(A, B), ...] (square float32 CUDA tensors) at thresholds ``taus``.
-    The sub-leaf cull changes the approximation (it drops more), so it is a
-    candidate only where the caller accepts that (``slices``)."""
+    = [(A, B), ...] (square float32 CUDA tensors) at thresholds ``taus``,
+    under the precision tier ``tier_bits`` (0 = off).  The sub-leaf cull
+    changes the approximation (it drops more), so it is a candidate only
+    where the caller accepts that (``slices``)."""
     import torch
     from . import Context
     ns = [A.shape[0] for A, _ in pairs]
-    sig = signature(ns, taus, precision) + (tuple(leaves), tuple(orders), tuple(slices))
+    decay = [decay_bucket(A) for A, _ in pairs]
+    sig = signature(ns, taus, precision, decay, tier_bits) + (tuple(leaves), tuple(orders),
+                                                              tuple(slices))
     if use_cache and sig in _CACHE:
         return _CACHE[sig]
     stream = torch.cuda.current_stream()
@@ -78,7 +107,7 @@ def tune_batch(pairs, taus, precision: str = "tf32x3", leaves=LEAVES, orders=ORD
     combos = [(b, sl) for b in leaves for sl in slices
               if sl == 0 or (precision != "fp32" and b >= 32)]
     for b, sl in combos:
-        ctx = Context(leaf=b, precision=precision, checked=True, slice=sl)
+        ctx = Context(leaf=b, precision=precision, checked=True, slice=sl, tier_bits=tier_bits)
         trees_a, trees_b = [], []
         for A, B in pairs:
             ta = ctx.build_norms(A)

@@ -17,6 +17,14 @@ iteration
      device;
   3. retires the requests whose chain is complete and frees their memory.
 
+With an executor that can launch a batch without waiting for it
+(``launch``/``ready``/``collect``, as ``GpuChainExecutor`` does), the
+squaring runs asynchronously: while it is on the device the server keeps
+taking arrivals, admits them and makes them resident (their copies and
+norm trees queue behind the batch), and it picks up the batch's results
+once its completion event has fired.  Admission counts the executor's own
+scratch (the triple pools of its batch slots) against the budget as well.
+
 A request's norm tree, pack arrays and triple lists stay resident on the
 device for its whole chain.  Every product of a batch gives the same C, bit
 for bit, as the same product run alone, so a request's result does not
@@ -77,35 +85,32 @@ class Server:
         self.iterations = 0
         self.peak_used = 0
         self.batch_sizes: list[int] = []
+        self.joining: list[Request] = []   # admitted while a batch is on the device
 
     def submit(self, req: Request) -> None:
         if self.ex.footprint(req) > self.budget:
             raise AdmissionError(f"request {req.rid} (n={req.n}) exceeds the memory budget")
         self.waiting.append(req)
 
-    def _admit(self) -> None:
-        while self.waiting and len(self.active) < self.max_active:
+    def _scratch(self) -> int:
+        f = getattr(self.ex, "scratch_bytes", None)
+        return int(f()) if f else 0
+
+    def _admit(self, into=None) -> None:
+        active = self.active if into is None else into
+        while self.waiting and len(self.active) + len(self.joining) < self.max_active:
             req = self.waiting[0]
             need = self.ex.footprint(req)
-            if self.used + need > self.budget:
+            if self.used + need + self._scratch() > self.budget:
                 break                      # arrival order: no overtaking
             self.waiting.pop(0)
             self.used += need
             self.peak_used = max(self.peak_used, self.used)
             self.ex.start(req)
             req.admitted = self.ex.now()
-            self.active.append(req)
+            active.append(req)
 
-    def step(self) -> bool:
-        """One scheduler iteration; False when there was nothing to run."""
-        self._admit()
-        if not self.active:
-            return False
-        batch = list(self.active)
-        flops = self.ex.step(batch)
-        self.iterations += 1
-        self.batch_sizes.append(len(batch))
-        t = self.ex.now()
+    def _retire(self, batch, flops, t) -> None:
         still = []
         for req, f in zip(batch, flops):
             req.kept_flops += f
@@ -118,7 +123,44 @@ class Server:
             else:
                 still.append(req)
         self.active = still
+
+    def step(self) -> bool:
+        """One scheduler iteration; False when there was nothing to run."""
+        self._admit()
+        if not self.active:
+            return False
+        batch = list(self.active)
+        flops = self.ex.step(batch)
+        self.iterations += 1
+        self.batch_sizes.append(len(batch))
+        self._retire(batch, flops, self.ex.now())
         return True
+
+    def step_async(self, pending, cursor: int) -> tuple[bool, int]:
+        """One iteration with the batch on the device while arrivals are
+        taken and admitted; returns (ran, new cursor into pending)."""
+        self._admit()
+        if not self.active:
+            return False, cursor
+        batch = list(self.active)
+        handle = self.ex.launch(batch)
+        self.iterations += 1
+        self.batch_sizes.append(len(batch))
+        self.joining = []
+        while True:
+            now = self.ex.now()
+            while cursor < len(pending) and pending[cursor].arrival <= now:
+                self.submit(pending[cursor])
+                cursor += 1
+            self._admit(into=self.joining)
+            if self.ex.ready(handle):
+                break
+            self.ex.idle()
+        flops = self.ex.collect(handle, batch)
+        self._retire(batch, flops, self.ex.now())
+        self.active += self.joining
+        self.joining = []
+        return True, cursor
 
     def run(self, requests, idle_wait=None) -> list[Request]:
         """Serve ``requests`` (sorted by arrival) in real time on the
@@ -126,13 +168,18 @@ class Server:
         arrival time; when nothing is active the server waits for the next
         arrival."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        asynchronous = getattr(self.ex, "asynchronous", False) and hasattr(self.ex, "launch")
         i = 0
         while i < len(pending) or self.waiting or self.active:
             now = self.ex.now()
             while i < len(pending) and pending[i].arrival <= now:
                 self.submit(pending[i])
                 i += 1
-            if not self.step():
+            if asynchronous:
+                ran, i = self.step_async(pending, i)
+            else:
+                ran = self.step()
+            if not ran:
                 if i < len(pending):
                     (idle_wait or self.ex.wait_until)(pending[i].arrival)
         return self.done
@@ -140,18 +187,28 @@ class Server:
 
 class GpuChainExecutor:
     """Runs chains of squarings on the CUDA library: per request a copy X of
-    X0, a buffer Y for X^2 and a norm tree (with its packs) on the device."""
+    X0, a buffer Y for X^2 and a norm tree (with its packs) on the device.
 
-    def __init__(self, leaf: int = 16, precision: str = "tf32x3", keep_results: bool = True):
+    With ``asynchronous`` (the default) a batch is launched unchecked and
+    an event recorded behind it; ``ready`` polls the event and ``collect``
+    reads the batch's statuses.  A batch whose triple pools overflowed is
+    run again in checked mode (which grows the pools); its inputs are
+    untouched until ``collect`` swaps X and X^2, so the rerun gives the same
+    result.  ``step`` is the synchronous form (launch, wait, collect)."""
+
+    def __init__(self, leaf: int = 16, precision: str = "tf32x3", keep_results: bool = True,
+                 tier_bits: int = 0, slice: int = 0, asynchronous: bool = True):
         import torch
         from . import Context
         self.torch = torch
-        # checked: each batch waits for the device and grows pools as needed,
-        # so the server clock sees completions as they happen
-        self.ctx = Context(leaf=leaf, precision=precision, checked=True)
+        self.ctx = Context(leaf=leaf, precision=precision, checked=not asynchronous,
+                           tier_bits=tier_bits, slice=slice)
+        self.asynchronous = asynchronous
         self.keep_results = keep_results
         self.t0 = time.perf_counter()
         self._foot = {}
+        self._scratch = 0
+        self.reruns = 0
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -172,13 +229,62 @@ class GpuChainExecutor:
         tree = self.ctx.build_norms(X)
         req.state = {"X": X, "Y": Y, "tree": tree, "fresh": True}
 
-    def step(self, reqs):
+    def _note_device_use(self) -> None:
+        free, total = self.torch.cuda.mem_get_info()
+        self.device_used_peak = max(getattr(self, "device_used_peak", 0), total - free)
+
+    def scratch_bytes(self) -> int:
+        """Device bytes of the triple pools of the batch slots (they only grow)."""
+        return self._scratch
+
+    def _run(self, reqs, checked: bool):
         trees = [r.state["tree"] for r in reqs]
         Ys = [r.state["Y"] for r in reqs]
         stale = [r for r in reqs if not r.state["fresh"]]
         if stale:
             self.ctx.rebuild_batched([r.state["tree"] for r in stale], [r.state["X"] for r in stale])
+        self.ctx.set_checked(checked)
         self.ctx.multiply_batched(trees, trees, [r.tau for r in reqs], None, None, Ys)
+
+    def launch(self, reqs):
+        """Queue one squaring of every request; returns an event behind it."""
+        self._run(reqs, checked=False)
+        ev = self.torch.cuda.Event()
+        ev.record(self.ctx.stream)
+        return ev
+
+    def ready(self, handle) -> bool:
+        return handle.query()
+
+    def idle(self) -> None:
+        time.sleep(2e-5)
+
+    def collect(self, handle, reqs):
+        """Statuses of the finished batch (rerun checked if a pool
+        overflowed), kept flops per request, X <- X^2."""
+        handle.synchronize()
+        st = self.ctx.stats(raise_on_error=False)
+        if st["status"] != 0:
+            self.reruns += 1
+            for r in reqs:
+                if not r.state["fresh"]:
+                    r.state["fresh"] = True   # the trees already hold X's norms
+            self._run(reqs, checked=True)     # raises on anything but overflow
+            st = self.ctx.stats()
+        self._scratch = max(self._scratch, int(st["pool_bytes"]))
+        self._note_device_use()
+        flops = [f for f in self.ctx.per_product_flops(len(reqs))]
+        for r in reqs:
+            s = r.state
+            s["X"], s["Y"] = s["Y"], s["X"]     # X <- X^2
+            s["fresh"] = False
+        return flops
+
+    def step(self, reqs):
+        if self.asynchronous:
+            return self.collect(self.launch(reqs), reqs)
+        self._run(reqs, checked=True)
+        self._scratch = max(self._scratch, int(self.ctx.stats()["pool_bytes"]))
         flops = self.ctx.per_product_flops(len(reqs))
         for r in reqs:
             st = r.state

@@ -29,8 +29,9 @@ def test_reference_arm_json_line():
     d = lines[0]
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC
     assert d["value"] > 0 and d["unit"] == "TFLOP/s" and d["higher_is_better"] is True
-    b, tau = bench.SETTLED["water7500"]
+    b, tau, bits = bench.SETTLED["water7500"]
     assert d["config"]["leaf"] == b and d["config"]["tau"] == tau and d["config"]["n"] == 7500
+    assert d["config"]["tier_bits"] == bits
     cpu = d["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -102,3 +103,24 @@ def test_cpu_baseline_reports_model_and_single_thread_rate():
     v1, desc = bench.cpu_sample_single_thread(A, 16, 1e-6, 0.2)
     assert v1 > 0 and "kept leaf products" in desc
     assert O.threads() == threads          # restored
+
+
+def test_clipped_flops_and_passes():
+    """Kept flops over the leaves' extents inside the matrix (the ragged last
+    leaf row and column clipped), and the tensor-core passes per product
+    under precision chosen by norm."""
+    import numpy as np
+    import spamm_inputs as gen
+    from oracle import oracle as O
+    n, b, tau = 100, 16, 0.0
+    A = gen.uniform_dense(n, seed=3)
+    nl = -(-n // b)
+    ij = [(0, 0), (nl - 1, nl - 1), (nl - 1, 0)]
+    # tau = 0 on a dense matrix: every K is kept
+    ext = [min(b, n - k * b) for k in range(nl)]
+    want = sum(2.0 * ext[I] * ext[J] * sum(ext) for I, J in ij)
+    assert bench.clipped_flops(A, b, tau, ij) == want
+    assert bench.mma_passes("f16x3", {"leaf_triples": 10, "hi_products": 10}) == 3.0
+    assert bench.mma_passes("f16x3", {"leaf_triples": 10, "hi_products": 0}) == 1.0
+    assert bench.mma_passes("tf32", {"leaf_triples": 10, "hi_products": 10}) == 1.0
+    del np, O

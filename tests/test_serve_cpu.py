@@ -92,3 +92,70 @@ def test_slot_limit_and_oversized_request():
     srv2 = Server(FakeExec(), budget_bytes=100)
     with pytest.raises(AdmissionError):
         srv2.submit(Request(rid=0, n=1000, tau=1e-6))
+
+
+class FakeAsyncExec(FakeExec):
+    """A batch runs on a simulated device while the server keeps admitting:
+    launch returns the batch's completion time, ready compares the clock
+    with it, idle advances the clock."""
+
+    asynchronous = True
+
+    def __init__(self, rate=1e9, scratch=0):
+        super().__init__(rate)
+        self.scratch = scratch
+        self.admitted_during = []      # rids made resident while a batch ran
+        self.busy_until = None
+
+    def scratch_bytes(self):
+        return self.scratch
+
+    def start(self, req):
+        super().start(req)
+        if self.busy_until is not None:
+            self.admitted_during.append(req.rid)
+
+    def launch(self, reqs):
+        self.log.append((self.t, [r.rid for r in reqs]))
+        self.busy_until = self.t + sum(r.n * r.n for r in reqs) / self.rate
+        return self.busy_until
+
+    def ready(self, handle):
+        return self.t >= handle
+
+    def idle(self):
+        self.t += 1e-4
+
+    def collect(self, handle, reqs):
+        self.busy_until = None
+        return [2.0 * r.n ** 3 for r in reqs]
+
+
+def test_async_batches_admit_arrivals_while_the_device_runs():
+    """Requests arriving while a batch is on the device are admitted and
+    made resident during it, join the next batch, and every chain still
+    completes with its eight squarings."""
+    ex = FakeAsyncExec(rate=1e8)
+    srv = Server(ex, budget_bytes=10 ** 12)
+    done = srv.run(_trace([4000, 1000, 500, 2000, 800], gap=0.01))
+    assert sorted(r.rid for r in done) == list(range(5))
+    assert all(r.done_steps == 8 for r in done)
+    assert ex.admitted_during                     # admission overlapped a batch
+    for t, rids in ex.log:                        # a request never runs twice in a batch
+        assert len(rids) == len(set(rids))
+    assert not ex.resident
+
+
+def test_admission_counts_the_executor_scratch():
+    """The executor's own scratch (its batch slots' triple pools) comes out of
+    the budget before any request is admitted."""
+    ns = [1000, 1000, 1000]
+    scratch = 16 * 1000 * 1000
+    budget = 2 * 16 * 1000 * 1000 + scratch        # room for two requests beside the scratch
+    ex = FakeAsyncExec(rate=1e8, scratch=scratch)
+    srv = Server(ex, budget_bytes=budget)
+    done = srv.run([Request(rid=i, n=n, tau=1e-6, squarings=2, arrival=0.0)
+                    for i, n in enumerate(ns)])
+    assert len(done) == 3
+    assert srv.peak_used + scratch <= budget
+    assert max(len(r) for _, r in ex.log) == 2

@@ -26,16 +26,41 @@ def _requests():
             for i, (n, tau, t) in enumerate(spec)]
 
 
-@pytest.mark.parametrize("prec,b", [("tf32x3", 16), ("bf16x3", 32), ("fp32", 16)])
-def test_result_is_the_same_alone_and_in_the_mix(prec, b):
+@pytest.mark.parametrize("prec,b,bits,asynchronous", [("tf32x3", 16, 0, True),
+                                                      ("bf16x3", 32, 0, False),
+                                                      ("fp32", 16, 0, True),
+                                                      ("f16x3", 64, 10, True)])
+def test_result_is_the_same_alone_and_in_the_mix(prec, b, bits, asynchronous):
+    """Asynchronous batches (admission while a batch runs) and synchronous
+    ones, with and without precision chosen by norm."""
     from paper_1203_1692_gb300.serve import GpuChainExecutor, Server
-    mixed = Server(GpuChainExecutor(leaf=b, precision=prec), budget_bytes=8 << 30)
+
+    def ex():
+        return GpuChainExecutor(leaf=b, precision=prec, tier_bits=bits, asynchronous=asynchronous)
+    mixed = Server(ex(), budget_bytes=8 << 30)
     done = {r.rid: r for r in mixed.run(_requests())}
     assert max(mixed.batch_sizes) >= 3
     for req in _requests():
-        alone = Server(GpuChainExecutor(leaf=b, precision=prec), budget_bytes=8 << 30)
+        alone = Server(ex(), budget_bytes=8 << 30)
         got = alone.run([req])[0]
         assert torch.equal(got.result, done[req.rid].result)
+
+
+def test_async_batch_with_overflowing_pools_is_rerun():
+    """Sub-context pools that start tiny overflow in the unchecked batch; the
+    executor reruns the batch checked and the chain matches a checked run."""
+    from paper_1203_1692_gb300.serve import GpuChainExecutor, Server
+    ex = GpuChainExecutor(leaf=16, precision="tf32x3")
+    ex.ctx.close()
+    import paper_1203_1692_gb300 as P
+    ex.ctx = P.Context(leaf=16, precision="tf32x3", checked=False, pool_bytes=16384)
+    got = {r.rid: r for r in Server(ex, budget_bytes=8 << 30).run(_requests())}
+    assert ex.reruns >= 1
+    ref = {r.rid: r for r in Server(GpuChainExecutor(leaf=16, precision="tf32x3",
+                                                     asynchronous=False),
+                                    budget_bytes=8 << 30).run(_requests())}
+    for rid in ref:
+        assert torch.equal(got[rid].result, ref[rid].result)
 
 
 def test_one_squaring_matches_the_oracle():
