@@ -257,7 +257,7 @@ class GpuChainExecutor:
         return handle.query()
 
     def idle(self) -> None:
-        time.sleep(2e-5)
+        pass                                  # poll the event again at once
 
     def collect(self, handle, reqs):
         """Statuses of the finished batch (rerun checked if a pool
@@ -272,7 +272,9 @@ class GpuChainExecutor:
             self._run(reqs, checked=True)     # raises on anything but overflow
             st = self.ctx.stats()
         self._scratch = max(self._scratch, int(st["pool_bytes"]))
-        self._note_device_use()
+        self._collected = getattr(self, "_collected", 0) + 1
+        if self._collected % 8 == 1:
+            self._note_device_use()
         flops = [f for f in self.ctx.per_product_flops(len(reqs))]
         for r in reqs:
             s = r.state
