@@ -166,6 +166,16 @@ spamm_status spamm_set_stream(spamm_ctx *ctx, void *stream);
 /* Switch checked mode (see spamm_config.checked) on or off. */
 spamm_status spamm_set_checked(spamm_ctx *ctx, int32_t checked);
 
+/* Bound of the tensor-core leaf kernel's pipeline waits (each wait for a
+ * stage of operands, for shared memory to refill, or for a TMEM
+ * accumulator), in nanoseconds; wait_ns <= 0 restores the default of one
+ * second.  A wait that runs out makes the kernel give up: it raises the
+ * context's TIMEOUT status, lets the copies and MMAs it issued complete,
+ * frees its tensor memory and returns, so the context stays usable; C is
+ * not valid after a TIMEOUT.  A short bound exists for failure-detection
+ * tests (a wait that nothing satisfies in time), not for production use. */
+spamm_status spamm_set_wait_limit(spamm_ctx *ctx, int64_t wait_ns);
+
 /* Grow the triple pool to at least pool_bytes (never shrinks).  Synchronises
  * the stream when it reallocates.  OOM, INVALID_ARG (negative size). */
 spamm_status spamm_reserve(spamm_ctx *ctx, int64_t pool_bytes);

@@ -226,6 +226,10 @@ class Context:
     def reserve(self, pool_bytes: int):
         spamm_reserve(self.handle, pool_bytes)
 
+    def set_wait_limit(self, wait_ns: int):
+        """Bound of the leaf kernel's pipeline waits (ns; 0 = the default 1 s)."""
+        _abi.check(_abi.lib().spamm_set_wait_limit(self.handle, int(wait_ns)), self.handle)
+
     def stats(self, raise_on_error: bool = True) -> dict:
         return _stats_dict(spamm_stats(self.handle, raise_on_error))
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "spamm_set_stream": (_i32, [_vp, _vp]),
     "spamm_set_checked": (_i32, [_vp, _i32]),
     "spamm_reserve": (_i32, [_vp, _i64]),
+    "spamm_set_wait_limit": (_i32, [_vp, _i64]),
     "spamm_last_error": (ctypes.c_char_p, [_vp]),
     "spamm_build_norms": (_i32, [_vp, _vp, _i64, _i64, ctypes.POINTER(_vp)]),
     "spamm_tree_rebuild": (_i32, [_vp, _vp, _vp, _i64]),

@@ -77,7 +77,12 @@ constexpr int kEpiWarps = 8;
 constexpr int kChunkIters = 16;  // K-chunks of 16 per TMEM accumulation chunk
 constexpr int kGroupRows = 12;  // tile rows walked together (L2 reuse)
 constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: default bound of the waits
+
+// The bound of the pipeline's waits, set per launch (spamm_set_wait_limit;
+// kWaitNs unless a failure-detection test shortens it).  The drains at the
+// end of a block always allow kWaitNs.
+
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -123,22 +128,35 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
-// Bounded wait: true when the phase completed, false after a timeout (or
+// Bounded wait: true when the phase completed, false after limit_ns (or
 // when another role already gave up).
 __device__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                         unsigned int* status) {
+                         unsigned int* status, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (gtimer() - t0 > kWaitNs) {
+        if (gtimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, ST_TIMEOUT);
             return false;
         }
     }
+}
+
+// A drain before the block frees its resources: waits out the phase whether
+// or not another role gave up, for at most kWaitNs.
+__device__ bool wait_drain(uint32_t bar, uint32_t parity, unsigned int* status) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtimer() - t0 > kWaitNs) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
@@ -294,6 +312,7 @@ struct TcBatch {
     int first;             // first work item of this launch (0 but for banded launches)
     int total;             // work items (tiles) of all products; this launch ends here
     unsigned int* status;  // timeout status word
+    unsigned long long wait_ns;  // bound of the pipeline's waits
 };
 
 // BAND: at least one operand of the batch is sparsified; its pieces are
@@ -446,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 if (fill == 0) {
                     s = (int)(stage_it % ST);
                     const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
-                    ok = wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status);
+                    ok = wait_bar(smem_u32(&bar_empty[s]), ph ^ 1, &abort_flag, status, bt.wait_ns);
                 }
                 if (!ok) return;
                 const uint32_t full = smem_u32(&bar_full[s]);
@@ -689,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                 while (i < iters && ok) {
                     const int s = (int)(stage_it % ST);
                     const uint32_t ph = (uint32_t)((stage_it / ST) & 1);
-                    if (!wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status)) {
+                    if (!wait_bar(smem_u32(&bar_full[s]), ph, &abort_flag, status, bt.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -821,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     // wait until the epilogue has drained the buffer, clear it
                     auto open_chunk = [&]() -> bool {
                         const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
-                        if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status))
+                        if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status, bt.wait_ns))
                             return false;
                         tc_fence_after();
                         dacc = tmem + ab * 256;
@@ -879,7 +898,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             }
             // drain: every MMA issued so far has completed before TMEM is freed
             tc_commit(smem_u32(&bar_drain));
-            wait_bar(smem_u32(&bar_drain), 0, &abort_flag, status);
+            wait_drain(smem_u32(&bar_drain), 0, status);
         }
         __syncwarp();
     } else {
@@ -932,7 +951,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             for (uint32_t c = 0; c < nch; ++c, ++ccount) {
                 const uint32_t ab = ccount & 1;
                 const uint32_t aph = (ccount >> 1) & 1;
-                if (!wait_bar(smem_u32(&bar_accf[ab]), aph, &abort_flag, status)) {
+                if (!wait_bar(smem_u32(&bar_accf[ab]), aph, &abort_flag, status, bt.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -1048,6 +1067,7 @@ static bool fill_batch(spamm_ctx* ctx, const LeafJob* jobs, int count, TcBatch& 
     memset(&bt, 0, sizeof(bt));
     bt.count = count;
     bt.status = &ctx->ctl->status;
+    bt.wait_ns = ctx->wait_ns > 0 ? (unsigned long long)ctx->wait_ns : kWaitNs;
     int base = 0;
     bool band = false;
     for (int i = 0; i < bt.count; ++i) {

@@ -268,6 +268,12 @@ spamm_status spamm_set_checked(spamm_ctx* ctx, int32_t checked) {
     return SPAMM_OK;
 }
 
+spamm_status spamm_set_wait_limit(spamm_ctx* ctx, int64_t wait_ns) {
+    if (!ctx) return SPAMM_ERR_INVALID_ARG;
+    ctx->wait_ns = wait_ns > 0 ? wait_ns : 0;
+    return SPAMM_OK;
+}
+
 spamm_status spamm_reserve(spamm_ctx* ctx, int64_t pool_bytes) {
     if (!ctx || pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
     if (pool_bytes <= ctx->pool_words * 8) return SPAMM_OK;

@@ -274,6 +274,8 @@ struct spamm_ctx {
     cudaStream_t hi;
     cudaEvent_t hi_ev;
     bool aux_ready;
+    // bound of the leaf kernel's pipeline waits in ns (0: the default 1 s)
+    int64_t wait_ns;
     std::string err;
 };
 
