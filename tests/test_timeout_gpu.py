@@ -4,7 +4,6 @@ give up cleanly (TIMEOUT status, its copies and MMAs drained, tensor memory
 freed, the context still usable).  The test shortens the bound to 1 ns, so
 the first wait that is not satisfied at once runs out; nothing here faults
 or hangs the GPU."""
-import numpy as np
 import pytest
 
 import spamm_inputs as gen
@@ -38,4 +37,3 @@ def test_short_wait_bound_gives_timeout_and_the_context_recovers(prec, b, bits):
     # and the device is healthy for other work
     x = torch.ones(1024, device="cuda")
     assert float(x.sum()) == 1024.0
-    del np
