@@ -76,6 +76,7 @@ constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kChunkIters = 16;  // K-chunks of 16 per TMEM accumulation chunk
 constexpr int kGroupRows = 12;  // tile rows walked together (L2 reuse)
+constexpr int kTQ = 16;         // tile-queue entries (producer -> MMA and epilogue)
 constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: default bound of the waits
 
@@ -313,6 +314,7 @@ struct TcBatch {
     int total;             // work items (tiles) of all products; this launch ends here
     unsigned int* status;  // timeout status word
     unsigned long long wait_ns;  // bound of the pipeline's waits
+    unsigned int* ctr;     // work-item counter of the launch (zero at its start)
 };
 
 // BAND: at least one operand of the batch is sparsified; its pieces are
@@ -346,6 +348,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
     __shared__ unsigned long long st_hmask[ST][U][2];
     __shared__ uint32_t st_count[ST];                        // groups of each stage
     __shared__ volatile int abort_flag;
+    // work items in the order the producer took them: full (id written) and
+    // empty (taken by the MMA thread and every epilogue warp) barriers
+    __shared__ int tq_id[kTQ];
+    __shared__ __align__(8) uint64_t bar_tqf[kTQ], bar_tqe[kTQ];
     __shared__ unsigned long long issued_s, consumed_s;
     // per product: step-list offsets in its pool, skip flag, end of its work
     // items.  Everything else is read from the parameter space: pointers that
@@ -386,6 +392,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             mbar_init(smem_u32(&bar_acce[b]), kEpiWarps);
         }
         mbar_init(smem_u32(&bar_drain), 1);
+        for (int t = 0; t < kTQ; ++t) {
+            mbar_init(smem_u32(&bar_tqf[t]), 1);
+            mbar_init(smem_u32(&bar_tqe[t]), 1 + kEpiWarps);
+        }
         abort_flag = 0;
         issued_s = consumed_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -423,7 +433,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         bool ok = true;
         const size_t piece = (size_t)LEAF * 16 * T::kEsize;
         int pi = 0;
-        for (int k = bt.first + blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+        uint32_t tq = 0;   // work items handed on
+        while (ok) {
+            // the next work item from the launch's counter (items are taken
+            // in ascending order, so tiles in flight on all SMs stay close),
+            // handed to the MMA thread and the epilogue through the queue;
+            // -1 ends the launch
+            int k = -1;
+            if (lane == 0) {
+                const int w = (int)atomicAdd(bt.ctr, 1u) + bt.first;
+                k = w < bt.total ? w : -1;
+                const int slot = (int)(tq % kTQ);
+                const uint32_t tph = (tq / kTQ) & 1;
+                ok = wait_bar(smem_u32(&bar_tqe[slot]), tph ^ 1, &abort_flag, status, bt.wait_ns);
+                if (ok) {
+                    tq_id[slot] = k;
+                    mbar_arrive(smem_u32(&bar_tqf[slot]));
+                }
+            }
+            k = __shfl_sync(0xffffffffu, k, 0);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            ++tq;
+            if (k < 0 || !ok) break;
             product_of(k, pi);
             if (sp_skip[pi]) continue;
             const TcProd& q = bt.prods[pi];
@@ -698,7 +729,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
             uint32_t dacc = tmem;
             int pi = 0;
-            for (int k = bt.first + blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+            uint32_t tq = 0;
+            while (ok) {
+                const int slot = (int)(tq % kTQ);
+                const uint32_t tph = (tq / kTQ) & 1;
+                if (!wait_bar(smem_u32(&bar_tqf[slot]), tph, &abort_flag, status, bt.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                const int k = tq_id[slot];
+                mbar_arrive(smem_u32(&bar_tqe[slot]));
+                ++tq;
+                if (k < 0) break;
                 product_of(k, pi);
                 if (sp_skip[pi]) continue;
                 const TcProd& q = bt.prods[pi];
@@ -908,7 +950,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         uint32_t ccount = 0;
         bool ok = true;
         int pi = 0;
-        for (int k = bt.first + blockIdx.x; k < bt.total && ok; k += gridDim.x) {
+        uint32_t tq = 0;
+        while (ok) {
+            const int slot = (int)(tq % kTQ);
+            const uint32_t tph = (tq / kTQ) & 1;
+            int k = -1;
+            bool got = true;
+            if (lane == 0) {
+                got = wait_bar(smem_u32(&bar_tqf[slot]), tph, &abort_flag, status, bt.wait_ns);
+                if (got) k = tq_id[slot];
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (!got) {
+                ok = false;
+                break;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_tqe[slot]));
+            ++tq;
+            if (k < 0) break;
             product_of(k, pi);
             if (sp_skip[pi]) continue;
             const TcProd& q = bt.prods[pi];
@@ -1068,6 +1129,7 @@ static bool fill_batch(spamm_ctx* ctx, const LeafJob* jobs, int count, TcBatch& 
     bt.count = count;
     bt.status = &ctx->ctl->status;
     bt.wait_ns = ctx->wait_ns > 0 ? (unsigned long long)ctx->wait_ns : kWaitNs;
+    bt.ctr = &ctx->ctl->tile_ctr;
     int base = 0;
     bool band = false;
     for (int i = 0; i < bt.count; ++i) {
@@ -1118,7 +1180,9 @@ static bool fill_batch(spamm_ctx* ctx, const LeafJob* jobs, int count, TcBatch& 
 static cudaError_t dispatch(spamm_ctx* ctx, const TcBatch& bt, bool band) {
     const int p = ctx->cfg.precision;
     const int b = ctx->cfg.leaf;
-    cudaError_t e;
+    // every launch deals its work items out from a counter that starts at zero
+    cudaError_t e = cudaMemsetAsync(bt.ctr, 0, sizeof(unsigned int), ctx->stream);
+    if (e != cudaSuccess) return e;
     if (b == 16) {
         if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band);
         else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band);

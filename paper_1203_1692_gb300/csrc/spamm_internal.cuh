@@ -69,7 +69,7 @@ struct DevCtl {
     unsigned long long clip_vol;    // sum over kept products of rows x k x columns inside
                                     // the n x n matrices
     unsigned int status;
-    unsigned int pad;
+    unsigned int tile_ctr;          // work items taken by the blocks of the running leaf launch
 };
 
 // Words stored for tier t (a frontier that overflowed is truncated).
