@@ -74,7 +74,7 @@ namespace {
 
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
-constexpr int kChunkIters = 16;  // K-chunks of 16 per TMEM accumulation chunk
+constexpr int kChunkIters = 32;  // K-chunks of 16 per TMEM accumulation chunk
 constexpr int kGroupRows = 12;  // tile rows walked together (L2 reuse)
 constexpr int kTQ = 16;         // tile-queue entries (producer -> MMA and epilogue)
 constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
