@@ -94,7 +94,13 @@ typedef struct {
                               SPAMM_PREC_BF16X3), so tier_bits = p - 1 keeps
                               each such product's error near tau, like a
                               culled one.  Split precisions only. */
-    int32_t reserved[5];   /* must be zero */
+    int32_t staged;        /* 0 (default): an FP32 product of at most 128 leaves
+                              per side runs its cull, grouping and leaf
+                              products fused in one launch (the same triples,
+                              statistics and C as the staged launches);
+                              1: always the staged launches (one per tier
+                              and stage, with per-stage timings) */
+    int32_t reserved[4];   /* must be zero */
 } spamm_config;
 
 /* Fill *cfg with the defaults: leaf 16, SPAMM_PREC_FP32, tie_rel 1e-6,

@@ -124,12 +124,13 @@ class Context:
 
     def __init__(self, leaf: int = 16, precision: str = "fp32", tie_rel: float = 1e-6,
                  pool_bytes: int = 0, checked: bool = True, stream=None, slice: int = 0,
-                 tier_bits: int = 0):
+                 tier_bits: int = 0, staged: bool = False):
         torch = _torch()
         cfg = spamm_config_default()
         cfg.leaf = leaf
         cfg.slice = slice
         cfg.tier_bits = tier_bits
+        cfg.staged = 1 if staged else 0
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.tie_rel = tie_rel
         cfg.pool_bytes = pool_bytes

@@ -37,7 +37,8 @@ class spamm_config(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tie_rel", ctypes.c_double), ("pool_bytes", ctypes.c_int64),
                 ("checked", ctypes.c_int32), ("slice", ctypes.c_int32),
-                ("tier_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("tier_bits", ctypes.c_int32), ("staged", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class spamm_stats_t(ctypes.Structure):

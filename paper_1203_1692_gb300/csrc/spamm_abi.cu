@@ -181,8 +181,9 @@ spamm_status spamm_create(spamm_ctx** out, void* stream, const spamm_config* cfg
     if (!valid_leaf(c.leaf)) return SPAMM_ERR_INVALID_ARG;
     if (c.precision < SPAMM_PREC_FP32 || c.precision > SPAMM_PREC_F16X3) return SPAMM_ERR_INVALID_ARG;
     if (!(c.tie_rel >= 0.0 && c.tie_rel < 0.5) || c.pool_bytes < 0) return SPAMM_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (c.reserved[i]) return SPAMM_ERR_INVALID_ARG;
+    if (c.staged != 0 && c.staged != 1) return SPAMM_ERR_INVALID_ARG;
     if (c.tier_bits < 0 || c.tier_bits > 40) return SPAMM_ERR_INVALID_ARG;
     if (c.tier_bits && !split_precision(c.precision)) return SPAMM_ERR_INVALID_ARG;
     if (c.slice != 0 && c.slice != 16) return SPAMM_ERR_INVALID_ARG;
@@ -557,6 +558,18 @@ static spamm_status launch_multiply_once(spamm_ctx* ctx, const spamm_tree* A,
     const bool tc = precision_uses_tc(ctx->cfg.precision);
     cudaError_t e = cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], s);
+    ctx->last_small = small_path(ctx, A);
+    if (ctx->last_small) {
+        // one launch: cull, grouping and FP32 leaf products of a small product
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], s);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s);
+        if (e == cudaSuccess) e = launch_small_fp32(ctx, A, B, tau, alpha, beta, C, ldc);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2], s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s);
+        ctx->timed = (e == cudaSuccess);
+        return cuda_err(ctx, e, "multiply launch");
+    }
     const int tt = tile_tier(A);
     if (tc) {
         // fork: cull + grouping on ctx->hi, packs on the context stream, join
@@ -726,7 +739,9 @@ static spamm_status expand_triples(spamm_ctx* ctx, int32_t* host_out, int64_t ca
     const int64_t tiles = ctx->last_tiles;
     const int tc = ctx->last_tc;
     const int tl = kTileRows / ctx->last_b;
-    const uint64_t msteps = (uint64_t)c.tier_count[ctx->last_tt] * ctx->last_S;
+    // the fused small path lists every tile's steps in a slot per leaf column
+    const uint64_t msteps = ctx->last_small ? (uint64_t)tiles * ((uint64_t)1 << ctx->last_d)
+                                            : (uint64_t)c.tier_count[ctx->last_tt] * ctx->last_S;
     std::vector<uint32_t> off((size_t)tiles + 1), nst((size_t)tiles), pk((size_t)msteps);
     std::vector<uint64_t> pm((size_t)(2 * msteps * SL));
     e = cudaMemcpy(off.data(), ctx->tile_off, sizeof(uint32_t) * (tiles + 1), cudaMemcpyDeviceToHost);

@@ -276,6 +276,9 @@ struct spamm_ctx {
     bool aux_ready;
     // bound of the leaf kernel's pipeline waits in ns (0: the default 1 s)
     int64_t wait_ns;
+    // the last multiply ran the fused small-product path (its step list
+    // holds one slot per tile and leaf column)
+    bool last_small;
     std::string err;
 };
 
@@ -333,6 +336,11 @@ cudaError_t launch_pyramid(spamm_tree* t, cudaStream_t s);
 // leaf_simt.cu
 cudaError_t launch_leaf_simt(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                              float alpha, float beta, float* C, int64_t ldc);
+// The fused small-product path (leaf_simt.cu): FP32 products of at most 128
+// leaves per side run their cull, grouping and leaf products in one launch.
+bool small_path(const spamm_ctx* ctx, const spamm_tree* A);
+cudaError_t launch_small_fp32(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, double tau,
+                              float alpha, float beta, float* C, int64_t ldc);
 // leaf_tc.cu
 cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                            float alpha, float beta, float* C, int64_t ldc);
