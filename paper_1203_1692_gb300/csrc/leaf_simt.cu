@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(256) k_small_fp32(SmallArgs a) {
             a.ctl->tier_cand[0] = 1;
             a.ctl->tier_count[0] = k0 ? 1 : 0;
             tie += tb ? 1 : 0;
+            if (k0 && a.d == 0) vol += ext(0) * ext(0) * ext(0);   // the root is the leaf
         }
         for (int t = 1; t <= a.d; ++t) {
             const int64_t w = (int64_t)1 << t, wp = w >> 1;
