@@ -919,14 +919,14 @@ def run_sparse(args, P, dev, rank, world, dist):
     st_dense = ctx.stats()
     dense_tree.close()
     torch.cuda.empty_cache()
-    holder = {}
+    # one sparsified tree, re-sparsified in place every step: its storage is
+    # reused once the bands have settled
+    holder = {"t": ctx.sparsify(A, tau, 0.0)}
 
     def sparse_step():
-        t = ctx.sparsify(A, tau, 0.0)
+        t = holder["t"]
+        t.resparsify(A, tau, 0.0)
         ctx.multiply(t, t, tau, C=C_sparse)
-        if "t" in holder:
-            holder["t"].close()
-        holder["t"] = t
 
     clocks = Clocks(dev.index or 0)
     clocks.start()

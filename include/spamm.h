@@ -230,12 +230,27 @@ spamm_status spamm_tree_rebuild_batched(spamm_ctx *ctx, int32_t count, spamm_tre
  * squared Frobenius norm this is the paper's epsilon = tau / max(||A||_F,
  * ||B||_F), and spamm_multiply of two trees sparsified at that tau keeps
  * exactly the leaf products of the dense trees (a dropped leaf's product
- * with any leaf is below tau) and gives the same C.  The tree does not
- * reference A after the call (synchronises).  Tensor-core precisions only;
- * spamm_tree_rebuild does not apply (UNSUPPORTED).  INVALID_ARG,
- * NONFINITE, UNSUPPORTED, OOM, CUDA. */
+ * with any leaf is below tau) and gives the same C.  The tree keeps no
+ * reference to A: the call synchronises once (to size the bands) and then
+ * queues the copy of the kept leaves on ctx's stream, so A must stay
+ * unchanged until that stream has passed the call (stream-ordered reuse of
+ * A is safe).  Tensor-core precisions only; spamm_tree_rebuild does not
+ * apply (UNSUPPORTED).  INVALID_ARG, NONFINITE, UNSUPPORTED, OOM, CUDA. */
 spamm_status spamm_sparsify(spamm_ctx *ctx, const float *A, int64_t n, int64_t lda, double tau,
                             double partner_norm2, spamm_tree **out);
+
+/* spamm_sparsify into an existing sparsified tree of this context and
+ * configuration, for new contents A of the same n (lda >= n): the tree's
+ * device storage is reused whenever the new bands fit in it and grown by a
+ * quarter beyond the need when they do not, so re-sparsifying in a loop
+ * (Sec. IV's purification iterations) allocates nothing once the bands have
+ * settled.  tau and partner_norm2 may differ from the tree's first call.
+ * On an error the tree's root norm is left non-finite, so every multiply
+ * with it reports NONFINITE until a later spamm_sparsify_into succeeds.
+ * INVALID_ARG (NULL, a dense tree, another context or configuration),
+ * NONFINITE, OOM, CUDA. */
+spamm_status spamm_sparsify_into(spamm_ctx *ctx, spamm_tree *tree, const float *A, int64_t lda,
+                                 double tau, double partner_norm2);
 
 /* Device bytes a tree holds, and for a sparsified tree the number of kept
  * leaves (-1 for a dense tree). */

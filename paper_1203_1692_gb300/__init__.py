@@ -102,6 +102,15 @@ class Tree:
         self.A = A
         spamm_tree_rebuild(self.ctx.handle, self.handle, A.data_ptr(), lda)
 
+    def resparsify(self, A, tau: float, partner_norm2: float = 0.0):
+        """Sparsify new contents A (same n) into this sparsified tree, reusing
+        its device storage while the new bands fit."""
+        n, lda = _check_matrix(A)
+        if n != self.n:
+            raise ValueError("resparsify needs the same n")
+        _abi.spamm_sparsify_into(self.ctx.handle, self.handle, A.data_ptr(), lda, tau,
+                                 partner_norm2)
+
     def norms(self) -> np.ndarray:
         out = np.empty(self.nodes, dtype=np.float64)
         spamm_tree_norms(self.ctx.handle, self.handle, out.ctypes.data, self.nodes)

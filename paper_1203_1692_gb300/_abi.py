@@ -84,6 +84,7 @@ SIGNATURES = {
     "spamm_tree_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "spamm_tree_footprint": (_i32, [_vp, _i64, ctypes.POINTER(_i64)]),
     "spamm_sparsify": (_i32, [_vp, _vp, _i64, _i64, _dbl, _dbl, ctypes.POINTER(_vp)]),
+    "spamm_sparsify_into": (_i32, [_vp, _vp, _vp, _i64, _dbl, _dbl]),
     "spamm_tree_bytes": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "spamm_tree_norms": (_i32, [_vp, _vp, _vp, _i64]),
     "spamm_multiply": (_i32, [_vp, _vp, _vp, _dbl, _flt, _flt, _vp, _i64]),
@@ -205,6 +206,11 @@ def spamm_sparsify(ctx, A_ptr: int, n: int, lda: int, tau: float, partner_norm2:
     check(lib().spamm_sparsify(ctx, _vp(A_ptr), n, lda, float(tau), float(partner_norm2),
                                ctypes.byref(h)), ctx)
     return h
+
+
+def spamm_sparsify_into(ctx, tree, A_ptr: int, lda: int, tau: float, partner_norm2: float):
+    check(lib().spamm_sparsify_into(ctx, tree, _vp(A_ptr), lda, float(tau),
+                                    float(partner_norm2)), ctx)
 
 
 def spamm_tree_bytes(tree):

@@ -77,7 +77,6 @@ constexpr int kEpiWarps = 8;
 constexpr int kChunkIters = 32;  // K-chunks of 16 per TMEM accumulation chunk
 constexpr int kGroupRows = 12;  // tile rows walked together (L2 reuse)
 constexpr int kTQ = 16;         // tile-queue entries (producer -> MMA and epilogue)
-constexpr uint32_t kZeroBytes = 8192;  // zero A (128 rows) and B (256 rows) operands
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: default bound of the waits
 
 // The bound of the pipeline's waits, set per launch (spamm_set_wait_limit;
@@ -247,6 +246,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Zero 32 lanes x 32 columns of tensor memory (this warp's lane quarter).
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};"
+        ::"r"(taddr), "r"(0u)
+        : "memory");
+}
+
 template <int PREC>
 struct PrecTraits {
     static constexpr bool k16 = PREC == SPAMM_PREC_BF16X3 || PREC == SPAMM_PREC_F16X3;
@@ -363,8 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
 
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* zero = base;
-    unsigned char* stages = base + kZeroBytes;
+    unsigned char* stages = base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned int* status = bt.status;
     for (int i = threadIdx.x; i < bt.count; i += kThreads) {
@@ -379,9 +387,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             sp_uns[i] = f16_unscale(g.gmax[0], g.gmax[1]);
     }
 
-    for (int i = threadIdx.x; i < (int)(kZeroBytes / 16); i += kThreads)
-        reinterpret_cast<uint4*>(zero)[i] = make_uint4(0, 0, 0, 0);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
@@ -725,7 +730,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
             unsigned long long stage_it = 0;
             uint32_t ccount = 0;  // chunks opened so far (selects the TMEM buffer)
             bool ok = true;
-            const uint64_t zdesc = make_desc(smem_u32(zero), 128, 256);
             const uint32_t dis0[4] = {0u, 0u, 0u, 0u};
             uint32_t dacc = tmem;
             int pi = 0;
@@ -879,15 +883,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                         }
                     };
                     // a new TMEM chunk at every kChunkIters-th K-chunk of a tile:
-                    // wait until the epilogue has drained the buffer, clear it
+                    // wait until the epilogue has drained the buffer and left
+                    // it zero (use k of a buffer waits for the (k+1)-th phase of
+                    // its barrier: the first is the zeroing at the start)
                     auto open_chunk = [&]() -> bool {
                         const uint32_t ab = ccount & 1, aph = (ccount >> 1) & 1;
-                        if (!wait_bar(smem_u32(&bar_acce[ab]), aph ^ 1, &abort_flag, status, bt.wait_ns))
+                        if (!wait_bar(smem_u32(&bar_acce[ab]), aph, &abort_flag, status, bt.wait_ns))
                             return false;
                         tc_fence_after();
                         dacc = tmem + ab * 256;
-                        // clear the chunk accumulator: 0 * 0, input accumulator off
-                        mma<PREC>(dacc, zdesc, zdesc, make_idesc(T::kAB, 128, 256), dis0, 0u);
                         return true;
                     };
                     // Groups in stage order.  Consecutive groups with the same
@@ -947,6 +951,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
         // ---------------------------------------------------------- epilogue
         const int qq = warp & 3;                 // TMEM lane quarter this warp may access
         const int hcol = (warp - 2) >> 2;        // which 128 columns of the 256
+        // both chunk buffers start at zero (the MMAs accumulate onto them)
+        for (uint32_t ab = 0; ab < 2; ++ab) {
+            const uint32_t taddr =
+                tmem + ((uint32_t)(qq * 32) << 16) + ab * 256 + (uint32_t)(hcol * 128);
+#pragma unroll
+            for (int cc = 0; cc < 128; cc += 32) tmem_zero32(taddr + (uint32_t)cc);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(smem_u32(&bar_acce[0]));
+            mbar_arrive(smem_u32(&bar_acce[1]));
+        }
         uint32_t ccount = 0;
         bool ok = true;
         int pi = 0;
@@ -1025,7 +1043,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
                     tmem_ld32(taddr + (uint32_t)cc, r);
 #pragma unroll
                     for (int v = 0; v < 32; ++v) master[cc + v] += __uint_as_float(r[v]);
+                    tmem_zero32(taddr + (uint32_t)cc);   // ready for the buffer's next chunk
                 }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
@@ -1104,7 +1124,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
 template <int LEAF, int PREC, bool BAND>
 cudaError_t launch_b(spamm_ctx* ctx, const TcBatch& bt) {
     using T = PrecTraits<PREC>;
-    const size_t smem = 1024 + kZeroBytes + (size_t)T::kStages * T::kStage;
+    const size_t smem = 1024 + (size_t)T::kStages * T::kStage;
     cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, PREC, BAND>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -425,7 +425,15 @@ __global__ void __launch_bounds__(pack_threads<LEAF>()) k_leaf_pack(const float*
         const int rg = w / (8 * CPC), core = (w / 8) % CPC, rr = w % 8;
         const int prow = rg * 8 + rr;                    // row of the piece (b of them)
         // ---- A role: piece (leaf xa, chunk kca): rows = i, k contiguous
-        if (pa0 && needA[pc / CH]) {
+        bool roleA = pa0 && needA[pc / CH];
+        if constexpr (BAND) {
+            // a kept leaf lies inside its band; the test keeps every store
+            // inside the tree's storage even for norms that do not match the
+            // bands (a tree left by a failed re-sparsify)
+            const int64_t K = Q0 + pc / CH;
+            if (roleA && (I < bv.imin[K] || I > bv.imax[K])) roleA = false;
+        }
+        if (roleA) {
             const int xa = pc / CH, kca = pc % CH;
             const float* src = &raw[prow][xa * LEAF + kca * 16 + core * EPU];
             size_t g;
@@ -467,6 +475,7 @@ __global__ void __launch_bounds__(pack_threads<LEAF>()) k_leaf_pack(const float*
             const int k0 = kcb * 16 + core * EPU;        // staged first row
             size_t g;
             if constexpr (BAND) {
+                if (Q0 + xb < bv.kmin[I] || Q0 + xb > bv.kmax[I]) continue;   // as for A
                 const int64_t len = bv.kmax[I] - bv.kmin[I] + 1;
                 g = (size_t)(bv.boff[I] + kcb * len + (Q0 + xb - bv.kmin[I])) * PIECE +
                     (size_t)w * 16;
@@ -591,17 +600,28 @@ cudaError_t launch_pyramid(spamm_tree* t, cudaStream_t s) {
 
 // ------------------------------------------------------- sparsification
 // A leaf is kept iff its squared norm passes the SpAMM test against
-// norm2_max, the largest squared Frobenius norm it can meet in a product
-// (the paper's drop tolerance epsilon = tau / max ||.||_F in squared form);
-// a dropped leaf's norm and panel norms become zero, so no cull ever keeps
-// it.  Then the bands of the kept leaves: per leaf row I the first and last
-// kept column (kmin, kmax), per leaf column K the first and last kept row
-// (imin, imax); an empty band has min > max.
-__global__ void __launch_bounds__(256) k_sparse_mark(double* __restrict__ leaf, int64_t nb,
-                                                     int64_t nl, Thresh th, double norm2_max,
-                                                     int SL, double* __restrict__ panA,
+// norm2_max = max(||A||_F^2, partner_norm2), the largest squared Frobenius
+// norm it can meet in a product (the paper's drop tolerance epsilon =
+// tau / max ||.||_F in squared form); a dropped leaf's norm and panel norms
+// become zero, so no cull ever keeps it.  Then the bands of the kept
+// leaves: per leaf row I the first and last kept column (kmin, kmax), per
+// leaf column K the first and last kept row (imin, imax); an empty band has
+// min > max.  The dense root is read before any leaf changes (it is the leaf
+// when d = 0) and recorded in out[1]; a non-finite root drops nothing, so
+// the rebuilt tiers keep the Inf/NaN and a multiply reports it.  out[0]
+// counts the kept leaves.
+__global__ void __launch_bounds__(256) k_sparse_mark(double* leaf, int64_t nb,
+                                                     int64_t nl, Thresh th,
+                                                     const double* root,   // may be the leaf
+                                                     double partner_norm2, int SL,
+                                                     double* __restrict__ panA,
                                                      double* __restrict__ panB,
-                                                     unsigned long long* __restrict__ stored) {
+                                                     unsigned long long* __restrict__ out) {
+    const double r = *root;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[1] = __double_as_longlong(r);
+    if (!isfinite(r)) return;
+    const double norm2_max = fmax(r, partner_norm2);
+    __syncthreads();   // every thread of block 0 has read the root before a leaf changes
     unsigned long long kept = 0;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nl * nl;
          g += (int64_t)gridDim.x * blockDim.x) {
@@ -618,59 +638,52 @@ __global__ void __launch_bounds__(256) k_sparse_mark(double* __restrict__ leaf, 
         }
     }
     for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(stored, kept);
+    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(out, kept);
 }
 
-// blockIdx.y = 0: a warp per leaf row (kmin, kmax); 1: a thread per leaf
-// column (imin, imax).
+// A warp per leaf row (blockIdx.y = 0: kmin, kmax) or per leaf column
+// (blockIdx.y = 1: imin, imax; strided loads, but every column in flight at
+// once rather than one latency-bound walk down each column).
 __global__ void __launch_bounds__(256) k_bands(const double* __restrict__ leaf, int64_t nb,
                                                int64_t nl, int32_t* __restrict__ band) {
     const int lane = threadIdx.x & 31;
-    if (blockIdx.y == 0) {
-        const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-        for (int64_t I = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); I < nl;
-             I += warps) {
-            int lo = (int)nl, hi = -1;
-            for (int64_t K = lane; K < nl; K += 32)
-                if (leaf[I * nb + K] > 0.0) {
-                    lo = min(lo, (int)K);
-                    hi = max(hi, (int)K);
-                }
-            for (int o = 16; o > 0; o >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    const bool rows = blockIdx.y == 0;
+    // leaf (L, q) of line L: row L's leaf column q, or column L's leaf row q
+    const int64_t s_line = rows ? nb : 1, s_q = rows ? 1 : nb;
+    int32_t* lo_out = band + (rows ? 0 : 2 * nl);
+    int32_t* hi_out = lo_out + nl;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t L = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); L < nl;
+         L += warps) {
+        int lo = (int)nl, hi = -1;
+        for (int64_t q = lane; q < nl; q += 32)
+            if (leaf[L * s_line + q * s_q] > 0.0) {
+                lo = min(lo, (int)q);
+                hi = max(hi, (int)q);
             }
-            if (lane == 0) {
-                band[I] = lo;
-                band[nl + I] = hi;
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
-    } else {
-        for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < nl;
-             K += (int64_t)gridDim.x * blockDim.x) {
-            int lo = (int)nl, hi = -1;
-            for (int64_t I = 0; I < nl; ++I)
-                if (leaf[I * nb + K] > 0.0) {
-                    lo = min(lo, (int)I);
-                    hi = max(hi, (int)I);
-                }
-            band[2 * nl + K] = lo;
-            band[3 * nl + K] = hi;
+        if (lane == 0) {
+            lo_out[L] = lo;
+            hi_out[L] = hi;
         }
     }
 }
 
-cudaError_t launch_sparsify_mark(spamm_tree* t, double tau, double norm2_max, double rel,
-                                 int32_t* band, unsigned long long* stored, cudaStream_t s) {
+cudaError_t launch_sparsify_mark(spamm_tree* t, double tau, double partner_norm2, double rel,
+                                 int32_t* band, unsigned long long* out, cudaStream_t s) {
     const int64_t off_leaf = (((int64_t)1 << (2 * t->d)) - 1) / 3;
     double* leaf = t->pyr + off_leaf;
     const Thresh th = make_thresh(tau, rel);
     const int64_t m = t->nl * t->nl;
     const int blocks = (int)std::min<int64_t>((m + 255) / 256, 4096);
-    cudaError_t e = cudaMemsetAsync(stored, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_sparse_mark<<<std::max(blocks, 1), 256, 0, s>>>(leaf, t->nb, t->nl, th, norm2_max,
-                                                      t->slices, t->panA, t->panB, stored);
+    k_sparse_mark<<<std::max(blocks, 1), 256, 0, s>>>(leaf, t->nb, t->nl, th, t->pyr,
+                                                      partner_norm2, t->slices, t->panA,
+                                                      t->panB, out);
     const int bb = (int)std::max<int64_t>(1, std::min<int64_t>((t->nl + 7) / 8, 4096));
     k_bands<<<dim3(bb, 2), 256, 0, s>>>(leaf, t->nb, t->nl, band);
     e = cudaGetLastError();

@@ -109,9 +109,18 @@ void free_tree_storage(spamm_tree* t) {
     cudaFree(t->slab);
     cudaFree(t->band);
     cudaFree(t->offs);
+    cudaFree(t->band_new);
+    cudaFree(t->sdev);
+    cudaFreeHost(t->h_band);
+    cudaFreeHost(t->h_offs);
     t->slab = nullptr;
     t->band = nullptr;
     t->offs = nullptr;
+    t->band_new = nullptr;
+    t->sdev = nullptr;
+    t->h_band = nullptr;
+    t->h_offs = nullptr;
+    t->slab_cap = t->packa_cap = t->packb_cap = 0;
     for (int i = 0; i < 2; ++i) {
         cudaFree(t->packA[i]);
         cudaFree(t->packB[i]);
@@ -364,64 +373,64 @@ spamm_status spamm_build_norms(spamm_ctx* ctx, const float* A, int64_t n, int64_
     return SPAMM_OK;
 }
 
-spamm_status spamm_sparsify(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda, double tau,
-                            double partner_norm2, spamm_tree** out) {
-    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
-    *out = nullptr;
-    spamm_status st = check_matrix(ctx, A, n, lda);
-    if (st != SPAMM_OK) return st;
-    if (!(tau >= 0.0) || !std::isfinite(tau) || !(partner_norm2 >= 0.0) ||
-        !std::isfinite(partner_norm2))
-        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tau and partner_norm2 must be finite and >= 0");
-    if (!precision_uses_tc(ctx->cfg.precision))
-        return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "sparsified trees need a tensor-core precision");
-    spamm_tree* t = nullptr;
-    st = new_tree(ctx, A, n, lda, false, &t);
-    if (st != SPAMM_OK) return st;
-    auto fail = [&](cudaError_t e, const char* what) {
-        cudaStreamSynchronize(ctx->stream);
-        free_tree_storage(t);
-        delete t;
-        return cuda_err(ctx, e, what);
-    };
+// The sparsified storage of A in t (Sec. II.D): dense norms, the drop and
+// the bands on the device, one synchronisation to bring the bands to the
+// host, the slab and pack layout there, then the offsets, bands and slab
+// copy queued on the stream.  Storage already held is reused when the new
+// bands fit (grown a quarter beyond the need when they do not), so a
+// re-sparsify of a tree in a loop allocates nothing.  On any error the root
+// norm is left non-finite, so a multiply with the tree reports NONFINITE
+// before it reads bands, offsets or slab that no longer match its norms.
+static spamm_status sparsify_fill(spamm_ctx* ctx, spamm_tree* t, const float* A, int64_t lda,
+                                  double tau, double partner_norm2) {
     cudaStream_t s = ctx->stream;
     const int64_t nl = t->nl;
     const int b = t->b;
-    // 1. dense norms (and panels) of A, then its squared Frobenius norm
-    cudaError_t e = launch_build_norms(t, s);
-    double root = 0.0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&root, t->pyr, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(e, "sparsify norms");
-    if (!std::isfinite(root)) {
-        free_tree_storage(t);
-        delete t;
-        return set_err(ctx, SPAMM_ERR_NONFINITE, "an operand holds Inf or NaN");
+    const size_t nband = (size_t)4 * (size_t)std::max<int64_t>(nl, 1);
+    const size_t noffs = (size_t)(3 * nl + 2);
+    auto poison = [&](spamm_status st) {
+        // a NaN root: every multiply with this tree stops at its root test
+        cudaMemsetAsync(t->pyr, 0xff, sizeof(double), s);
+        return st;
+    };
+    cudaError_t e = cudaSuccess;
+    if (!t->band) {
+        e = cudaMalloc(&t->band, sizeof(int32_t) * nband);
+        if (e == cudaSuccess) e = cudaMalloc(&t->band_new, sizeof(int32_t) * nband);
+        if (e == cudaSuccess) e = cudaMalloc(&t->offs, sizeof(int64_t) * noffs);
+        if (e == cudaSuccess) e = cudaMalloc(&t->sdev, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&t->h_band, sizeof(int32_t) * nband + 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMallocHost(&t->h_offs, sizeof(int64_t) * noffs);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "sparsify bands");
     }
-    const double norm2_max = std::max(root, partner_norm2);
-    // 2. drop, bands, upper tiers
-    unsigned long long* stored_dev = nullptr;
-    e = cudaMalloc(&t->band, sizeof(int32_t) * 4 * (size_t)std::max<int64_t>(nl, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&stored_dev, sizeof(unsigned long long));
+    // 1. dense norms (and panels) of A; 2. drop, new bands, upper tiers
+    t->A = A;
+    t->lda = lda;
+    e = launch_build_norms(t, s);
+    t->A = nullptr;       // the tree holds its own copy of the kept leaves
+    t->lda = 0;
+    unsigned long long* hw = reinterpret_cast<unsigned long long*>(t->h_band + nband);
     if (e == cudaSuccess)
-        e = launch_sparsify_mark(t, tau, norm2_max, ctx->cfg.tie_rel, t->band, stored_dev, s);
-    std::vector<int32_t> band((size_t)(4 * nl));
-    unsigned long long stored = 0;
+        e = launch_sparsify_mark(t, tau, partner_norm2, ctx->cfg.tie_rel, t->band_new, t->sdev, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(band.data(), t->band, sizeof(int32_t) * 4 * nl, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(t->h_band, t->band_new, sizeof(int32_t) * 4 * nl,
+                            cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&stored, stored_dev, sizeof(stored), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(hw, t->sdev, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(stored_dev);
-    if (e != cudaSuccess) return fail(e, "sparsify bands");
-    // 3. slab and pack layout (host), storage
-    const int32_t* kmin = band.data();
+    if (e != cudaSuccess) return poison(cuda_err(ctx, e, "sparsify bands"));
+    double root;
+    memcpy(&root, &hw[1], sizeof(root));
+    if (!std::isfinite(root))
+        return set_err(ctx, SPAMM_ERR_NONFINITE, "an operand holds Inf or NaN");
+    // 3. slab and pack layout (host)
+    const int32_t* kmin = t->h_band;
     const int32_t* kmax = kmin + nl;
     const int32_t* imin = kmin + 2 * nl;
     const int32_t* imax = kmin + 3 * nl;
     const int CH = b / 16;
-    std::vector<int64_t> offs((size_t)(3 * nl + 2));
-    int64_t* roff = offs.data();
+    int64_t* roff = t->h_offs;
     int64_t* aoff = roff + nl;
     int64_t* boff = aoff + nl + 1;
     int64_t slab = 0, pa = 0, pb = 0;
@@ -437,31 +446,102 @@ spamm_status spamm_sparsify(spamm_ctx* ctx, const float* A, int64_t n, int64_t l
     }
     aoff[nl] = pa;
     boff[nl] = pb;
-    const int64_t piece = (int64_t)b * 16 * ((t->precision == SPAMM_PREC_BF16X3 || t->precision == SPAMM_PREC_F16X3) ? 2 : 4);
-    e = cudaMalloc(&t->offs, sizeof(int64_t) * offs.size());
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(t->offs, offs.data(), sizeof(int64_t) * offs.size(),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMalloc(&t->slab, sizeof(float) * (size_t)std::max<int64_t>(slab, 64));
+    const int64_t piece =
+        (int64_t)b * 16 *
+        ((t->precision == SPAMM_PREC_BF16X3 || t->precision == SPAMM_PREC_F16X3) ? 2 : 4);
     const int arrays = pack_arrays_for(t->precision);
-    for (int i = 0; i < arrays && e == cudaSuccess; ++i) {
-        e = cudaMalloc(&t->packA[i], (size_t)std::max<int64_t>(pa * piece, 256));
-        if (e == cudaSuccess) e = cudaMalloc(&t->packB[i], (size_t)std::max<int64_t>(pb * piece, 256));
+    // 4. storage: kept while the new bands fit.  The stream is idle here
+    // (synchronised above), so nothing in flight reads what is freed.
+    const bool first = t->slab == nullptr;
+    auto grown = [&](int64_t need, int64_t floor) {
+        return std::max<int64_t>(first ? need : need + need / 4, floor);
+    };
+    if (slab > t->slab_cap || first) {
+        cudaFree(t->slab);
+        t->slab = nullptr;
+        t->slab_cap = 0;
+        const int64_t c = grown(slab, 64);
+        e = cudaMalloc(&t->slab, sizeof(float) * (size_t)c);
+        if (e != cudaSuccess) return poison(cuda_err(ctx, e, "sparsify storage"));
+        t->slab_cap = c;
     }
+    auto packs = [&](void** arr, int64_t need, int64_t* cap) -> cudaError_t {
+        if (need <= *cap && arr[0]) return cudaSuccess;
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(arr[i]);
+            arr[i] = nullptr;
+        }
+        *cap = 0;
+        const int64_t c = grown(need, 256);
+        for (int i = 0; i < arrays; ++i) {
+            const cudaError_t ee = cudaMalloc(&arr[i], (size_t)c);
+            if (ee != cudaSuccess) return ee;
+        }
+        *cap = c;
+        return cudaSuccess;
+    };
+    e = packs(t->packA, pa * piece, &t->packa_cap);
+    if (e == cudaSuccess) e = packs(t->packB, pb * piece, &t->packb_cap);
+    if (e != cudaSuccess) return poison(cuda_err(ctx, e, "sparsify storage"));
+    // 5. offsets and bands, then the kept leaves into the slab (queued: the
+    // slab copy may still read A when the call returns)
+    e = cudaMemcpyAsync(t->offs, t->h_offs, sizeof(int64_t) * noffs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t->band, t->band_new, sizeof(int32_t) * 4 * nl,
+                            cudaMemcpyDeviceToDevice, s);
     t->sparse = 1;
     if (e == cudaSuccess) e = launch_slab_copy(t, A, lda, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(e, "sparsify storage");
-    t->A = nullptr;       // the tree holds its own copy of the kept leaves
-    t->lda = 0;
-    t->stored = (int64_t)stored;
-    t->bytes = (int64_t)sizeof(double) * t->nodes + (int64_t)sizeof(int32_t) * 4 * nl +
-               (int64_t)sizeof(int64_t) * (3 * nl + 2) + (int64_t)sizeof(float) * slab +
-               (int64_t)arrays * (pa + pb) * piece +
+    if (e != cudaSuccess) return poison(cuda_err(ctx, e, "sparsify storage"));
+    t->stored = (int64_t)hw[0];
+    t->bytes = (int64_t)sizeof(double) * t->nodes + (int64_t)sizeof(int32_t) * 8 * nl +
+               (int64_t)sizeof(int64_t) * (3 * nl + 2) + (int64_t)sizeof(float) * t->slab_cap +
+               (int64_t)arrays * (t->packa_cap + t->packb_cap) +
                (t->slices ? 2 * (int64_t)sizeof(double) * nl * nl * t->slices : 0);
+    return SPAMM_OK;
+}
+
+static spamm_status sparsify_args(spamm_ctx* ctx, double tau, double partner_norm2) {
+    if (!(tau >= 0.0) || !std::isfinite(tau) || !(partner_norm2 >= 0.0) ||
+        !std::isfinite(partner_norm2))
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tau and partner_norm2 must be finite and >= 0");
+    if (!precision_uses_tc(ctx->cfg.precision))
+        return set_err(ctx, SPAMM_ERR_UNSUPPORTED, "sparsified trees need a tensor-core precision");
+    return SPAMM_OK;
+}
+
+spamm_status spamm_sparsify(spamm_ctx* ctx, const float* A, int64_t n, int64_t lda, double tau,
+                            double partner_norm2, spamm_tree** out) {
+    if (!ctx || !out) return SPAMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    spamm_status st = check_matrix(ctx, A, n, lda);
+    if (st == SPAMM_OK) st = sparsify_args(ctx, tau, partner_norm2);
+    if (st != SPAMM_OK) return st;
+    spamm_tree* t = nullptr;
+    st = new_tree(ctx, A, n, lda, false, &t);
+    if (st != SPAMM_OK) return st;
+    st = sparsify_fill(ctx, t, A, lda, tau, partner_norm2);
+    if (st != SPAMM_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        free_tree_storage(t);
+        delete t;
+        return st;
+    }
     ctx->trees.push_back(t);
     *out = t;
     return SPAMM_OK;
+}
+
+spamm_status spamm_sparsify_into(spamm_ctx* ctx, spamm_tree* tree, const float* A, int64_t lda,
+                                 double tau, double partner_norm2) {
+    if (!ctx || !tree) return set_err(ctx, SPAMM_ERR_INVALID_ARG, "NULL argument");
+    if (!tree->sparse)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "not a sparsified tree");
+    if (tree->ctx != ctx || tree->precision != ctx->cfg.precision || tree->b != ctx->cfg.leaf)
+        return set_err(ctx, SPAMM_ERR_INVALID_ARG, "tree built under another configuration");
+    spamm_status st = check_matrix(ctx, A, tree->n, lda);
+    if (st == SPAMM_OK) st = sparsify_args(ctx, tau, partner_norm2);
+    if (st != SPAMM_OK) return st;
+    return sparsify_fill(ctx, tree, A, lda, tau, partner_norm2);
 }
 
 spamm_status spamm_tree_bytes(const spamm_tree* t, int64_t* bytes, int64_t* stored) {

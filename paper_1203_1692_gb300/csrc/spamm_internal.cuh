@@ -183,6 +183,15 @@ struct spamm_tree {
     int64_t* offs;      // roff (nl), aoff (nl + 1), boff (nl + 1) (device)
     int64_t stored;     // leaves kept
     int64_t bytes;      // device bytes the tree holds
+    // re-sparsify in place (spamm_sparsify_into): the new bands land in
+    // band_new until they are known to fit, the mark kernel's kept count and
+    // dense root in sdev[0..1]; pinned host copies of bands and offsets; the
+    // capacities of slab (floats) and of each pack array (bytes)
+    int32_t* band_new;
+    unsigned long long* sdev;
+    int32_t* h_band;    // 4 x nl, then the two words of sdev
+    int64_t* h_offs;    // 3 nl + 2
+    int64_t slab_cap, packa_cap, packb_cap;
 };
 
 // Device view of a sparsified tree's bands (see spamm_tree).
@@ -327,8 +336,8 @@ cudaError_t launch_packs(DevCtl* ctl, const spamm_tree* A, const spamm_tree* B, 
 // Sparsification (norms.cu): drop the leaves whose product with norm2_max
 // fails the SpAMM test at tau (norms and panels zeroed), then the row and
 // column bands of the kept leaves (4 x nl int32: kmin, kmax, imin, imax).
-cudaError_t launch_sparsify_mark(spamm_tree* t, double tau, double norm2_max, double rel,
-                                 int32_t* band, unsigned long long* stored, cudaStream_t s);
+cudaError_t launch_sparsify_mark(spamm_tree* t, double tau, double partner_norm2, double rel,
+                                 int32_t* band, unsigned long long* out, cudaStream_t s);
 // Copy the kept leaves of the dense A into the tree's slab.
 cudaError_t launch_slab_copy(spamm_tree* t, const float* A, int64_t lda, cudaStream_t s);
 cudaError_t launch_pyramid(spamm_tree* t, cudaStream_t s);

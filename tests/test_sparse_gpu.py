@@ -99,3 +99,73 @@ def test_sparsify_rejects_rebuild_and_fp32():
         t.rebuild(dA)
     with pytest.raises(P.SpammError):
         P.Context(leaf=16, precision="fp32").sparsify(dA, 1e-6, 0.0)
+
+
+@pytest.mark.parametrize("prec,b", [("tf32x3", 32), ("f16x3", 64), ("bf16x3", 16)])
+def test_resparsify_in_place_equals_a_fresh_tree(prec, b):
+    """spamm_sparsify_into gives the fresh tree's product bit for bit, when
+    the new bands fit (narrower decay: the storage is reused) and when they
+    do not (wider decay: it grows), and keeps its storage on a second call
+    with the same matrix."""
+    import paper_1203_1692_gb300 as P
+    n, tau = 1200, 1e-6
+    ctx = P.Context(leaf=b, precision=prec)
+    mats = [gen.exp_decay(n, lam, seed=s) for lam, s in ((0.85, 1), (0.7, 2), (0.93, 3))]
+    t = None
+    for A in mats:
+        dA = torch.from_numpy(A).cuda()
+        fresh = ctx.sparsify(dA, tau, 0.0)
+        C_ref = ctx.multiply(fresh, fresh, tau)
+        if t is None:
+            t = ctx.sparsify(dA, tau, 0.0)
+        else:
+            before = t.bytes
+            t.resparsify(dA, tau, 0.0)
+            # reused when the bands fit, grown beyond the need when not
+            assert t.bytes == before or t.bytes > fresh.bytes
+        assert t.stored_leaves == fresh.stored_leaves
+        C = ctx.multiply(t, t, tau)
+        torch.cuda.synchronize()
+        assert torch.equal(C, C_ref)
+        kept = t.bytes
+        t.resparsify(dA, tau, 0.0)
+        assert t.bytes == kept
+        assert torch.equal(ctx.multiply(t, t, tau), C_ref)
+        fresh.close()
+
+
+def test_resparsify_against_the_oracle_and_errors():
+    """A re-sparsified tree matches the oracle's sparsified product; a NaN
+    leaves the tree reporting NONFINITE until a good matrix is sparsified
+    into it; a dense tree, another n or another context is refused."""
+    import paper_1203_1692_gb300 as P
+    n, b, tau = 900, 32, 1e-5
+    A = gen.exp_decay(n, 0.8, seed=3)
+    big = 1e6 * _n2(A)
+    dA = torch.from_numpy(A).cuda()
+    ctx = P.Context(leaf=b, precision="tf32x3")
+    t = ctx.sparsify(torch.from_numpy(gen.exp_decay(n, 0.9, seed=4)).cuda(), tau, 0.0)
+    t.resparsify(dA, tau, big)
+    As, m = O.sparsify(A, b, tau, big)
+    assert t.stored_leaves == m
+    C = ctx.multiply(t, t, tau)
+    ref = O.multiply(As, As, b, tau)
+    assert rel_max_err(C.cpu().numpy(), ref.C) <= TOL["tf32x3"]
+    bad = A.copy()
+    bad[10, 20] = np.nan
+    with pytest.raises(P.SpammError) as err:
+        t.resparsify(torch.from_numpy(bad).cuda(), tau, 0.0)
+    assert err.value.status == P._abi.SPAMM_ERR_NONFINITE
+    with pytest.raises(P.SpammError) as err:
+        ctx.multiply(t, t, tau)
+    assert err.value.status == P._abi.SPAMM_ERR_NONFINITE
+    t.resparsify(dA, tau, big)
+    assert torch.equal(ctx.multiply(t, t, tau), C)
+    with pytest.raises(ValueError):
+        t.resparsify(torch.zeros(n + 1, n + 1, device="cuda"), tau, 0.0)
+    with pytest.raises(P.SpammError):
+        P._abi.spamm_sparsify_into(ctx.handle, ctx.build_norms(dA).handle, dA.data_ptr(), n,
+                                   tau, 0.0)
+    other = P.Context(leaf=b, precision="tf32x3")
+    with pytest.raises(P.SpammError):
+        P._abi.spamm_sparsify_into(other.handle, t.handle, dA.data_ptr(), n, tau, 0.0)
