@@ -44,7 +44,10 @@
 // every chunk starts from a zeroed TMEM accumulator, and the epilogue warps
 // add the finished chunk into a master FP32 accumulator held in registers
 // (one row of 128 values per thread) with round-to-nearest adds.  Chunks are
-// added in ascending K, so the result stays deterministic.
+// added in ascending K, so the result stays deterministic.  The epilogue
+// leaves each buffer zero when it has read it (and zeroes both at the
+// start), so the MMAs of a chunk accumulate onto zeros without a clearing
+// MMA of their own.
 //
 // Tile order: consecutive work items walk down a group of kGroupRows tile
 // rows before moving one tile column right, so the tiles in flight at once
@@ -56,7 +59,8 @@
 // columns) and its lane 0 issues the MMAs and commits, a stage's masks read
 // at once and its slots unrolled; warps 2-9 move the double-buffered
 // 128 x 256 chunk accumulators out of TMEM (two warps per TMEM lane quarter,
-// 128 columns each), sum them, apply alpha/beta and store C.  Every wait on
+// 128 columns each), zero them for the next chunk, sum them, apply
+// alpha/beta and store C.  Every wait on
 // an mbarrier gives up after one second, raises the timeout status and lets
 // the block drain its copies and MMAs, free TMEM and exit.
 //
