@@ -54,18 +54,31 @@ def order_of(order: str, ns):
     return idx
 
 
+def decay_from_pyramid(pyr, d: int) -> float:
+    """Share of ||A||_F^2 held by the diagonal leaves, read from a squared-norm
+    pyramid of depth d (tier t row-major at offset (4^t - 1) / 3, the root
+    first): 1 for a block-diagonal matrix, about b / n without decay."""
+    import numpy as np
+    nb = 1 << d
+    off = ((1 << (2 * d)) - 1) // 3
+    leaf = np.asarray(pyr[off:off + nb * nb], dtype=np.float64).reshape(nb, nb)
+    tot = float(pyr[0])
+    return float(np.trace(leaf)) / tot if tot > 0 else 1.0
+
+
 def decay_estimate(A, blk: int = 64) -> float:
-    """Share of ||A||_F^2 held by the blk x blk diagonal blocks of the square
-    matrix A (1 for block-diagonal matrices, about blk / n without decay)."""
-    import torch
-    n = A.shape[0]
-    nb = -(-n // blk)
-    P = torch.zeros((nb * blk, nb * blk), dtype=torch.float32, device=A.device)
-    P[:n, :n] = A
-    Q = P.view(nb, blk, nb, blk)
-    diag = torch.diagonal(Q, dim1=0, dim2=2)          # blk x blk x nb
-    tot = float((P.double() ** 2).sum())
-    return float((diag.double() ** 2).sum()) / tot if tot > 0 else 1.0
+    """The decay estimate of the square CUDA matrix A from its norm profile:
+    the library's leaf-norm pyramid at leaf blk (an FP32 context, no packs),
+    then the diagonal leaves' share of the root."""
+    from . import Context
+    ctx = Context(leaf=blk, precision="fp32")
+    try:
+        tree = ctx.build_norms(A)
+        share = decay_from_pyramid(tree.norms(), tree.depth)
+        tree.close()
+    finally:
+        ctx.close()
+    return share
 
 
 def decay_bucket(A) -> int:

@@ -31,30 +31,33 @@ def test_choice_permutation_and_cache_lookup():
         del autotune._CACHE[key]
 
 
+def _decay(A):
+    from oracle import oracle as O
+    return autotune.decay_from_pyramid(O.pyramid(A, 64), O.depth(A.shape[0], 64))
+
+
 def test_decay_estimate_separates_decay_rates():
     """The norm-profile decay estimate (share of ||A||_F^2 on the 64 x 64
-    diagonal blocks): 1 for a block-diagonal matrix, about 64/n without
-    decay, and ordered by the decay rate of exponential-decay matrices, so
-    batches of equal orders but different decay get different signatures."""
+    diagonal leaves, read from a squared-norm pyramid): 1 for a
+    block-diagonal matrix, about 64/n without decay, and ordered by the
+    decay rate of exponential-decay matrices, so batches of equal orders but
+    different decay get different signatures.  The pyramid here is the
+    oracle's; on the GPU the library builds it."""
+    import math
     import numpy as np
-    import torch
     import spamm_inputs as gen
     n = 512
-    bd = torch.zeros((n, n))
+    bd = np.zeros((n, n), dtype=np.float32)
     for k in range(0, n, 64):
         bd[k:k + 64, k:k + 64] = 1.0
-    assert abs(autotune.decay_estimate(bd) - 1.0) < 1e-12
-    flat = torch.from_numpy(gen.uniform_dense(n, seed=1))
-    assert abs(autotune.decay_estimate(flat) - 64 / n) < 0.02
-    e = [autotune.decay_estimate(torch.from_numpy(gen.exp_decay(n, lam, seed=2)))
-         for lam in (0.5, 0.9, 0.99)]
+    assert abs(_decay(bd) - 1.0) < 1e-12
+    assert abs(_decay(gen.uniform_dense(n, seed=1)) - 64 / n) < 0.02
+    e = [_decay(gen.exp_decay(n, lam, seed=2)) for lam in (0.5, 0.9, 0.99)]
     assert e[0] > e[1] > e[2]
-    b = [autotune.decay_bucket(torch.from_numpy(gen.exp_decay(n, lam, seed=2)))
-         for lam in (0.5, 0.99)]
+    b = [int(round(math.log2(_decay(gen.exp_decay(n, lam, seed=2))))) for lam in (0.5, 0.99)]
     assert b[0] != b[1]
     s1 = autotune.signature([n, n], [1e-7], "f16x3", decay=b)
     s2 = autotune.signature([n, n], [1e-7], "f16x3", decay=[b[0], b[0]])
     assert s1 != s2
     assert autotune.signature([n], [1e-7], "f16x3", tier_bits=10) != \
         autotune.signature([n], [1e-7], "f16x3")
-    del np

@@ -190,3 +190,14 @@ def test_rebuild_batched_matches_single_builds():
     ctx.rebuild_batched(trees, mats)
     for t, A in zip(trees, mats):
         assert np.array_equal(t.norms(), ctx.build_norms(A).norms())
+
+
+def test_decay_estimate_on_the_device_matches_the_oracle_pyramid():
+    """The autotuner's decay estimate reads the library's own norm pyramid;
+    it equals the same share computed from the oracle's pyramid."""
+    from paper_1203_1692_gb300 import autotune
+    for n, lam in ((700, 0.8), (2048, 0.95)):
+        A = gen.exp_decay(n, lam, seed=3)
+        ref = autotune.decay_from_pyramid(oracle.pyramid(A, 64), oracle.depth(n, 64))
+        got = autotune.decay_estimate(torch.from_numpy(A).cuda())
+        assert abs(got - ref) <= 1e-9 * ref
