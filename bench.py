@@ -75,8 +75,10 @@ TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense tensor-core ratio
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from an ncu capture (GB), keyed by (kernel, workload, precision,
-# leaf); refreshed whenever that kernel changes.
-TRAFFIC = {}
+# leaf, tier bits); refreshed whenever that kernel changes.  The water-like
+# entry: 1.2549 GB read + 0.2208 GB written, one launch of the settled
+# configuration (--quick --leaf 128 --tau 1e-3 --tier-bits 16).
+TRAFFIC = {("k_leaf_tc", "water7500", "f16x3", 128, 16): 1.2549 + 0.2208}
 
 
 def parse():
