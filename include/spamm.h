@@ -332,10 +332,11 @@ spamm_status spamm_stats_item(spamm_ctx *ctx, int32_t index, spamm_stats_t *out)
 /* End-to-end form with HOST matrices (row-major, ld = n): copies A and B
  * (and C when beta != 0) to device buffers owned by ctx, builds both trees,
  * multiplies and copies C back.  B may be NULL or equal to A for a square.
- * On the tensor-core precisions the leaf products run in up to three
- * launches of whole tile-row groups, and each group's rows of C are copied
- * back (on a side stream of ctx) while the next computes; C is the same as
- * from spamm_multiply, bit for bit.  Host buffers may be pageable or pinned
+ * On the tensor-core precisions the leaf products run in up to eight
+ * launches of whole tile-row groups on two side-by-side streams, and each
+ * launch's rows of C are copied back (on another side stream of ctx) as
+ * soon as it finishes, while the later ones compute; C is the same as from
+ * spamm_multiply, bit for bit.  Host buffers may be pageable or pinned
  * (pinned is faster).  Synchronises. */
 spamm_status spamm_multiply_host(spamm_ctx *ctx, const float *A, const float *B, int64_t n,
                                  double tau, float alpha, float beta, float *C);

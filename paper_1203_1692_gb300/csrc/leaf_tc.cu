@@ -1126,7 +1126,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_leaf_tc(TcBatch bt) {
 }
 
 template <int LEAF, int PREC, bool BAND>
-cudaError_t launch_b(spamm_ctx* ctx, const TcBatch& bt) {
+cudaError_t launch_b(spamm_ctx* ctx, const TcBatch& bt, cudaStream_t stream) {
     using T = PrecTraits<PREC>;
     const size_t smem = 1024 + (size_t)T::kStages * T::kStage;
     cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<LEAF, PREC, BAND>,
@@ -1135,13 +1135,13 @@ cudaError_t launch_b(spamm_ctx* ctx, const TcBatch& bt) {
     const int items = bt.total - bt.first;
     const int grid = items < ctx->sm_count ? items : ctx->sm_count;
     if (grid <= 0) return cudaSuccess;
-    k_leaf_tc<LEAF, PREC, BAND><<<grid, kThreads, smem, ctx->stream>>>(bt);
+    k_leaf_tc<LEAF, PREC, BAND><<<grid, kThreads, smem, stream>>>(bt);
     return cudaGetLastError();
 }
 
 template <int LEAF, int PREC>
-cudaError_t launch_t(spamm_ctx* ctx, const TcBatch& bt, bool band) {
-    return band ? launch_b<LEAF, PREC, true>(ctx, bt) : launch_b<LEAF, PREC, false>(ctx, bt);
+cudaError_t launch_t(spamm_ctx* ctx, const TcBatch& bt, bool band, cudaStream_t s) {
+    return band ? launch_b<LEAF, PREC, true>(ctx, bt, s) : launch_b<LEAF, PREC, false>(ctx, bt, s);
 }
 
 }  // namespace
@@ -1201,32 +1201,36 @@ static bool fill_batch(spamm_ctx* ctx, const LeafJob* jobs, int count, TcBatch& 
     return band;
 }
 
-static cudaError_t dispatch(spamm_ctx* ctx, const TcBatch& bt, bool band) {
+// On stream s; zero_ctr: clear the launch's work-item counter first (the
+// per-band counters of a banded launch start at zero with the control block).
+static cudaError_t dispatch(spamm_ctx* ctx, const TcBatch& bt, bool band, cudaStream_t s,
+                            bool zero_ctr) {
     const int p = ctx->cfg.precision;
     const int b = ctx->cfg.leaf;
     // every launch deals its work items out from a counter that starts at zero
-    cudaError_t e = cudaMemsetAsync(bt.ctr, 0, sizeof(unsigned int), ctx->stream);
+    cudaError_t e = cudaSuccess;
+    if (zero_ctr) e = cudaMemsetAsync(bt.ctr, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (b == 16) {
-        if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band);
-        else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band);
-        else if (p == SPAMM_PREC_BF16X3) e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band);
-        else e = launch_t<16, SPAMM_PREC_F16X3>(ctx, bt, band);
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<16, SPAMM_PREC_TF32X3>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<16, SPAMM_PREC_TF32>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<16, SPAMM_PREC_BF16X3>(ctx, bt, band, s);
+        else e = launch_t<16, SPAMM_PREC_F16X3>(ctx, bt, band, s);
     } else if (b == 32) {
-        if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt, band);
-        else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt, band);
-        else if (p == SPAMM_PREC_BF16X3) e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band);
-        else e = launch_t<32, SPAMM_PREC_F16X3>(ctx, bt, band);
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<32, SPAMM_PREC_TF32X3>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<32, SPAMM_PREC_TF32>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<32, SPAMM_PREC_BF16X3>(ctx, bt, band, s);
+        else e = launch_t<32, SPAMM_PREC_F16X3>(ctx, bt, band, s);
     } else if (b == 64) {
-        if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt, band);
-        else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt, band);
-        else if (p == SPAMM_PREC_BF16X3) e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band);
-        else e = launch_t<64, SPAMM_PREC_F16X3>(ctx, bt, band);
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<64, SPAMM_PREC_TF32X3>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<64, SPAMM_PREC_TF32>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<64, SPAMM_PREC_BF16X3>(ctx, bt, band, s);
+        else e = launch_t<64, SPAMM_PREC_F16X3>(ctx, bt, band, s);
     } else if (b == 128) {
-        if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt, band);
-        else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt, band);
-        else if (p == SPAMM_PREC_BF16X3) e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band);
-        else e = launch_t<128, SPAMM_PREC_F16X3>(ctx, bt, band);
+        if (p == SPAMM_PREC_TF32X3) e = launch_t<128, SPAMM_PREC_TF32X3>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_TF32) e = launch_t<128, SPAMM_PREC_TF32>(ctx, bt, band, s);
+        else if (p == SPAMM_PREC_BF16X3) e = launch_t<128, SPAMM_PREC_BF16X3>(ctx, bt, band, s);
+        else e = launch_t<128, SPAMM_PREC_F16X3>(ctx, bt, band, s);
     } else {
         e = cudaErrorNotSupported;
     }
@@ -1240,7 +1244,7 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
         TcBatch bt;
         const bool band =
             fill_batch(ctx, jobs + j0, count - j0 < kMaxBatch ? count - j0 : kMaxBatch, bt);
-        const cudaError_t e = dispatch(ctx, bt, band);
+        const cudaError_t e = dispatch(ctx, bt, band, ctx->stream, true);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1254,33 +1258,48 @@ cudaError_t launch_leaf_tc_jobs(spamm_ctx* ctx, const LeafJob* jobs, int count) 
 // the same bit for bit.
 cudaError_t launch_leaf_tc_banded(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                                   float alpha, float beta, float* C, int64_t ldc, int bands,
-                                  cudaError_t (*done)(void*, int64_t, int64_t), void* user) {
+                                  cudaError_t (*done)(void*, int64_t, int64_t, cudaStream_t),
+                                  void* user) {
     LeafJob jb{A, B, ctx, alpha, beta, C, ldc};
     TcBatch bt;
     const bool band = fill_batch(ctx, &jb, 1, bt);
     const int tr = bt.prods[0].tr, tc = bt.prods[0].tc;
     const int groups = (tr + kGroupRows - 1) / kGroupRows;
+    constexpr int kMaxBands = (int)(sizeof(DevCtl::band_ctr) / sizeof(unsigned int));
     if (bands > groups) bands = groups;
+    if (bands > kMaxBands) bands = kMaxBands;
     if (bands < 1) bands = 1;
+    // Bands alternate between the context stream and a side stream, so that
+    // the next band's blocks take the SMs a band's last wave leaves idle (the
+    // bands write disjoint rows of C); each has its own work-item counter.
+    cudaStream_t side = ctx->aux[1];
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->fork_ev, 0);
+    if (e != cudaSuccess) return e;
     // band i ends at group ceil(groups (i+1) / bands): the remainder goes to
     // the front, so the last band, whose copy-out nothing hides, is the
     // smallest
     int g0 = 0;
     for (int i = 0; i < bands; ++i) {
         const int g1 = (int)(((int64_t)groups * (i + 1) + bands - 1) / bands);
+        cudaStream_t s = (i & 1) ? side : ctx->stream;
         bt.first = g0 * kGroupRows * tc;
         bt.total = (g1 * kGroupRows < tr ? g1 * kGroupRows : tr) * tc;
-        cudaError_t e = dispatch(ctx, bt, band);
+        bt.ctr = &ctx->ctl->band_ctr[i];
+        e = dispatch(ctx, bt, band, s, false);
         if (e != cudaSuccess) return e;
         const int64_t r0 = (int64_t)g0 * kGroupRows * kTileRows;
         const int64_t r1 = std::min<int64_t>((int64_t)g1 * kGroupRows * kTileRows, A->n);
         if (done && r1 > r0) {
-            e = done(user, r0, r1);
+            e = done(user, r0, r1, s);
             if (e != cudaSuccess) return e;
         }
         g0 = g1;
     }
-    return cudaSuccess;
+    // the context stream continues after every band
+    e = cudaEventRecord(ctx->aux_ev[1], side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->aux_ev[1], 0);
+    return e;
 }
 
 cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B, float alpha,

@@ -611,11 +611,12 @@ spamm_status spamm_tree_norms(spamm_ctx* ctx, const spamm_tree* t, double* host_
 }
 
 // Copy-out hook of the banded leaf launch: rows [r0, r1) of the staged C
-// go to the host on aux[0] once the band that finished them has run.
-static cudaError_t copy_rows_out(void* user, int64_t r0, int64_t r1) {
+// go to the host on aux[0] once the band that finished them (on stream s)
+// has run.
+static cudaError_t copy_rows_out(void* user, int64_t r0, int64_t r1, cudaStream_t s) {
     spamm_ctx* ctx = static_cast<spamm_ctx*>(user);
     const int64_t n = ctx->last_n;
-    cudaError_t e = cudaEventRecord(ctx->aux_ev[0], ctx->stream);
+    cudaError_t e = cudaEventRecord(ctx->aux_ev[0], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux[0], ctx->aux_ev[0], 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->band_host + r0 * n, ctx->dC + r0 * n,
@@ -1292,14 +1293,16 @@ spamm_status spamm_multiply_host(spamm_ctx* ctx, const float* A, const float* B,
         if (st != SPAMM_OK) return st;
         tb = ctx->hostTreeB;
     }
-    // tensor-core path: C leaves in three bands, each copied out (aux[0])
-    // while the next band computes; the FP32 path copies it after the fact
+    // tensor-core path: C leaves in up to eight bands of whole tile-row
+    // groups, each copied out (aux[0]) while the later bands compute (the
+    // bands themselves overlap on two streams); the FP32 path copies it after
+    // the fact
     const bool banded = precision_uses_tc(ctx->cfg.precision);
     if (banded) {
         st = ensure_aux(ctx);
         if (st != SPAMM_OK) return st;
         ctx->band_host = C;
-        ctx->band_count = 3;
+        ctx->band_count = 8;
     }
     st = spamm_multiply(ctx, ctx->hostTreeA, tb, tau, alpha, beta, ctx->dC, n);
     ctx->band_host = nullptr;

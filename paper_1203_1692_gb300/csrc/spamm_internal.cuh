@@ -70,6 +70,8 @@ struct DevCtl {
                                     // the n x n matrices
     unsigned int status;
     unsigned int tile_ctr;          // work items taken by the blocks of the running leaf launch
+    unsigned int band_ctr[8];       // the same for each band of a banded leaf launch (host
+                                    // entry point; the bands may run at the same time)
 };
 
 // Words stored for tier t (a frontier that overflowed is truncated).
@@ -355,9 +357,12 @@ cudaError_t launch_leaf_tc(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree
                            float alpha, float beta, float* C, int64_t ldc);
 // The same product in `bands` launches of whole tile-row groups; after each,
 // done(user, row0, row1) is told which rows of C are final.
+// `done(user, r0, r1, s)`: rows [r0, r1) of C are final once stream s has
+// passed the call.  At most 8 bands.
 cudaError_t launch_leaf_tc_banded(spamm_ctx* ctx, const spamm_tree* A, const spamm_tree* B,
                                   float alpha, float beta, float* C, int64_t ldc, int bands,
-                                  cudaError_t (*done)(void*, int64_t, int64_t), void* user);
+                                  cudaError_t (*done)(void*, int64_t, int64_t, cudaStream_t),
+                                  void* user);
 // One product of a batched leaf launch: its trees, the context that ran its
 // cull and grouping (pool, control block, tile arrays), and its C.
 struct LeafJob {
