@@ -381,7 +381,8 @@ def run_reference(args, rank, world):
 
 def sampled_parity(A_h, C, b, tau, count=48, seed=1, tier_bits=0, precision="f16x3"):
     """max|dC| / max|C| of the GPU result against the FP64 oracle at the same
-    tau (and precision tier), on sampled C blocks (plus diagonal ones)."""
+    tau (and precision tier), on sampled C blocks (plus diagonal ones).  Part
+    of the CPU-baseline leg: called only where that leg runs."""
     from oracle import oracle as O
     n = A_h.shape[0]
     nl = -(-n // b)
@@ -402,8 +403,9 @@ def sampled_parity(A_h, C, b, tau, count=48, seed=1, tier_bits=0, precision="f16
 
 
 def measure_alt(P, precision, A, A_h, b, tau, C_exact, stream, steps, t_sgemm, tier_bits=0):
-    """The same step in another leaf precision: time, max error against the
-    FP64 product and sampled parity against the oracle."""
+    """The same step in another leaf precision: time and max error against
+    the FP64 product; returns the line's entry and the product (its sampled
+    parity against the oracle is taken in the CPU-baseline leg)."""
     import torch
     bits = tier_bits if precision in HIGH_BITS else 0
     ctx = P.Context(leaf=b, precision=precision, checked=True, tier_bits=bits)
@@ -411,7 +413,6 @@ def measure_alt(P, precision, A, A_h, b, tau, C_exact, stream, steps, t_sgemm, t
     C = torch.empty_like(A)
     ctx.multiply(tree, tree, tau, C=C)
     err = float((C.double() - C_exact).abs().max())
-    parity = sampled_parity(A_h, C, b, tau, tier_bits=bits, precision=precision)
     ctx.set_checked(False)
     for _ in range(3):
         tree.rebuild(A)
@@ -430,7 +431,7 @@ def measure_alt(P, precision, A, A_h, b, tau, C_exact, stream, steps, t_sgemm, t
     return {"precision": precision, "tier_bits": bits,
             "value": st["kept_flops_clipped"] / (ms * 1e-3) / 1e12,
             "unit": "TFLOP/s", "ms_per_step": ms, "speedup_vs_sgemm": t_sgemm / ms,
-            "max_err": err, "parity_sampled": parity}
+            "max_err": err, "parity_sampled": None}, C
 
 
 def run_quick(args, P, A, n, b, stream):
@@ -524,24 +525,30 @@ def run_batched(args, P, dev, rank, world, dist, summary=False):
         err_sp = max(err_sp, float((Cs[q][r].double() - ref).abs().max()) / scale)
         err_sg = max(err_sg, float(((A[r] @ A).double() - ref).abs().max()) / scale)
         del ref
-    # oracle parity on the four smallest products (sampled C blocks)
-    parity = []
-    for q in sorted(range(count), key=lambda q: ns[perm[q]])[:(2 if summary else 4)]:
-        A_h = mats[perm[q]].cpu().numpy()
-        if choice.slice:
-            # the sliced oracle is a full product: the smallest products only
-            from oracle import oracle as O
-            refC = O.multiply_sliced(A_h, A_h, b, 16, tau, tau_h=tau * 2.0 ** bits if bits
-                                     else 0.0, p=p_hi or 53,
-                                     ties_away=args.precision == "tf32x3")[0]
-            den = np.abs(refC).max()
-            parity.append({"rel_max_err_vs_oracle": float(
-                np.abs(Cs[q].cpu().numpy().astype(np.float64) - refC).max() / den),
-                "blocks": "all", "tau": tau, "tier_bits": bits, "slice": 16})
-        else:
-            parity.append(sampled_parity(A_h, Cs[q], b, tau, count=24, tier_bits=bits,
-                                         precision=args.precision))
-    par_worst = max(x["rel_max_err_vs_oracle"] for x in parity)
+    # CPU-baseline leg (rank 0, one GPU): the oracle on the smallest products
+    # also checks the GPU's results (sampled C blocks, or the whole sliced
+    # product, which the oracle forms in full)
+    def oracle_parity():
+        parity = []
+        for q in sorted(range(count), key=lambda q: ns[perm[q]])[:(2 if summary else 4)]:
+            A_h = mats[perm[q]].cpu().numpy()
+            if choice.slice:
+                from oracle import oracle as O
+                refC = O.multiply_sliced(A_h, A_h, b, 16, tau, tau_h=tau * 2.0 ** bits if bits
+                                         else 0.0, p=p_hi or 53,
+                                         ties_away=args.precision == "tf32x3")[0]
+                den = np.abs(refC).max()
+                parity.append({"rel_max_err_vs_oracle": float(
+                    np.abs(Cs[q].cpu().numpy().astype(np.float64) - refC).max() / den),
+                    "blocks": "all", "tau": tau, "tier_bits": bits, "slice": 16})
+            else:
+                parity.append(sampled_parity(A_h, Cs[q], b, tau, count=24, tier_bits=bits,
+                                             precision=args.precision))
+        return max(x["rel_max_err_vs_oracle"] for x in parity)
+
+    par_worst = None
+    if not args.no_cpu_baseline and world == 1 and rank == 0:
+        par_worst = oracle_parity()
 
     # --- the step in a CUDA graph -----------------------------------------
     ctx.set_checked(False)
@@ -962,6 +969,142 @@ def run_sparse(args, P, dev, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def median_ms(fn, warm, reps, flush):
+    """Median CUDA-event time of fn (ms) over reps runs after warm untimed
+    ones, with the buffer `flush` (larger than L2) written before every timed
+    run, so small inputs do not stay in L2 from one run to the next."""
+    import torch
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sorted(ts)[len(ts) // 2]
+
+
+def median_graph_ms(fn, s, warm, reps, flush):
+    """The same for fn captured once in a CUDA graph on stream s and
+    replayed (no host launch cost: what a serving loop pays)."""
+    import torch
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(warm):
+            fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fn()
+    ts = []
+    with torch.cuda.stream(s):
+        for _ in range(warm):
+            g.replay()
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.replay()
+            e1.record(s)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    del g
+    return sorted(ts)[len(ts) // 2]
+
+
+def run_configs(args, P, dev):
+    """The two other single-product configurations, one step each (norm
+    tree + multiply) against cuBLAS SGEMM, medians of CUDA-event timed runs
+    with L2 flushed between them, eager and as CUDA graphs:
+    - exponential decay n = 1024, FP32, b = 16, tau = 1e-6 (the fused
+      small-product path); errors against the whole FP64 product;
+    - algebraic decay n = 16384, b = 16, tau = 1e-8, TF32 and BF16x3; errors
+      against the FP64 product (cuBLAS DGEMM) on 256 sampled rows."""
+    import torch
+    from spamm_inputs import device as D
+    torch.backends.cuda.matmul.allow_tf32 = False
+    reps, warm = max(5, args.steps), max(3, args.warmup)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    gs = torch.cuda.Stream(device=dev)
+
+    def spamm(A, b, tau, prec):
+        ctx = P.Context(leaf=b, precision=prec, checked=True)
+        tree = ctx.build_norms(A)
+        C = torch.empty_like(A)
+        ctx.multiply(tree, tree, tau, C=C)
+        ctx.set_checked(False)
+
+        def step():
+            tree.rebuild(A)
+            ctx.multiply(tree, tree, tau, C=C)
+
+        ms = median_ms(step, warm, reps, flush)
+        st = ctx.stats()
+        P._abi.spamm_set_stream(ctx.handle, gs.cuda_stream)
+        ms_g = median_graph_ms(step, gs, warm, reps, flush)
+        ctx.stats()                      # raises if a replayed step failed
+        tree.close()
+        ctx.close()
+        return C, ms, ms_g, st
+
+    def sgemm(A):
+        Cs = torch.empty_like(A)
+        ms = median_ms(lambda: torch.mm(A, A, out=Cs), warm, reps, flush)
+        ms_g = median_graph_ms(lambda: torch.mm(A, A, out=Cs), gs, warm, reps, flush)
+        return Cs, ms, ms_g
+
+    out = {}
+    n, b, tau = 1024, 16, 1e-6
+    A = D.exp_decay(n, 0.9, seed=0, device=dev)
+    Cs, ms_sg, ms_sg_g = sgemm(A)
+    exact = A.double() @ A.double()
+    C, ms, ms_g, st = spamm(A, b, tau, "fp32")
+    nl = -(-n // b)
+    out["exp1024"] = {
+        "workload": WORKLOADS["exp1024"], "precision": "fp32", "leaf": b, "tau": tau,
+        "ms_per_step": ms, "graph_ms_per_step": ms_g, "sgemm_ms": ms_sg,
+        "sgemm_graph_ms": ms_sg_g, "throughput_vs_sgemm": ms_sg / ms,
+        "graph_throughput_vs_sgemm_graph": ms_sg_g / ms_g,
+        "kept_leaf_triples": st["leaf_triples"], "kept_fraction": st["leaf_triples"] / nl ** 3,
+        "kept_tflops": st["kept_flops_clipped"] / (ms * 1e-3) / 1e12,
+        "max_err": float((C.double() - exact).abs().max()),
+        "sgemm_max_err": float((Cs.double() - exact).abs().max())}
+    del A, Cs, C, exact
+
+    n, b, tau = 16384, 16, 1e-8
+    A = D.algebraic_decay(n, seed=0, device=dev)
+    Cs, ms_sg, ms_sg_g = sgemm(A)
+    rows = torch.randint(0, n, (256,), generator=torch.Generator().manual_seed(5)).to(dev)
+    A64 = A.double()
+    ref = A64[rows] @ A64
+    del A64
+    err_sg = float((Cs[rows].double() - ref).abs().max())
+    del Cs
+    nl = -(-n // b)
+    entry = {"workload": WORKLOADS["alg16384"], "leaf": b, "tau": tau, "sgemm_ms": ms_sg,
+             "sgemm_graph_ms": ms_sg_g, "sgemm_max_err_sampled_rows": err_sg,
+             "max_abs_C_sampled_rows": float(ref.abs().max())}
+    for prec in ("tf32", "bf16x3"):
+        C, ms, ms_g, st = spamm(A, b, tau, prec)
+        entry[prec] = {"ms_per_step": ms, "graph_ms_per_step": ms_g,
+                       "speedup_vs_sgemm": ms_sg / ms,
+                       "kept_tflops": st["kept_flops_clipped"] / (ms * 1e-3) / 1e12,
+                       "kept_leaf_triples": st["leaf_triples"],
+                       "kept_fraction": st["leaf_triples"] / nl ** 3,
+                       "max_err_sampled_rows": float((C[rows].double() - ref).abs().max())}
+        del C
+    out["alg16384"] = entry
+    del A, ref
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_nsweep(args, P, dev, rank, world, dist):
     """SpAMM against dense SGEMM as n grows (the paper's effective-rate and
     cycle-count-versus-n figures, on GB300): per n one step (norm tree +
@@ -975,48 +1118,13 @@ def run_nsweep(args, P, dev, rank, world, dist):
     ns = [256, 512, 1024, 2048, 4096, 8192, 16384]
     reps = max(3, args.steps)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    warm = max(2, args.warmup)
 
     def med(fn):
-        for _ in range(max(2, args.warmup)):
-            fn()
-        ts = []
-        for _ in range(reps):
-            flush.zero_()            # L2 flushed between timed runs (small n fits in it)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            fn()
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return sorted(ts)[len(ts) // 2]
+        return median_ms(fn, warm, reps, flush)
 
     def med_graph(fn, s):
-        """The same, for fn captured once in a CUDA graph on stream s and
-        replayed (no host launch cost: what a serving loop pays)."""
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            for _ in range(max(2, args.warmup)):
-                fn()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            fn()
-        ts = []
-        with torch.cuda.stream(s):
-            for _ in range(max(2, args.warmup)):
-                g.replay()
-            for _ in range(reps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(s)
-                g.replay()
-                e1.record(s)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-        del g
-        return sorted(ts)[len(ts) // 2]
+        return median_graph_ms(fn, s, warm, reps, flush)
 
     rows, launches = [], 0
     clocks = Clocks(dev.index or 0)
@@ -1203,12 +1311,11 @@ def run_single(args, P, A_h, A, n, dev, stream, rank, world, dist, local):
         ctx.multiply(tree, tree, tau, C=C)
         err_tau = float((C.double() - C_exact).abs().max())
         chosen = "search"
-    parity = sampled_parity(A_h, C, b, tau, tier_bits=bits, precision=args.precision)
     sweep = configured_range(args, P, A, C_exact, err_sgemm, b, stream)
-    alt = None
+    alt, C_alt = None, None
     if args.alt and args.alt != args.precision:
-        alt = measure_alt(P, args.alt, A, A_h, b, tau, C_exact, stream, args.steps, t_sgemm,
-                          tier_bits=bits)
+        alt, C_alt = measure_alt(P, args.alt, A, A_h, b, tau, C_exact, stream, args.steps,
+                                 t_sgemm, tier_bits=bits)
     del C_exact
     torch.cuda.empty_cache()
 
@@ -1285,6 +1392,7 @@ def run_single(args, P, A_h, A, n, dev, stream, rank, world, dist, local):
     if not args.no_sub and args.workload == "water7500":
         subs["batched64"] = run_batched(args, P, dev, rank, world, dist, summary=True)
         subs["serving"] = run_serving(args, P, dev, rank, world, dist, summary=True)
+        subs["configs"] = run_configs(args, P, dev)
 
     if rank != 0:
         return
@@ -1297,13 +1405,21 @@ def run_single(args, P, A_h, A, n, dev, stream, rank, world, dist, local):
                          sms, passes=mma_passes(args.precision, st))
     roof["traffic_unit"] = "GB per launch"
     cpu = None
+    parity = None
     if not args.no_cpu_baseline and world == 1:
+        # CPU-baseline leg: the oracle timed on sampled C blocks, and the same
+        # oracle checking the GPU's products on sampled blocks
         v, threads, desc, _ = cpu_sample(A_h, b, tau, args.cpu_seconds, tier_bits=bits,
                                          precision=args.precision)
         v1, desc1 = cpu_sample_single_thread(A_h, b, tau, min(3.0, args.cpu_seconds),
                                              tier_bits=bits, precision=args.precision)
         cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": desc,
                "single_thread": {"value": v1, "sample": desc1}, "cpu_model": cpu_model()}
+        parity = sampled_parity(A_h, C, b, tau, tier_bits=bits, precision=args.precision)
+        if alt is not None:
+            alt["parity_sampled"] = sampled_parity(A_h, C_alt, b, tau, tier_bits=alt["tier_bits"],
+                                                   precision=args.alt)
+    del C_alt
     in_range = [r for r in sweep if r["meets_sgemm_error"]]
     line = {
         "metric": METRIC,

@@ -76,3 +76,30 @@ def exp_decay(n: int, lam: float = 0.9, seed: int = 0, device="cuda", out=None):
         u = (_srl(z, 11).to(torch.float64) + 0.5) * (2.0 ** -52) - 1.0
         out[r0:r1] = (u * powers[(i - j).abs()]).to(torch.float32)
     return out
+
+
+def algebraic_decay(n: int, seed: int = 0, device="cuda", out=None):
+    """a_ij = s_ij / (|i-j|^2 + 1), s_ij = +-1, as
+    ``generators.algebraic_decay(n, seed)``: the same SplitMix64 draws
+    (stream 3), the sign from their top bit, the quotient in float64 and one
+    rounding to float32, so the same matrix bit for bit."""
+    import torch
+    if n <= 0 or n > _MAX_INDEX:
+        raise ValueError(f"matrix order {n} out of range")
+    dev = torch.device(device)
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    base = _as_i64(int(_seed_base(seed)))
+    j = torch.arange(n, dtype=torch.int64, device=dev)[None, :]
+    rows = max(1, _SLAB // n)
+    for r0 in range(0, n, rows):
+        r1 = min(n, r0 + rows)
+        i = torch.arange(r0, r1, dtype=torch.int64, device=dev)[:, None]
+        lo = torch.minimum(i, j)
+        hi = torch.maximum(i, j)
+        c = (3 << 56) | (lo << 28) | hi                      # stream 3
+        z = _mix64(base + (c + 1) * _GAMMA)
+        s = torch.where(z < 0, -1.0, 1.0).to(torch.float64)  # top bit set: -1
+        d = (i - j).abs().to(torch.float64)
+        out[r0:r1] = (s / (d * d + 1.0)).to(torch.float32)
+    return out

@@ -1,5 +1,5 @@
-"""The seeded input generators: the device form of the exponential-decay
-generator gives the host form's matrix bit for bit."""
+"""The seeded input generators: the device forms of the exponential- and
+algebraic-decay generators give the host forms' matrices bit for bit."""
 import numpy as np
 import pytest
 
@@ -37,3 +37,17 @@ def test_device_exp_decay_equals_host_on_gpu():
         a = gen.exp_decay(n, lam, seed=seed)
         b = D.exp_decay(n, lam, seed=seed, device="cuda").cpu().numpy()
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (300, 3), (1025, 12345)])
+def test_device_algebraic_decay_equals_host_on_cpu(n, seed):
+    a = gen.algebraic_decay(n, seed=seed)
+    b = D.algebraic_decay(n, seed=seed, device="cpu").numpy()
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.gpu
+def test_device_algebraic_decay_equals_host_on_gpu():
+    a = gen.algebraic_decay(3000, seed=0)
+    b = D.algebraic_decay(3000, seed=0, device="cuda").cpu().numpy()
+    assert np.array_equal(a, b)
