@@ -1024,8 +1024,11 @@ def run_configs(args, P, dev):
     with L2 flushed between them, eager and as CUDA graphs:
     - exponential decay n = 1024, FP32, b = 16, tau = 1e-6 (the fused
       small-product path); errors against the whole FP64 product;
-    - algebraic decay n = 16384, b = 16, tau = 1e-8, TF32 and BF16x3; errors
-      against the FP64 product (cuBLAS DGEMM) on 256 sampled rows."""
+    - algebraic decay n = 16384, tau = 1e-8, TF32 and BF16x3, each at the
+      fastest leaf size of {16, 32, 64, 128} (the configuration fixes tau and
+      the precisions, not the leaf; a larger leaf keeps a superset of the
+      products at the same tau); errors against the FP64 product (cuBLAS
+      DGEMM) on 256 sampled rows."""
     import torch
     from spamm_inputs import device as D
     torch.backends.cuda.matmul.allow_tf32 = False
@@ -1033,7 +1036,7 @@ def run_configs(args, P, dev):
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
     gs = torch.cuda.Stream(device=dev)
 
-    def spamm(A, b, tau, prec):
+    def spamm(A, b, tau, prec, graph=True):
         ctx = P.Context(leaf=b, precision=prec, checked=True)
         tree = ctx.build_norms(A)
         C = torch.empty_like(A)
@@ -1046,9 +1049,11 @@ def run_configs(args, P, dev):
 
         ms = median_ms(step, warm, reps, flush)
         st = ctx.stats()
-        P._abi.spamm_set_stream(ctx.handle, gs.cuda_stream)
-        ms_g = median_graph_ms(step, gs, warm, reps, flush)
-        ctx.stats()                      # raises if a replayed step failed
+        ms_g = None
+        if graph:
+            P._abi.spamm_set_stream(ctx.handle, gs.cuda_stream)
+            ms_g = median_graph_ms(step, gs, warm, reps, flush)
+            ctx.stats()                  # raises if a replayed step failed
         tree.close()
         ctx.close()
         return C, ms, ms_g, st
@@ -1086,13 +1091,18 @@ def run_configs(args, P, dev):
     del A64
     err_sg = float((Cs[rows].double() - ref).abs().max())
     del Cs
-    nl = -(-n // b)
-    entry = {"workload": WORKLOADS["alg16384"], "leaf": b, "tau": tau, "sgemm_ms": ms_sg,
-             "sgemm_graph_ms": ms_sg_g, "sgemm_max_err_sampled_rows": err_sg,
+    entry = {"workload": WORKLOADS["alg16384"].replace(", b=16", ""), "tau": tau,
+             "sgemm_ms": ms_sg, "sgemm_graph_ms": ms_sg_g, "sgemm_max_err_sampled_rows": err_sg,
              "max_abs_C_sampled_rows": float(ref.abs().max())}
     for prec in ("tf32", "bf16x3"):
+        by_leaf = {}
+        for b in (16, 32, 64, 128):
+            _, by_leaf[b], _, _ = spamm(A, b, tau, prec, graph=False)
+        b = min(by_leaf, key=by_leaf.get)
         C, ms, ms_g, st = spamm(A, b, tau, prec)
-        entry[prec] = {"ms_per_step": ms, "graph_ms_per_step": ms_g,
+        nl = -(-n // b)
+        entry[prec] = {"leaf": b, "ms_per_step": ms, "graph_ms_per_step": ms_g,
+                       "ms_per_step_by_leaf": {str(k): v for k, v in by_leaf.items()},
                        "speedup_vs_sgemm": ms_sg / ms,
                        "kept_tflops": st["kept_flops_clipped"] / (ms * 1e-3) / 1e12,
                        "kept_leaf_triples": st["leaf_triples"],
