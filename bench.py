@@ -221,8 +221,9 @@ def leaf_roofline(precision, peaks, peak_src, clk, kept_flops, alg_bytes, leaf_m
     if precision == "fp32":
         mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
         fpeak = dev_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        which = "median sampled SM clock" if clk["sm_mhz"] else "maximum SM clock"
         kernel, fsrc = "k_leaf_simt", (f"{dev_sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} "
-                                       "MHz (median sampled SM clock)")
+                                       f"MHz ({which})")
         fbound = "alu"
     else:
         key = "bf16_tflops"
@@ -1035,6 +1036,17 @@ def run_configs(args, P, dev):
     reps, warm = max(5, args.steps), max(3, args.warmup)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
     gs = torch.cuda.Stream(device=dev)
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def roofline(prec, st, n, b, kernel):
+        """The roofline of the leaf-product launch of the last step (its own
+        events), as for the headline line."""
+        roof = leaf_roofline(prec, peaks, peak_src, {"sm_mhz": None}, st["kept_flops_clipped"],
+                             leaf_alg_bytes(st, float(n) * n, b, prec), st["ms_numeric"], None,
+                             sms, passes=mma_passes(prec, st))
+        roof["kernel"] = kernel
+        return roof
 
     def spamm(A, b, tau, prec, graph=True):
         ctx = P.Context(leaf=b, precision=prec, checked=True)
@@ -1079,7 +1091,11 @@ def run_configs(args, P, dev):
         "kept_leaf_triples": st["leaf_triples"], "kept_fraction": st["leaf_triples"] / nl ** 3,
         "kept_tflops": st["kept_flops_clipped"] / (ms * 1e-3) / 1e12,
         "max_err": float((C.double() - exact).abs().max()),
-        "sgemm_max_err": float((Cs.double() - exact).abs().max())}
+        "sgemm_max_err": float((Cs.double() - exact).abs().max()),
+        # FP32 products of at most 128 leaves per side: one fused launch
+        # (cull, statistics, step list and leaf products)
+        "leaf_kernel_ms": st["ms_numeric"],
+        "roofline": roofline("fp32", st, n, b, "k_small_fp32 (fused cull and leaf products)")}
     del A, Cs, C, exact
 
     n, b, tau = 16384, 16, 1e-8
@@ -1107,7 +1123,9 @@ def run_configs(args, P, dev):
                        "kept_tflops": st["kept_flops_clipped"] / (ms * 1e-3) / 1e12,
                        "kept_leaf_triples": st["leaf_triples"],
                        "kept_fraction": st["leaf_triples"] / nl ** 3,
-                       "max_err_sampled_rows": float((C[rows].double() - ref).abs().max())}
+                       "max_err_sampled_rows": float((C[rows].double() - ref).abs().max()),
+                       "leaf_kernel_ms": st["ms_numeric"],
+                       "roofline": roofline(prec, st, n, b, "k_leaf_tc")}
         del C
     out["alg16384"] = entry
     del A, ref
