@@ -201,13 +201,20 @@ def test_tier_host_entry_point_equals_device_multiply():
     assert np.array_equal(Ch, Cd)
 
 
+def _settled():
+    import bench
+    return bench.SETTLED["water7500"]
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("b,tau,bits", [(64, 1e-3, 10), (128, 1e-3, 12), (64, 3e-3, 14)])
+@pytest.mark.parametrize("b,tau,bits", [(64, 1e-3, 10), (128, 1e-3, 12), (64, 3e-3, 14),
+                                        _settled()])
 def test_tier_water_like_n7500(b, tau, bits):
     """The water-like n = 7500 workload at the tolerances and tiers the
-    bench searches: the whole kept set and the full-split set against the
-    oracle's flat enumeration and leaf norms, and sampled C blocks against
-    the oracle's tiered blocks."""
+    bench searches, including the configuration it settles on and times:
+    the whole kept set and the full-split set against the oracle's flat
+    enumeration and leaf norms, and sampled C blocks against the oracle's
+    tiered blocks."""
     A = gen.water_like()
     n = A.shape[0]
     p, away = O.HIGH_PART["f16x3"]
