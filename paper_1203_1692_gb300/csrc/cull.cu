@@ -710,6 +710,7 @@ static void share_blocks(const std::vector<double>& weight, int total, int64_t c
 
 template <int NB>
 static int set_bases(CullBatch<NB>& cb, const std::vector<int>& blocks) {
+    if (cb.count < 0 || cb.count > NB) return 0;   // callers pass 1..NB products
     int b = 0;
     for (int p = 0; p < cb.count; ++p) {
         cb.bbase[p] = b;
