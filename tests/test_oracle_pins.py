@@ -549,3 +549,49 @@ def test_tiered_blocks_match_the_tiered_product():
         for q, (I, J) in enumerate(ij):
             blk = C[I * b:min(n, (I + 1) * b), J * b:min(n, (J + 1) * b)]
             assert np.array_equal(acc[q][:blk.shape[0], :blk.shape[1]], blk)
+
+
+# ------------------------------------- leaf-tier test == tier-by-tier (R17)
+def _keep_grid(na, nb, tau):
+    """The SpAMM predicate (R1-R3) on every (I, K, J) of two norm tiers."""
+    a = na[:, :, None]
+    b = nb[None, :, :]
+    return (a > 0.0) & (b > 0.0) & (a * b >= tau * tau)
+
+
+@pytest.mark.parametrize("n,b,tau,kind", [(300, 16, 1e-4, "exp"), (257, 8, 1e-3, "alg"),
+                                          (128, 4, 0.0, "dense"), (200, 16, 3e-2, "exp"),
+                                          (96, 2, 1e-2, "alg")])
+def test_leaf_tier_test_gives_the_tier_by_tier_cull_and_its_counts(n, b, tau, kind):
+    """R17: a leaf triple survives the level-by-level cull iff its own leaf
+    norms pass (every ancestor's norm product is at least the leaf's), and
+    tier t's tested triples are those whose parent passes, its kept ones
+    those that pass themselves.  Both readings, evaluated directly on the
+    oracle's pyramids, give the oracle's recursive triple set and per-tier
+    counts exactly."""
+    if kind == "exp":
+        A, B = gen.exp_decay(n, 0.85, seed=1), gen.exp_decay_nonsym(n, 0.9, seed=2)
+    elif kind == "alg":
+        A, B = gen.algebraic_decay(n, seed=3), gen.algebraic_decay(n, seed=4)
+    else:
+        A, B = gen.uniform_dense(n, seed=5, symmetric=False), gen.uniform_dense(n, seed=6)
+    ref = O.multiply(A, B, b, tau)
+    pa, pb = O.pyramid(A, b), O.pyramid(B, b)
+    d = O.depth(n, b)
+    leaf = _keep_grid(O.tier(pa, d), O.tier(pb, d), tau)
+    got = set(map(tuple, np.argwhere(leaf).tolist()))
+    assert got == set(map(tuple, ref.triples.tolist()))
+    cand, kept = [], []
+    for t in range(d + 1):
+        own = _keep_grid(O.tier(pa, t), O.tier(pb, t), tau)
+        if t == 0:
+            tested = np.ones_like(own)
+        else:
+            par = _keep_grid(O.tier(pa, t - 1), O.tier(pb, t - 1), tau)
+            tested = par.repeat(2, 0).repeat(2, 1).repeat(2, 2)
+        cand.append(int(tested.sum()))
+        kept.append(int((tested & own).sum()))
+        # kept iff passing itself: a passing triple's parent always passes
+        assert int(own.sum()) == kept[-1]
+    assert cand == ref.cand.tolist()
+    assert kept == ref.kept.tolist()
